@@ -1,0 +1,299 @@
+"""FP64 CPU oracle for the meshfree ALE / WLS scheme for the BGK equation.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may use it; the CUDA library never does.  The
+arithmetic lives in ``bgk_oracle.c`` (plain C, IEEE double, no fused
+multiply-add); this module builds it with gcc and wraps it with ctypes and
+numpy.  Every function names the passage of arXiv 2408.02350 it follows.
+
+Parity status: every function is pinned by a test of ``tests/test_oracle_*``
+against closed forms, invariants, brute force or the paper's printed numbers.
+The driven-cavity flow fields themselves have no printed values in the paper
+(its figures carry no data), so they rest on those pins and on GPU parity.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bgk_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_handle = None
+
+OK, E_OVERFLOW, E_SINGULAR, E_INVAL, E_NOMEM = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile bgk_oracle.c into oracle/_build/liboracle.so (gcc -O2, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("nv", C.c_int32), ("vmax", C.c_double), ("kn", C.c_double),
+        ("tau_mode", C.c_int32), ("ale", C.c_int32), ("periodic", C.c_int32),
+        ("lid_wall", C.c_int32), ("max_nbrs", C.c_int32), ("pad_", C.c_int32),
+        ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
+        ("guard", C.c_double), ("lid_u", C.c_double * 3),
+    ]
+
+
+def params(p: dict) -> Params:
+    """Oracle parameter block from a workload dict (see bgk_inputs)."""
+    q = Params()
+    q.dim, q.nv, q.vmax, q.kn = int(p["dim"]), int(p["nv"]), float(p["vmax"]), float(p["kn"])
+    q.tau_mode, q.ale, q.periodic = int(p.get("tau_mode", 0)), int(p.get("ale", 0)), int(p.get("periodic", 0))
+    q.lid_wall, q.max_nbrs = int(p.get("lid_wall", 0)), int(p.get("max_nbrs", 48))
+    q.dt, q.h, q.alpha = float(p["dt"]), float(p["h"]), float(p["alpha"])
+    q.wall_T, q.guard = float(p.get("wall_T", 1.0)), float(p.get("guard", 0.0))
+    lu = list(p.get("lid_u", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
+    for a in range(3):
+        q.lid_u[a] = float(lu[a])
+    return q
+
+
+_PD = C.POINTER(C.c_double)
+_PI = C.POINTER(C.c_int32)
+_PL = C.POINTER(C.c_int64)
+_PP = C.POINTER(Params)
+
+
+def lib():
+    global _handle
+    with _lock:
+        if _handle is None:
+            h = C.CDLL(build())
+            sig = {
+                "or_dv": (C.c_double, [C.c_int32, C.c_double]),
+                "or_velocity_nodes": (None, [C.c_int32, C.c_double, _PD]),
+                "or_velocity_grid": (None, [C.c_int32, C.c_int32, C.c_double, _PD]),
+                "or_tau_si": (C.c_double, [C.c_double] * 5),
+                "or_lambda_si": (C.c_double, [C.c_double] * 4),
+                "or_tau": (C.c_double, [_PP, C.c_double, C.c_double]),
+                "or_maxwellian": (None, [_PP, C.c_double, _PD, C.c_double, _PD]),
+                "or_moments_point": (None, [_PP, _PD, _PD, _PD, _PD]),
+                "or_neighbours_brute": (C.c_int64, [C.c_int32, C.c_int64, _PD, C.c_double, C.c_int32, C.c_int32, _PI, _PI]),
+                "or_neighbours_cells": (C.c_int64, [C.c_int32, C.c_int64, _PD, C.c_double, C.c_int32, C.c_int32, _PI, _PI]),
+                "or_frame": (None, [C.c_int32, _PD, _PD]),
+                "or_stencils": (C.c_int, [_PP, C.c_int64, _PD, _PI, _PI, _PI, _PD, _PD, _PD, _PD]),
+                "or_transport": (None, [_PP, C.c_int64, _PI, _PI, _PI, _PD, _PD, _PD, _PD, _PD]),
+                "or_moments": (None, [_PP, C.c_int64, _PD, _PD, _PD, _PD]),
+                "or_relax": (None, [_PP, C.c_int64, _PI, _PD, _PD, _PD, _PD, _PD]),
+                "or_boundary": (C.c_int, [_PP, C.c_int64, _PI, _PD, _PI, _PI, _PD, _PD, _PD, _PD, _PD]),
+                "or_move": (C.c_int64, [_PP, C.c_int64, _PI, _PD, _PD]),
+                "or_init_maxwellian": (None, [_PP, C.c_int64, C.c_double, _PD, C.c_double, _PD, _PD, _PD, _PD]),
+                "or_run": (C.c_int, [_PP, C.c_int64, _PD, _PI, _PD, _PD, _PD, _PD, _PD, C.c_int32, _PL]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(h, name)
+                fn.restype = res
+                fn.argtypes = args
+            _handle = h
+    return _handle
+
+
+def _d(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_PD)
+
+
+def _i(a):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_PI)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def ncomp(dim: int) -> int:
+    return 2 if dim == 2 else 1
+
+
+def nvel(dim: int, nv: int) -> int:
+    return nv ** dim
+
+
+# ---- velocity grid (Sec. 3.3) ----
+
+def dv(nv: int, vmax: float) -> float:
+    return lib().or_dv(nv, vmax)
+
+
+def velocity_nodes(nv: int, vmax: float) -> np.ndarray:
+    out = np.empty(nv)
+    lib().or_velocity_nodes(nv, vmax, _d(out))
+    return out
+
+
+def velocity_grid(dim: int, nv: int, vmax: float) -> np.ndarray:
+    out = np.empty((nv ** dim, dim))
+    lib().or_velocity_grid(dim, nv, vmax, _d(out))
+    return out
+
+
+# ---- kinetic model (Sec. 2) ----
+
+def tau_si(kb, R, diam, rho, T) -> float:
+    return lib().or_tau_si(kb, R, diam, rho, T)
+
+
+def lambda_si(kb, R, diam, rho) -> float:
+    return lib().or_lambda_si(kb, R, diam, rho)
+
+
+def tau(p: dict, rho: float, T: float) -> float:
+    q = params(p)
+    return lib().or_tau(C.byref(q), rho, T)
+
+
+def maxwellian(p: dict, rho: float, U, T: float) -> np.ndarray:
+    """[ncomp, NV] Maxwellian (3D) or Chu pair (G1, G2) (2D)."""
+    q = params(p)
+    U = _f64(np.resize(np.asarray(U, dtype=np.float64), 3))
+    out = np.empty((ncomp(p["dim"]), nvel(p["dim"], p["nv"])))
+    lib().or_maxwellian(C.byref(q), rho, _d(U), T, _d(out))
+    return out
+
+
+def moments_point(p: dict, fi: np.ndarray):
+    q = params(p)
+    fi = _f64(fi)
+    rho, T, U = np.empty(1), np.empty(1), np.empty(3)
+    lib().or_moments_point(C.byref(q), _d(fi), _d(rho), _d(U), _d(T))
+    return float(rho[0]), U[: p["dim"]].copy(), float(T[0])
+
+
+def moments(p: dict, f: np.ndarray):
+    q = params(p)
+    f = _f64(f)
+    n = f.shape[0]
+    rho, T, U = np.empty(n), np.empty(n), np.empty((n, p["dim"]))
+    lib().or_moments(C.byref(q), n, _d(f), _d(rho), _d(U), _d(T))
+    return rho, U, T
+
+
+# ---- neighbours (Sec. 3.5.1, Sec. 4.2) ----
+
+def neighbours(x: np.ndarray, h: float, periodic: bool = False, cap: int = 48, method: str = "cells"):
+    """(cnt [n], col [n, cap]) ELL lists, ascending per row; raises on overflow."""
+    x = _f64(x)
+    n, dim = x.shape
+    cnt = np.zeros(n, dtype=np.int32)
+    col = np.full((n, cap), -1, dtype=np.int32)
+    fn = lib().or_neighbours_cells if method == "cells" else lib().or_neighbours_brute
+    nnz = fn(dim, n, _d(x), h, int(periodic), cap, _i(cnt), _i(col))
+    if nnz < 0:
+        raise OverflowError("neighbour list overflow (max count %d > cap %d)" % (cnt.max(), cap))
+    return cnt, col
+
+
+def to_csr(cnt: np.ndarray, col: np.ndarray):
+    rowptr = np.zeros(len(cnt) + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(cnt)
+    cols = np.concatenate([col[i, : cnt[i]] for i in range(len(cnt))]) if len(cnt) else np.zeros(0, np.int32)
+    return rowptr, cols.astype(np.int32)
+
+
+# ---- stencils (Sec. 3.4) ----
+
+def frame(dim: int, dr) -> np.ndarray:
+    dr = _f64(dr)
+    out = np.empty((dim, dim))
+    lib().or_frame(dim, _d(dr), _d(out))
+    return out
+
+
+def stencils(p: dict, x, kind, cnt, col) -> dict:
+    q = params(p)
+    x, kind, cnt, col = _f64(x), _i32(kind), _i32(cnt), _i32(col)
+    n, dim = x.shape
+    cap = q.max_nbrs
+    assert col.shape == (n, cap)
+    coef = np.empty((n, cap, dim))
+    abar = np.empty((n, cap, dim))
+    frm = np.empty((n, cap, dim, dim))
+    recon = np.empty((n, cap))
+    st = lib().or_stencils(C.byref(q), n, _d(x), _i(kind), _i(cnt), _i(col), _d(coef), _d(abar), _d(frm), _d(recon))
+    if st != OK:
+        raise ArithmeticError("or_stencils: singular WLS system (status %d)" % st)
+    return {"coef": coef, "abar": abar, "frame": frm, "recon": recon}
+
+
+# ---- step pieces (Sec. 3.2, 3.4.2, 5) ----
+
+def transport(p: dict, kind, cnt, col, st: dict, U, f) -> np.ndarray:
+    q = params(p)
+    kind, cnt, col, f = _i32(kind), _i32(cnt), _i32(col), _f64(f)
+    U = _f64(U)
+    ft = np.empty_like(f)
+    lib().or_transport(C.byref(q), f.shape[0], _i(kind), _i(cnt), _i(col), _d(_f64(st["abar"])),
+                       _d(_f64(st["frame"])), _d(U), _d(f), _d(ft))
+    return ft
+
+
+def relax(p: dict, kind, ft, f, rho, U, T):
+    """In place on f, rho, U, T (interior points)."""
+    q = params(p)
+    lib().or_relax(C.byref(q), ft.shape[0], _i(_i32(kind)), _d(_f64(ft)), _d(f), _d(rho), _d(U), _d(T))
+
+
+def boundary(p: dict, kind, normal, cnt, col, st: dict, f, rho, U, T) -> int:
+    q = params(p)
+    return lib().or_boundary(C.byref(q), f.shape[0], _i(_i32(kind)), _d(_f64(normal)), _i(_i32(cnt)),
+                             _i(_i32(col)), _d(_f64(st["recon"])), _d(f), _d(rho), _d(U), _d(T))
+
+
+def move(p: dict, kind, U, x) -> int:
+    q = params(p)
+    return lib().or_move(C.byref(q), x.shape[0], _i(_i32(kind)), _d(_f64(U)), _d(x))
+
+
+class Simulation:
+    """State (x, f, rho, U, T) of one point cloud advanced by ``or_run``."""
+
+    def __init__(self, p: dict, cloud: dict, rho0: float = 1.0, U0=(0.0, 0.0, 0.0), T0: float = 1.0, f0=None):
+        self.p = dict(p)
+        self.q = params(p)
+        self.x = _f64(cloud["x"]).copy()
+        self.kind = _i32(cloud["kind"])
+        self.normal = _f64(cloud["normal"])
+        n, dim = self.x.shape
+        self.n, self.dim = n, dim
+        row = ncomp(dim) * nvel(dim, p["nv"])
+        self.f = np.empty((n, ncomp(dim), nvel(dim, p["nv"])))
+        self.rho, self.U, self.T = np.empty(n), np.empty((n, dim)), np.empty(n)
+        U0 = _f64(np.resize(np.asarray(U0, dtype=np.float64), 3))
+        lib().or_init_maxwellian(C.byref(self.q), n, rho0, _d(U0), T0, _d(self.f), _d(self.rho), _d(self.U), _d(self.T))
+        if f0 is not None:
+            self.f[...] = np.asarray(f0, dtype=np.float64).reshape(self.f.shape)
+            self.rho, self.U, self.T = moments(self.p, self.f)
+        self.clamps = 0
+        self.steps = 0
+        assert self.f.size == n * row
+
+    def run(self, nsteps: int) -> None:
+        cl = np.zeros(1, dtype=np.int64)
+        st = lib().or_run(C.byref(self.q), self.n, _d(self.x), _i(self.kind), _d(self.normal), _d(self.f),
+                          _d(self.rho), _d(self.U), _d(self.T), nsteps, cl.ctypes.data_as(_PL))
+        if st != OK:
+            raise RuntimeError("oracle or_run failed with status %d" % st)
+        self.clamps += int(cl[0])
+        self.steps += nsteps

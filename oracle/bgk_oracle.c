@@ -1,0 +1,654 @@
+/*
+ * FP64 CPU oracle for one time step of the meshfree ALE / weighted-least-squares
+ * scheme for the BGK equation (Mariappan, Willems, Boregowda, Tiwari, Klar,
+ * arXiv 2408.02350).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  The CUDA library never
+ * links it, and the two share no code: this file includes nothing but libc.
+ *
+ * Plain, slow loops in IEEE double, written to be checked against the paper by
+ * eye.  Built with -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Layouts (all row-major, C order):
+ *   x       [n][dim]               point positions
+ *   kind    [n]                    0 interior, >0 wall id
+ *   normal  [n][dim]               inward unit normal of a wall point
+ *   cnt/col [n], [n][cap]          neighbour lists, ascending index per row
+ *   f       [n][ncomp][NV]         ncomp = 2 in 2D (Chu g1, g2), 1 in 3D
+ *   velocity index k = kx + nv*(ky + nv*kz)
+ *
+ * Readings of the paper taken where it is garbled or silent:
+ *   - Maxwellian exponent carries a minus sign; the Chu G1 prefactor is
+ *     rho/(2 pi R T) (Eqs. maxwellian, Maxw_G1).
+ *   - In the upwind flux the second and third projected coefficients are beta
+ *     and gamma, "sign(b |c.t|)" means sign(b)|c.t|, and the 3D third bracket
+ *     uses c.b (Sec. 3.4.2).  The projected coefficients are the rows n, t, b
+ *     of the frame matrix applied to (alpha, beta, gamma).
+ *   - Nondimensional units R = 1, L = 1, rho0 = 1, T0 = 1, so
+ *     tau = sqrt(2/pi) Kn / (rho sqrt(T)) (Eqs. tau, lambda).
+ *   - Velocity nodes v_j = -vmax + j dv, j = 0..nv-1, dv = 2 vmax/(nv-1),
+ *     quadrature weight dv per axis (Sec. 3.3); nv counts the nodes (N_v + 1).
+ *   - Walls: diffuse reflection.  Velocities with v.n <= 0 (n inward) are
+ *     reconstructed from interior neighbours by a linear WLS fit (a constant
+ *     fit where fewer than dim+1 interior neighbours exist); velocities
+ *     with v.n > 0 get rho_w M(v; 1, u_w, T_w), rho_w from zero net mass flux.
+ *   - Sub-step order: neighbours and stencils, transport, moments, relaxation,
+ *     boundary, point motion.  The transport uses U^n, the moments of the
+ *     previous transported state (moments of f^0 at the first step).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+  int32_t dim;       /* 2: Chu-reduced g1, g2 ; 3: full f */
+  int32_t nv;        /* velocity nodes per axis */
+  double vmax;
+  double kn;         /* Knudsen number */
+  int32_t tau_mode;  /* 0 local tau(rho,T); 1 constant sqrt(2/pi) Kn; 2 no collisions */
+  int32_t ale;       /* 1: points move with U (Lagrangian form), transport with v - U */
+  int32_t periodic;  /* 1: periodic unit box, minimum-image separations, no walls */
+  int32_t lid_wall;  /* wall id that carries the lid velocity */
+  int32_t max_nbrs;  /* neighbour-list capacity per point */
+  int32_t pad_;
+  double dt, h, alpha, wall_T, guard;
+  double lid_u[3];
+} or_params;
+
+enum { OR_OK = 0, OR_E_OVERFLOW = 1, OR_E_SINGULAR = 2, OR_E_INVAL = 3, OR_E_NOMEM = 4 };
+
+static int ncomp_of(int dim) { return dim == 2 ? 2 : 1; }
+static int64_t nvel_of(int dim, int nv) { return dim == 2 ? (int64_t)nv * nv : (int64_t)nv * nv * nv; }
+
+/* ---- velocity grid (Sec. 3.3) ---- */
+
+double or_dv(int32_t nv, double vmax) { return 2.0 * vmax / (double)(nv - 1); }
+
+/* v_j = -vmax + j dv, written in the centred form (j - (nv-1)/2) dv, which is the
+ * same number in exact arithmetic and makes the grid exactly symmetric in floating
+ * point (v_{nv-1-j} = -v_j), so that a grazing velocity has v.n = 0 exactly on
+ * axis-aligned and diagonal walls. */
+void or_velocity_nodes(int32_t nv, double vmax, double* v) {
+  double dv = or_dv(nv, vmax);
+  for (int j = 0; j < nv; ++j) v[j] = ((double)j - 0.5 * (double)(nv - 1)) * dv;
+}
+
+/* vel[k][a] for the tensor-product grid, kx fastest. */
+void or_velocity_grid(int32_t dim, int32_t nv, double vmax, double* vel) {
+  double* nodes = (double*)malloc(sizeof(double) * nv);
+  or_velocity_nodes(nv, vmax, nodes);
+  int64_t NV = nvel_of(dim, nv);
+  for (int64_t k = 0; k < NV; ++k) {
+    int64_t r = k;
+    for (int a = 0; a < dim; ++a) {
+      vel[k * dim + a] = nodes[r % nv];
+      r /= nv;
+    }
+  }
+  free(nodes);
+}
+
+static double quad_weight(const or_params* p) {
+  double dv = or_dv(p->nv, p->vmax);
+  return p->dim == 2 ? dv * dv : dv * dv * dv;
+}
+
+/* ---- kinetic model (Sec. 2) ---- */
+
+/* Relaxation time, Eqs. (tau) and (lambda) in SI units. */
+double or_tau_si(double kb, double R, double diam, double rho, double T) {
+  const double pi = 3.14159265358979323846;
+  double lambda = kb / (sqrt(2.0) * pi * rho * R * diam * diam);
+  double cbar = sqrt(8.0 * R * T / pi);
+  return 4.0 * lambda / (pi * cbar);
+}
+
+/* Mean free path, Eq. (lambda). */
+double or_lambda_si(double kb, double R, double diam, double rho) {
+  const double pi = 3.14159265358979323846;
+  return kb / (sqrt(2.0) * pi * rho * R * diam * diam);
+}
+
+/* Nondimensional relaxation time: Eqs. (tau), (lambda) with R = L = rho0 = T0 = 1. */
+double or_tau(const or_params* p, double rho, double T) {
+  const double pi = 3.14159265358979323846;
+  if (p->tau_mode == 1) return sqrt(2.0 / pi) * p->kn;
+  return sqrt(2.0 / pi) * p->kn / (rho * sqrt(T));
+}
+
+/* Maxwellian at every node, Eq. (maxwellian) in 3D, Eqs. (Maxw_G1), (Maxw_G2) in 2D.
+ * out[ncomp][NV]. */
+void or_maxwellian(const or_params* p, double rho, const double* U, double T, double* out) {
+  const double pi = 3.14159265358979323846;
+  int dim = p->dim;
+  int64_t NV = nvel_of(dim, p->nv);
+  double* vel = (double*)malloc(sizeof(double) * NV * dim);
+  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  for (int64_t k = 0; k < NV; ++k) {
+    double c2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      double c = vel[k * dim + a] - U[a];
+      c2 = c2 + c * c;
+    }
+    if (dim == 3) {
+      out[k] = rho / pow(2.0 * pi * T, 1.5) * exp(-c2 / (2.0 * T));
+    } else {
+      double g1 = rho / (2.0 * pi * T) * exp(-c2 / (2.0 * T));
+      out[k] = g1;
+      out[NV + k] = T * g1;
+    }
+  }
+  free(vel);
+}
+
+/* Moments of one point's distribution, Eqs. (moments), (internal_energy), (macroeq),
+ * two-pass centred form.  fi[ncomp][NV] -> rho, U[dim], T. */
+void or_moments_point(const or_params* p, const double* fi, double* rho, double* U, double* T) {
+  int dim = p->dim;
+  int64_t NV = nvel_of(dim, p->nv);
+  double wv = quad_weight(p);
+  double* vel = (double*)malloc(sizeof(double) * NV * dim);
+  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  double r = 0.0, mom[3] = {0.0, 0.0, 0.0};
+  for (int64_t k = 0; k < NV; ++k) {
+    r += fi[k] * wv;
+    for (int a = 0; a < dim; ++a) mom[a] += vel[k * dim + a] * fi[k] * wv;
+  }
+  for (int a = 0; a < dim; ++a) U[a] = mom[a] / r;
+  double e = 0.0;
+  for (int64_t k = 0; k < NV; ++k) {
+    double c2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      double c = vel[k * dim + a] - U[a];
+      c2 = c2 + c * c;
+    }
+    e += c2 * fi[k] * wv;
+    if (dim == 2) e += fi[NV + k] * wv; /* + integral of g2, Eq. (macroeq) */
+  }
+  *rho = r;
+  *T = e / (3.0 * r);
+  free(vel);
+}
+
+/* ---- neighbour search (Sec. 3.5.1, Sec. 4.2) ---- */
+
+static double sep(double xi, double xj, int periodic) {
+  double d = xj - xi;
+  if (periodic) {
+    if (d > 0.5) d -= 1.0;
+    else if (d < -0.5) d += 1.0;
+  }
+  return d;
+}
+
+/* Squared distance as dx*dx + dy*dy (+ dz*dz), left to right, no fused multiply-add. */
+static double dist2(int dim, const double* xi, const double* xj, int periodic) {
+  double d2 = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    double d = sep(xi[a], xj[a], periodic);
+    d2 = d2 + d * d;
+  }
+  return d2;
+}
+
+/* Definition: N(i) = { j != i : |x_j - x_i|^2 <= h^2 }, ascending j.  O(n^2).
+ * Returns nnz, or -1 when a row exceeds cap (cnt then holds the true counts). */
+int64_t or_neighbours_brute(int32_t dim, int64_t n, const double* x, double h, int32_t periodic,
+                            int32_t cap, int32_t* cnt, int32_t* col) {
+  double h2 = h * h;
+  int64_t nnz = 0;
+  int overflow = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      if (dist2(dim, x + i * dim, x + j * dim, periodic) <= h2) {
+        if (c < cap) col[i * cap + c] = (int32_t)j;
+        ++c;
+      }
+    }
+    if (c > cap) overflow = 1;
+    cnt[i] = c;
+    nnz += c;
+  }
+  return overflow ? -1 : nnz;
+}
+
+/* Voxel (cell) search, as the paper's program does it: cells of side >= h,
+ * each point scans its own and the adjacent cells, then the row is sorted.
+ * Same contract as or_neighbours_brute. */
+int64_t or_neighbours_cells(int32_t dim, int64_t n, const double* x, double h, int32_t periodic,
+                            int32_t cap, int32_t* cnt, int32_t* col) {
+  double h2 = h * h;
+  int nc = (int)floor(1.0 / (h * (1.0 + 1e-9)));
+  if (nc < 1) nc = 1;
+  int64_t ncell = 1;
+  for (int a = 0; a < dim; ++a) ncell *= nc;
+  int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * n);
+  int64_t* start = (int64_t*)calloc(ncell + 1, sizeof(int64_t));
+  int64_t* fill = (int64_t*)calloc(ncell, sizeof(int64_t));
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+  int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0, stride = 1;
+    for (int a = 0; a < dim; ++a) {
+      int ca = (int)floor(x[i * dim + a] * nc);
+      if (ca < 0) ca = 0;
+      if (ca > nc - 1) ca = nc - 1;
+      c += ca * stride;
+      stride *= nc;
+    }
+    cell[i] = (int32_t)c;
+    start[c + 1]++;
+  }
+  for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+  for (int64_t i = 0; i < n; ++i) order[start[cell[i]] + fill[cell[i]]++] = (int32_t)i;
+
+  int64_t nnz = 0;
+  int overflow = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int ci[3] = {0, 0, 0};
+    int64_t r = cell[i];
+    for (int a = 0; a < dim; ++a) { ci[a] = (int)(r % nc); r /= nc; }
+    /* per-axis list of distinct cells to scan */
+    int lst[3][3], len[3];
+    for (int a = 0; a < 3; ++a) { len[a] = 1; lst[a][0] = 0; }
+    for (int a = 0; a < dim; ++a) {
+      len[a] = 0;
+      if (periodic && nc < 3) {
+        for (int c = 0; c < nc; ++c) lst[a][len[a]++] = c;
+      } else {
+        for (int o = -1; o <= 1; ++o) {
+          int c = ci[a] + o;
+          if (periodic) c = (c + nc) % nc;
+          else if (c < 0 || c >= nc) continue;
+          lst[a][len[a]++] = c;
+        }
+      }
+    }
+    int32_t m = 0;
+    for (int u = 0; u < len[2]; ++u)
+      for (int t = 0; t < len[1]; ++t)
+        for (int s = 0; s < len[0]; ++s) {
+          int64_t c = lst[0][s];
+          if (dim >= 2) c += (int64_t)lst[1][t] * nc;
+          if (dim >= 3) c += (int64_t)lst[2][u] * nc * nc;
+          for (int64_t q = start[c]; q < start[c + 1]; ++q) {
+            int32_t j = order[q];
+            if (j == i) continue;
+            if (dist2(dim, x + i * dim, x + (int64_t)j * dim, periodic) <= h2) cand[m++] = j;
+          }
+        }
+    /* insertion sort, ascending index */
+    for (int32_t a = 1; a < m; ++a) {
+      int32_t v = cand[a], b = a - 1;
+      while (b >= 0 && cand[b] > v) { cand[b + 1] = cand[b]; --b; }
+      cand[b + 1] = v;
+    }
+    for (int32_t a = 0; a < m && a < cap; ++a) col[i * cap + a] = cand[a];
+    if (m > cap) overflow = 1;
+    cnt[i] = m;
+    nnz += m;
+  }
+  free(cell); free(start); free(fill); free(order); free(cand);
+  return overflow ? -1 : nnz;
+}
+
+/* ---- weighted least squares (Sec. 3.4.1) ---- */
+
+/* Inverse of a small symmetric matrix by Gauss-Jordan elimination with partial
+ * pivoting.  Returns 0, or OR_E_SINGULAR when a pivot is not above tol * max|A|. */
+static int gj_inverse(int m, const double* A, double* Ainv) {
+  double a[4][8];
+  double amax = 0.0;
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c) {
+      a[r][c] = A[r * m + c];
+      a[r][m + c] = (r == c) ? 1.0 : 0.0;
+      if (fabs(a[r][c]) > amax) amax = fabs(a[r][c]);
+    }
+  if (!(amax > 0.0)) return OR_E_SINGULAR;
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r) if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+    if (!(fabs(a[piv][c]) > 1e-12 * amax)) return OR_E_SINGULAR;
+    if (piv != c)
+      for (int k = 0; k < 2 * m; ++k) { double t = a[c][k]; a[c][k] = a[piv][k]; a[piv][k] = t; }
+    double d = a[c][c];
+    for (int k = 0; k < 2 * m; ++k) a[c][k] /= d;
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      double fct = a[r][c];
+      for (int k = 0; k < 2 * m; ++k) a[r][k] -= fct * a[c][k];
+    }
+  }
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c) Ainv[r * m + c] = a[r][m + c];
+  return OR_OK;
+}
+
+/* Truncated Gaussian weight, Eq. (weight); callers pass only r <= h. */
+static double weight(const or_params* p, double r2) { return exp(-p->alpha * r2 / (p->h * p->h)); }
+
+/* Local frame of the pair (i, j) from the angles of Sec. 3.4.2:
+ * 2D  n = (cos phi, sin phi), t = (-sin phi, cos phi), phi = atan2(dy, dx);
+ * 3D  rows n, t, b of the matrix A, phi = atan2(dy, dx), theta = arccos(dz / r). */
+void or_frame(int32_t dim, const double* dr, double* frame /* [dim][dim], rows n, t(, b) */) {
+  if (dim == 2) {
+    double phi = atan2(dr[1], dr[0]);
+    frame[0] = cos(phi); frame[1] = sin(phi);
+    frame[2] = -sin(phi); frame[3] = cos(phi);
+  } else {
+    double r = sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+    double phi = atan2(dr[1], dr[0]);
+    double theta = acos(dr[2] / r);
+    frame[0] = sin(theta) * cos(phi); frame[1] = sin(theta) * sin(phi); frame[2] = cos(theta);
+    frame[3] = cos(theta) * cos(phi); frame[4] = cos(theta) * sin(phi); frame[5] = -sin(theta);
+    frame[6] = -sin(phi);             frame[7] = cos(phi);              frame[8] = 0.0;
+  }
+}
+
+/* Stencils of every point.
+ * Interior i: S = (M^T W M)^-1 (Eq. solution), gradient coefficients
+ *   coef_j = w_j S dr_j, i.e. (alpha_ij, beta_ij, gamma_ij) of Eqs. (x_derivative)-(z_derivative);
+ *   frame_j (rows n, t, b) and the projected coefficients abar_j = frame_j coef_j.
+ * Wall b: linear WLS reconstruction over interior neighbours, p_j = (1, dr_j):
+ *   recon_j = e_0^T (sum_k w_k p_k p_k^T)^-1 w_j p_j, so that f_b = sum_j recon_j f_j;
+ *   with fewer than dim+1 interior neighbours (3D corners) the constant fit
+ *   recon_j = w_j / sum_k w_k.
+ * Slots of a row that do not apply are zero.  Returns OR_OK or OR_E_SINGULAR. */
+int or_stencils(const or_params* p, int64_t n, const double* x, const int32_t* kind,
+                const int32_t* cnt, const int32_t* col, double* coef, double* abar, double* frame,
+                double* recon) {
+  int dim = p->dim, cap = p->max_nbrs;
+  int status = OR_OK;
+  memset(coef, 0, sizeof(double) * n * cap * dim);
+  memset(abar, 0, sizeof(double) * n * cap * dim);
+  memset(frame, 0, sizeof(double) * n * cap * dim * dim);
+  memset(recon, 0, sizeof(double) * n * cap);
+  for (int64_t i = 0; i < n; ++i) {
+    const double* xi = x + i * dim;
+    if (kind[i] == 0) {
+      double A[9] = {0}, S[9];
+      for (int s = 0; s < cnt[i]; ++s) {
+        const double* xj = x + (int64_t)col[i * cap + s] * dim;
+        double dr[3];
+        for (int a = 0; a < dim; ++a) dr[a] = sep(xi[a], xj[a], p->periodic);
+        double w = weight(p, dist2(dim, xi, xj, p->periodic));
+        for (int a = 0; a < dim; ++a)
+          for (int b = 0; b < dim; ++b) A[a * dim + b] += w * dr[a] * dr[b];
+      }
+      if (cnt[i] < dim || gj_inverse(dim, A, S) != OR_OK) { status = OR_E_SINGULAR; continue; }
+      for (int s = 0; s < cnt[i]; ++s) {
+        int64_t slot = i * cap + s;
+        const double* xj = x + (int64_t)col[slot] * dim;
+        double dr[3], fr[9];
+        for (int a = 0; a < dim; ++a) dr[a] = sep(xi[a], xj[a], p->periodic);
+        double w = weight(p, dist2(dim, xi, xj, p->periodic));
+        for (int a = 0; a < dim; ++a) {
+          double acc = 0.0;
+          for (int b = 0; b < dim; ++b) acc += S[a * dim + b] * dr[b];
+          coef[slot * dim + a] = w * acc;
+        }
+        or_frame(dim, dr, fr);
+        for (int d = 0; d < dim; ++d) {
+          double acc = 0.0;
+          for (int a = 0; a < dim; ++a) acc += fr[d * dim + a] * coef[slot * dim + a];
+          abar[slot * dim + d] = acc;
+        }
+        for (int q = 0; q < dim * dim; ++q) frame[slot * dim * dim + q] = fr[q];
+      }
+    } else {
+      int m = dim + 1, ninner = 0;
+      double B[16] = {0}, Binv[16];
+      for (int s = 0; s < cnt[i]; ++s) {
+        int32_t j = col[i * cap + s];
+        if (kind[j] != 0) continue;
+        const double* xj = x + (int64_t)j * dim;
+        double pj[4];
+        pj[0] = 1.0;
+        for (int a = 0; a < dim; ++a) pj[1 + a] = sep(xi[a], xj[a], p->periodic);
+        double w = weight(p, dist2(dim, xi, xj, p->periodic));
+        for (int a = 0; a < m; ++a)
+          for (int b = 0; b < m; ++b) B[a * m + b] += w * pj[a] * pj[b];
+        ++ninner;
+      }
+      if (ninner == 0) { status = OR_E_SINGULAR; continue; }
+      if (ninner < m) {
+        /* too few interior neighbours for a linear fit: weighted mean (constant fit) */
+        double wsum = 0.0;
+        for (int s = 0; s < cnt[i]; ++s) {
+          int32_t j = col[i * cap + s];
+          if (kind[j] != 0) continue;
+          wsum += weight(p, dist2(dim, xi, x + (int64_t)j * dim, p->periodic));
+        }
+        for (int s = 0; s < cnt[i]; ++s) {
+          int32_t j = col[i * cap + s];
+          if (kind[j] != 0) continue;
+          recon[i * cap + s] = weight(p, dist2(dim, xi, x + (int64_t)j * dim, p->periodic)) / wsum;
+        }
+        continue;
+      }
+      if (gj_inverse(m, B, Binv) != OR_OK) { status = OR_E_SINGULAR; continue; }
+      for (int s = 0; s < cnt[i]; ++s) {
+        int32_t j = col[i * cap + s];
+        if (kind[j] != 0) continue;
+        const double* xj = x + (int64_t)j * dim;
+        double pj[4];
+        pj[0] = 1.0;
+        for (int a = 0; a < dim; ++a) pj[1 + a] = sep(xi[a], xj[a], p->periodic);
+        double w = weight(p, dist2(dim, xi, xj, p->periodic));
+        double acc = 0.0;
+        for (int b = 0; b < m; ++b) acc += Binv[b] * pj[b];
+        recon[i * cap + s] = w * acc;
+      }
+    }
+  }
+  return status;
+}
+
+/* ---- explicit transport with the positive upwind flux (Eq. explicit, Sec. 3.4.2) ---- */
+
+static double sgn(double a) { return a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0); }
+
+/* Upwind coefficient of neighbour slot s for convective velocity c:
+ * abar_n [(c.n) - |c.n|] + abar_t [(c.t) - sign(abar_t)|c.t|] + abar_b [(c.b) - sign(abar_b)|c.b|]. */
+static double upwind_coef(int dim, const double* ab, const double* fr, const double* c) {
+  double cn = 0.0, ct = 0.0, cb = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    cn += c[a] * fr[a];
+    ct += c[a] * fr[dim + a];
+    if (dim == 3) cb += c[a] * fr[2 * dim + a];
+  }
+  double K = ab[0] * (cn - fabs(cn)) + ab[1] * (ct - sgn(ab[1]) * fabs(ct));
+  if (dim == 3) K += ab[2] * (cb - sgn(ab[2]) * fabs(cb));
+  return K;
+}
+
+/* ft_i = f_i - dt Q(f)_i for interior i, Q = sum_j K_ij(v - U_i) (f_j - f_i);
+ * U enters only with ale = 1.  Wall rows are copied. */
+void or_transport(const or_params* p, int64_t n, const int32_t* kind, const int32_t* cnt,
+                  const int32_t* col, const double* abar, const double* frame, const double* U,
+                  const double* f, double* ft) {
+  int dim = p->dim, cap = p->max_nbrs, nc = ncomp_of(dim);
+  int64_t NV = nvel_of(dim, p->nv), row = nc * NV;
+  double* vel = (double*)malloc(sizeof(double) * NV * dim);
+  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  for (int64_t i = 0; i < n; ++i) {
+    const double* fi = f + i * row;
+    double* fti = ft + i * row;
+    if (kind[i] != 0) { memcpy(fti, fi, sizeof(double) * row); continue; }
+    for (int64_t k = 0; k < NV; ++k) {
+      double c[3] = {0.0, 0.0, 0.0};
+      for (int a = 0; a < dim; ++a) c[a] = vel[k * dim + a] - (p->ale ? U[i * dim + a] : 0.0);
+      double Q[2] = {0.0, 0.0};
+      for (int s = 0; s < cnt[i]; ++s) {
+        int64_t slot = i * cap + s;
+        const double* fj = f + (int64_t)col[slot] * row;
+        double K = upwind_coef(dim, abar + slot * dim, frame + slot * dim * dim, c);
+        for (int q = 0; q < nc; ++q) Q[q] += K * (fj[q * NV + k] - fi[q * NV + k]);
+      }
+      for (int q = 0; q < nc; ++q) fti[q * NV + k] = fi[q * NV + k] - p->dt * Q[q];
+    }
+  }
+  free(vel);
+}
+
+/* ---- moments and implicit relaxation (Sec. 3.2.1, 3.2.2) ---- */
+
+void or_moments(const or_params* p, int64_t n, const double* f, double* rho, double* U, double* T) {
+  int dim = p->dim;
+  int64_t row = ncomp_of(dim) * nvel_of(dim, p->nv);
+  for (int64_t i = 0; i < n; ++i) or_moments_point(p, f + i * row, rho + i, U + i * dim, T + i);
+}
+
+/* f^{n+1} = (tau ft + dt M^{n+1}) / (tau + dt) at interior points, M^{n+1} from the
+ * moments of ft (Eqs. fullmoment1a, moment1a, moment1b).  Writes the moments to rho, U, T. */
+void or_relax(const or_params* p, int64_t n, const int32_t* kind, const double* ft, double* f,
+              double* rho, double* U, double* T) {
+  int dim = p->dim;
+  int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
+  double* M = (double*)malloc(sizeof(double) * row);
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != 0) continue;
+    const double* fti = ft + i * row;
+    double* fi = f + i * row;
+    or_moments_point(p, fti, rho + i, U + i * dim, T + i);
+    if (p->tau_mode == 2) { memcpy(fi, fti, sizeof(double) * row); continue; }
+    double tau = or_tau(p, rho[i], T[i]);
+    or_maxwellian(p, rho[i], U + i * dim, T[i], M);
+    for (int64_t q = 0; q < row; ++q) fi[q] = (tau * fti[q] + p->dt * M[q]) / (tau + p->dt);
+  }
+  free(M);
+}
+
+/* ---- diffuse-reflection walls (Sec. 5.1, 5.2; Table 3) ---- */
+
+/* At every wall point: v.n <= 0 reconstructed, f_b = sum_j recon_j f_j;
+ * v.n > 0: rho_w M(v; 1, u_w, T_w) with
+ * rho_w = sum_{v.n<=0} |v.n| g_b / sum_{v.n>0} (v.n) M(v; 1, u_w, T_w)   (g = first component).
+ * u_w is the lid velocity on kind == lid_wall, zero elsewhere.  Then the wall
+ * point's moments are taken from f_b.  Returns OR_OK or OR_E_SINGULAR (no flux). */
+int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double* normal,
+                const int32_t* cnt, const int32_t* col, const double* recon, double* f,
+                double* rho, double* U, double* T) {
+  int dim = p->dim, cap = p->max_nbrs, nc = ncomp_of(dim);
+  int64_t NV = nvel_of(dim, p->nv), row = nc * NV;
+  int status = OR_OK;
+  double* vel = (double*)malloc(sizeof(double) * NV * dim);
+  double* Mw = (double*)malloc(sizeof(double) * row);
+  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  for (int64_t b = 0; b < n; ++b) {
+    if (kind[b] == 0) continue;
+    double* fb = f + b * row;
+    const double* nb = normal + b * dim;
+    double uw[3] = {0.0, 0.0, 0.0};
+    if (kind[b] == p->lid_wall)
+      for (int a = 0; a < dim; ++a) uw[a] = p->lid_u[a];
+    or_maxwellian(p, 1.0, uw, p->wall_T, Mw);
+    double out_flux = 0.0, in_norm = 0.0;
+    for (int64_t k = 0; k < NV; ++k) {
+      double vn = 0.0;
+      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      if (vn <= 0.0) {
+        for (int q = 0; q < nc; ++q) {
+          double acc = 0.0;
+          for (int s = 0; s < cnt[b]; ++s) {
+            int64_t slot = b * cap + s;
+            if (kind[col[slot]] != 0) continue;
+            acc += recon[slot] * f[(int64_t)col[slot] * row + q * NV + k];
+          }
+          fb[q * NV + k] = acc;
+        }
+        out_flux += -vn * fb[k];
+      } else {
+        in_norm += vn * Mw[k];
+      }
+    }
+    if (!(in_norm > 0.0)) { status = OR_E_SINGULAR; continue; }
+    double rho_w = out_flux / in_norm;
+    for (int64_t k = 0; k < NV; ++k) {
+      double vn = 0.0;
+      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      if (vn > 0.0)
+        for (int q = 0; q < nc; ++q) fb[q * NV + k] = rho_w * Mw[q * NV + k];
+    }
+    or_moments_point(p, fb, rho + b, U + b * dim, T + b);
+  }
+  free(vel);
+  free(Mw);
+  return status;
+}
+
+/* ---- point motion (Eq. originalALE1, ALE1): x^{n+1} = x^n + dt U^{n+1} ---- */
+
+/* Interior points only.  Cavity: each coordinate is clamped to [guard, 1 - guard];
+ * periodic box: wrapped into [0, 1).  Returns the number of clamped coordinates. */
+int64_t or_move(const or_params* p, int64_t n, const int32_t* kind, const double* U, double* x) {
+  int dim = p->dim;
+  int64_t clamps = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != 0) continue;
+    for (int a = 0; a < dim; ++a) {
+      double y = x[i * dim + a] + p->dt * U[i * dim + a];
+      if (p->periodic) {
+        if (y >= 1.0) y -= 1.0;
+        else if (y < 0.0) y += 1.0;
+      } else if (y < p->guard) { y = p->guard; ++clamps; }
+      else if (y > 1.0 - p->guard) { y = 1.0 - p->guard; ++clamps; }
+      x[i * dim + a] = y;
+    }
+  }
+  return clamps;
+}
+
+/* ---- initial state (Sec. 2.1): f^0 = Maxwellian(rho0, U0, T0) everywhere ---- */
+
+void or_init_maxwellian(const or_params* p, int64_t n, double rho0, const double* U0, double T0,
+                        double* f, double* rho, double* U, double* T) {
+  int dim = p->dim;
+  int64_t row = ncomp_of(dim) * nvel_of(dim, p->nv);
+  or_maxwellian(p, rho0, U0, T0, f);
+  for (int64_t i = 1; i < n; ++i) memcpy(f + i * row, f, sizeof(double) * row);
+  or_moments(p, n, f, rho, U, T);
+}
+
+/* ---- full time steps ---- */
+
+/* nsteps steps in place on (x, f, rho, U, T).  rho/U/T hold the moments of the
+ * last transported state (interior) or of f_b (walls) and supply U^n on entry.
+ * Neighbours and stencils are rebuilt every step with ale = 1, once otherwise.
+ * Returns OR_OK or an error code; *clamps accumulates wall-guard clamps. */
+int or_run(const or_params* p, int64_t n, double* x, const int32_t* kind, const double* normal,
+           double* f, double* rho, double* U, double* T, int32_t nsteps, int64_t* clamps) {
+  int dim = p->dim, cap = p->max_nbrs;
+  int64_t row = ncomp_of(dim) * nvel_of(dim, p->nv);
+  int32_t* cnt = (int32_t*)malloc(sizeof(int32_t) * n);
+  int32_t* col = (int32_t*)malloc(sizeof(int32_t) * n * cap);
+  double* coef = (double*)malloc(sizeof(double) * n * cap * dim);
+  double* abar = (double*)malloc(sizeof(double) * n * cap * dim);
+  double* frame = (double*)malloc(sizeof(double) * n * cap * dim * dim);
+  double* recon = (double*)malloc(sizeof(double) * n * cap);
+  double* ft = (double*)malloc(sizeof(double) * n * row);
+  int status = OR_OK;
+  if (!cnt || !col || !coef || !abar || !frame || !recon || !ft) { status = OR_E_NOMEM; goto done; }
+  for (int32_t s = 0; s < nsteps; ++s) {
+    if (s == 0 || p->ale) {
+      if (or_neighbours_cells(dim, n, x, p->h, p->periodic, cap, cnt, col) < 0) { status = OR_E_OVERFLOW; goto done; }
+      if ((status = or_stencils(p, n, x, kind, cnt, col, coef, abar, frame, recon)) != OR_OK) goto done;
+    }
+    or_transport(p, n, kind, cnt, col, abar, frame, U, f, ft);
+    or_relax(p, n, kind, ft, f, rho, U, T);
+    if (!p->periodic)
+      if ((status = or_boundary(p, n, kind, normal, cnt, col, recon, f, rho, U, T)) != OR_OK) goto done;
+    if (p->ale) {
+      int64_t c = or_move(p, n, kind, U, x);
+      if (clamps) *clamps += c;
+    }
+  }
+done:
+  free(cnt); free(col); free(coef); free(abar); free(frame); free(recon); free(ft);
+  return status;
+}
