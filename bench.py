@@ -1,0 +1,333 @@
+"""Benchmark of the per-time-step hot path (point-velocity updates per second).
+
+Default workload: the 2D driven cavity with ALE motion, 201^2 points, 32^2
+velocities in [-6, 6]^2, Kn = 0.1, lid 0.1, f stored in FP32 (the
+configuration the headline metric is quoted on).  One step = one full time
+step: cell lists, neighbour lists and WLS stencils (rebuilt every step under
+ALE), upwind transport + moments + BGK relaxation, diffuse-reflection walls,
+point motion.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own independent cavity (Kn from the sweep
+0.01 / 0.1 / 1 by rank): weak scaling, no data-path collective; the time is
+the max over ranks.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import bgk_inputs as bi  # noqa: E402
+
+METRIC = "point·velocity updates/s, FP32/batched vs plain FP64 GPU at 1e-4 moments"
+UNIT = "updates/s"
+WORKLOAD = "cavity2d_ale_n201_v32_f32"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+# FP32 lane-instructions per (point, neighbour, velocity) of the upwind transport:
+# 2D: two projections c.P_d (2 each), two min(., 0), one add, sk +=, acc_g, acc_h  -> 10
+# 3D: three projections (3 each), three min, two adds, sk +=, acc                  -> 16
+OPS_PER_PAIR = {2: 10, 3: 16}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        d["source"] = "measured"
+        return d
+    return dict(PEAKS_FALLBACK)
+
+
+def _dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except ValueError:
+        return None
+    src = os.path.join(ROOT, "paper_2408_02350_gb300", "csrc", "step.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    r = rec.get(kernel + ":" + workload)
+    if not r or r.get("source_sha") != h:
+        return None
+    return r.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
+    """The FP64 CPU oracle, single-threaded, on a bounded sample of the workload."""
+    import oracle
+    cl = bi.cloud_for(p)
+    sim = oracle.Simulation(p, cl)
+    t0 = time.perf_counter()
+    sim.run(nsteps)
+    dt = time.perf_counter() - t0
+    n = cl["x"].shape[0]
+    upd = n * p["nv"] ** p["dim"] * nsteps
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d full time step(s) of the %d^%d x %d^%d cavity (%d points), FP64, one thread, %.1f s"
+                      % (nsteps, p["n"], p["dim"], p["nv"], p["dim"], n, dt)}
+
+
+def run_reference(args, p: dict) -> None:
+    """Reference arm: the FP64 CPU oracle timed on host cores, each step a bounded sample."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    sample_n = 51
+    q = bi.config(WORKLOAD, n=sample_n)
+    cl = bi.cloud_for(q)
+    sim = oracle.Simulation(q, cl)
+    sim.run(args.warmup)
+    t0 = time.perf_counter()
+    sim.run(args.steps)
+    dt = time.perf_counter() - t0
+    n = cl["x"].shape[0]
+    value = n * q["nv"] ** 2 * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "points": p["n"] ** 2, "velocities": p["nv"] ** 2, "kn": p["kn"],
+                       "ale": True, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: one full FP64 time step of a %d^2-point cavity with the same "
+                                       "32^2 velocity grid, ALE, Kn %.2g (%d points)" % (sample_n, q["kn"], n)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--storage", default=None, choices=[None, "f64", "f32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
+    ap.add_argument("--n", type=int, default=None, help="override points per axis (profiling runs)")
+    args = ap.parse_args()
+    rank, world, local_rank = _dist_env()
+    p = bi.config(args.workload, **({"n": args.n} if args.n else {}))
+    if world > 1:
+        p["kn"] = bi.KN_SWEEP_ALE[rank % len(bi.KN_SWEEP_ALE)] if p.get("ale") else p["kn"]
+    if args.storage:
+        p["storage"] = args.storage
+    if args.impl == "reference":
+        run_reference(args, p)
+        return
+
+    import torch
+    import paper_2408_02350_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    cl = bi.cloud_for(p)
+    n = cl["x"].shape[0]
+    dim, nv = p["dim"], p["nv"]
+    NV = nv ** dim
+    ncomp = 2 if dim == 2 else 1
+    upd_per_step = n * NV
+
+    s = g.Solver([p], [cl])
+    s.set_maxwellian(stream=stream)
+    s.step(args.warmup, stream=stream)
+    s.sync(stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    g.bgk_set_timing(s.ctx, True)
+    launches0 = s.stats()["launches"]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps, stream=stream)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    s.sync(stream)
+    launches = s.stats()["launches"] - launches0
+    kt_ms, kt_n = g.bgk_get_timing(s.ctx, g.K_TRANSPORT)
+    per_kernel = {name: g.bgk_get_timing(s.ctx, k) for name, k in
+                  (("transport", g.K_TRANSPORT), ("walls", g.K_WALLS), ("neighbours", g.K_NBR),
+                   ("stencils", g.K_STENCIL), ("move", g.K_MOVE))}
+    g.bgk_set_timing(s.ctx, False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = upd_per_step * args.steps * world / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    elem = {"f64": 8, "f32": 4, "bf16": 2}[p["storage"]]
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[p["storage"]]
+    f_host = torch.empty((n, ncomp, NV), dtype=tdt, pin_memory=True)
+    g.bgk_get_f(s.ctx, 0, f_host, {"f64": 0, "f32": 1, "bf16": 2}[p["storage"]], stream)
+    mom_host = [torch.empty(n, dtype=torch.float64, pin_memory=True),
+                torch.empty((n, dim), dtype=torch.float64, pin_memory=True),
+                torch.empty(n, dtype=torch.float64, pin_memory=True)]
+    h2d = f_host.numel() * elem
+    d2h = n * (dim + 2) * 8
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.bgk_set_f(s.ctx, 0, f_host, {"f64": 0, "f32": 1, "bf16": 2}[p["storage"]], stream)
+        g.bgk_step(s.ctx, 1, stream)
+        g.bgk_moments(s.ctx, 0, *mom_host, stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    s.sync(stream)
+    e2e_value = upd_per_step * args.e2e_steps * world / e2e_s
+
+    # ---- plain FP64 GPU step on the same workload (the comparison the metric names) ----
+    fp64 = None
+    if p["storage"] != "f64" and not args.no_fp64:
+        q = dict(p, storage="f64")
+        s64 = g.Solver([q], [cl])
+        s64.set_maxwellian(stream=stream)
+        s64.step(2, stream=stream)
+        s64.sync(stream)
+        k64 = 5
+        e0.record(stream)
+        s64.step(k64, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        s64.sync(stream)
+        fp64 = {"value": upd_per_step * k64 / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
+                "ms_per_step": ms64 / k64}
+        s64.close()
+
+    # ---- roofline of the dominant kernel (transport + moments + relaxation) ----
+    peaks = _peaks()
+    rowptr, _ = s.get_neighbours()
+    nnz_interior = int(sum(rowptr[i + 1] - rowptr[i] for i in np.where(cl["kind"] == 0)[0]))
+    kt_avg_s = kt_ms / max(kt_n, 1) * 1e-3
+    instr_per_launch = nnz_interior * NV * OPS_PER_PAIR[dim]
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = N_SM * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tinstr/s
+    achieved = instr_per_launch / kt_avg_s / 1e12
+    bytes_per_update = 2 * ncomp * elem  # read f once, write f^{n+1} once
+    hbm_achieved = bytes_per_update * upd_per_step / kt_avg_s / 1e9
+    traffic = _traffic_record("k_transport", args.workload)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinstr/s",
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock, %s)" % (sm_max, peaks["source"]),
+                "kernel": "k_transport", "avg_launch_ms": kt_avg_s * 1e3,
+                "instr_per_launch": instr_per_launch,
+                "hbm": {"achieved": hbm_achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                        "frac": hbm_achieved / peaks.get("hbm_gbs", 6800.0),
+                        "bytes_per_update": bytes_per_update}}
+    kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in per_kernel.items()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": p["storage"], "data": "synthetic",
+                "config": {"workload": args.workload, "points": n, "velocities": NV, "dim": dim,
+                           "kn": p["kn"], "ale": bool(p["ale"]), "storage": p["storage"],
+                           "l2": "inputs larger than L2 (f %.0f MB per buffer, two buffers)"
+                                 % (n * ncomp * NV * elem / 1e6)},
+                "clocks": clk, "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": args.e2e_steps},
+                "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p, 1)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

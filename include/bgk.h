@@ -1,0 +1,178 @@
+/*
+ * bgk.h -- C ABI of the GB300 library for one time step of the meshfree
+ * Arbitrary-Lagrangian-Eulerian / weighted-least-squares scheme for the BGK
+ * equation (Mariappan, Willems, Boregowda, Tiwari, Klar, arXiv 2408.02350).
+ *
+ * Every call takes plain pointers and sizes.  Conventions for all calls:
+ *  - The return value is a bgk_status.  No call aborts, traps or prints;
+ *    bgk_last_error(ctx) gives a one-line description of the last failure.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that take a stream are asynchronous with respect to the
+ *    host and ordered on that stream, except where noted as synchronous.
+ *  - Device-side failures (neighbour overflow, singular WLS system,
+ *    non-finite moments) are recorded in a device status word and returned by
+ *    the next bgk_sync.
+ *  - The caller owns every pointer it passes.  The context owns all device
+ *    memory it allocates (positions, neighbour lists, stencils, the two
+ *    distribution buffers) and frees it in bgk_free.
+ *  - Units are nondimensional: R = 1, L = 1, rho0 = 1, T0 = 1.
+ *
+ * Layouts:
+ *   x, normal  [n][dim] double, row-major
+ *   kind       [n] int32: 0 interior point, k > 0 wall id
+ *   f          [n][ncomp][NV] with ncomp = 2 (Chu g1, g2) in 2D, 1 in 3D,
+ *              NV = nv^dim, velocity index k = kx + nv*(ky + nv*kz)
+ *   velocity nodes v_j = -vmax + j*dv, dv = 2 vmax / (nv - 1), j = 0..nv-1
+ */
+#ifndef BGK_H
+#define BGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BGK_ABI_VERSION 1
+
+typedef struct bgk_ctx bgk_ctx;
+
+typedef enum bgk_status {
+  BGK_OK = 0,
+  BGK_E_INVAL = 1,         /* bad argument or size */
+  BGK_E_NOMEM = 2,         /* device or host allocation failed */
+  BGK_E_CUDA = 3,          /* a CUDA runtime call failed */
+  BGK_E_SINGULAR = 4,      /* WLS normal matrix not invertible, or a wall point without interior neighbours */
+  BGK_E_NBR_OVERFLOW = 5,  /* a point has more than max_nbrs neighbours */
+  BGK_E_NONFINITE = 6,     /* non-finite or non-positive density or temperature */
+  BGK_E_TIMEOUT = 7,       /* a bounded device wait gave up */
+  BGK_E_STATE = 8          /* call not valid in the context's state */
+} bgk_status;
+
+typedef enum bgk_storage { BGK_F64 = 0, BGK_F32 = 1, BGK_BF16 = 2 } bgk_storage;
+
+typedef enum bgk_tau_mode {
+  BGK_TAU_LOCAL = 0,   /* tau = sqrt(2/pi) Kn / (rho sqrt(T)), Eqs. (tau), (lambda) */
+  BGK_TAU_CONST = 1,   /* tau = sqrt(2/pi) Kn */
+  BGK_TAU_NONE = 2     /* no collisions (free transport) */
+} bgk_tau_mode;
+
+/* Parameters of one problem (Sec. 3 and Sec. 5). */
+typedef struct bgk_params {
+  int32_t dim;       /* 2: Chu-reduced g1, g2 (Sec. 2.1); 3: full f */
+  int32_t nv;        /* velocity nodes per axis (the paper's N_v + 1), >= 2 */
+  double vmax;       /* velocity grid covers [-vmax, vmax]^dim (Sec. 3.3) */
+  double kn;         /* Knudsen number */
+  int32_t tau_mode;  /* bgk_tau_mode */
+  int32_t ale;       /* 1: points move with U and transport uses v - U (Sec. 3.1) */
+  int32_t periodic;  /* 1: periodic unit box (minimum image), no walls */
+  int32_t lid_wall;  /* wall id whose points move with lid_u (diffuse reflection) */
+  int32_t max_nbrs;  /* neighbour-list capacity per point */
+  int32_t storage;   /* bgk_storage of f: F64 computes in double, F32/BF16 in float */
+  double dt;         /* time step */
+  double h;          /* neighbour radius and WLS support (Sec. 3.4.1) */
+  double alpha;      /* Gaussian weight w = exp(-alpha r^2 / h^2), Eq. (weight) */
+  double wall_T;     /* wall temperature */
+  double guard;      /* ALE: interior coordinates are clamped to [guard, 1 - guard] */
+  double lid_u[3];   /* lid velocity */
+} bgk_params;
+
+typedef struct bgk_stats {
+  int64_t steps;          /* time steps taken */
+  int64_t launches;       /* kernels launched by this context since creation */
+  int64_t clamps;         /* ALE wall-guard clamps (valid after bgk_sync) */
+  int64_t nnz;            /* neighbour pairs of the last build (valid after bgk_sync) */
+  int32_t nv_pad;         /* padded velocity stride of the internal f layout */
+  int32_t n_cases;
+} bgk_stats;
+
+/* Library ABI version (BGK_ABI_VERSION). */
+int bgk_version(void);
+
+/* Create a context for n_cases independent problems (Sec. 5; several cavities
+ * of different sizes and parameters may share one context).  p[n_cases],
+ * n_points[n_cases]; x, kind, normal are host arrays concatenated over the
+ * cases.  Copies the geometry to the current CUDA device and allocates every
+ * device buffer.  f is not initialised until bgk_set_maxwellian or bgk_set_f.
+ * Synchronous.  Returns BGK_E_INVAL for an unsupported parameter. */
+int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, const double* x,
+             const int32_t* kind, const double* normal, bgk_ctx** out);
+
+/* f^0 = Maxwellian(rho0, u0[dim], T0) at every point of every case
+ * (Sec. 2.1: g1 = G1, g2 = T0 G1 in 2D), and the stored moments (rho, U, T)
+ * are those of f^0 (the transport of the first step uses their U). */
+int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, void* stream);
+
+/* Copy case c's distribution in or out, layout [n][ncomp][NV] with element
+ * type dtype (bgk_storage), from/to host memory (on_device = 0) or device
+ * memory (on_device = 1).  bgk_set_f also recomputes the stored moments.
+ * Host copies are staged and synchronous; device copies are stream-ordered. */
+int bgk_set_f(bgk_ctx* ctx, int32_t c, const void* f, int32_t dtype, int32_t on_device, void* stream);
+int bgk_get_f(bgk_ctx* ctx, int32_t c, void* f, int32_t dtype, int32_t on_device, void* stream);
+
+/* Rebuild cell lists, neighbour lists N(i) = {j != i : |x_j - x_i|^2 <= h^2}
+ * (ascending j, FP64 without fused multiply-add) and the WLS stencils of
+ * every case from the current positions (Sec. 3.4, Sec. 3.5.1, Sec. 4.2).
+ * bgk_step does this itself: every step when ale = 1, once otherwise. */
+int bgk_neighbours(bgk_ctx* ctx, void* stream);
+
+/* Host copy of case c's neighbour lists as CSR: rowptr[n+1], col[cap].
+ * *nnz receives the pair count; BGK_E_INVAL if cap < nnz.  Synchronous. */
+int bgk_get_neighbours(bgk_ctx* ctx, int32_t c, int64_t* rowptr, int32_t* col, int64_t cap, int64_t* nnz);
+
+/* Host copy of case c's stencils in neighbour-list order (CSR slots):
+ * P[nnz][dim][dim] holds, for interior rows, the projected frame vectors
+ * abar_d e_d (d = n, t[, b]) of Sec. 3.4.2 so that the upwind coefficient is
+ * K = sum_d (c.P_d - |c.P_d|); recon[nnz] holds, for wall rows, the WLS
+ * reconstruction weights (zero for wall neighbours).  Synchronous. */
+int bgk_get_stencils(bgk_ctx* ctx, int32_t c, double* P, double* recon, int64_t cap);
+
+/* Advance every case by nsteps time steps of the first-order splitting of
+ * Sec. 3.2: positive upwind transport f~ = f - dt (v - U^n).grad f (Sec. 3.4.2),
+ * moments of f~ (Eqs. fullmoment1a, moment1a, moment1b), implicit BGK
+ * relaxation f^{n+1} = (tau f~ + dt M^{n+1}) / (tau + dt), diffuse-reflection
+ * walls, and with ale = 1 the motion x^{n+1} = x^n + dt U^{n+1}.  Asynchronous. */
+int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream);
+
+/* Case c's stored moments: rho[n], u[n][dim], T[n] (interior points: moments
+ * of the last transported state; wall points: moments of f_b).  Host
+ * destination (on_device = 0) is synchronous; device destination is
+ * stream-ordered. */
+int bgk_moments(bgk_ctx* ctx, int32_t c, double* rho, double* u, double* T, int32_t on_device, void* stream);
+
+/* Case c's current positions x[n][dim] (host or device destination, as bgk_moments). */
+int bgk_get_positions(bgk_ctx* ctx, int32_t c, double* x, int32_t on_device, void* stream);
+
+/* Wait for the stream and return the first device-side error since the last
+ * bgk_sync (then cleared), or BGK_OK. */
+int bgk_sync(bgk_ctx* ctx, void* stream);
+
+/* Checkpoint: the full state (positions, f, moments, step count) of every
+ * case as one host blob.  bgk_get_state with blob == NULL stores the size
+ * needed in *used.  Both calls are synchronous. */
+int bgk_get_state(bgk_ctx* ctx, void* blob, size_t cap, size_t* used);
+int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size);
+
+/* Per-kernel timing with CUDA events on the launching stream: enable = 1
+ * brackets every launch of the transport kernel with an event pair.
+ * bgk_get_timing synchronises and returns the summed device time (ms) and
+ * launch count of kernel `which` (0 = transport+relaxation, 1 = wall, 2 =
+ * neighbour build, 3 = stencils, 4 = motion) since timing was enabled. */
+int bgk_set_timing(bgk_ctx* ctx, int32_t enable);
+int bgk_get_timing(bgk_ctx* ctx, int32_t which, double* total_ms, int64_t* launches);
+
+int bgk_get_stats(bgk_ctx* ctx, bgk_stats* out);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * bgk_init when ctx is NULL).  The string lives until the next call on ctx. */
+const char* bgk_last_error(const bgk_ctx* ctx);
+
+/* Release the context and all device memory it owns.  NULL is ignored. */
+void bgk_free(bgk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BGK_H */

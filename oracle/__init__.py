@@ -92,6 +92,7 @@ def lib():
                 "or_transport": (None, [_PP, C.c_int64, _PI, _PI, _PI, _PD, _PD, _PD, _PD, _PD]),
                 "or_moments": (None, [_PP, C.c_int64, _PD, _PD, _PD, _PD]),
                 "or_relax": (None, [_PP, C.c_int64, _PI, _PD, _PD, _PD, _PD, _PD]),
+                "or_transport_relax_points": (None, [_PP, C.c_int64, _PL, _PI, _PI, _PD, _PD, _PD, _PD, _PD, _PD]),
                 "or_boundary": (C.c_int, [_PP, C.c_int64, _PI, _PD, _PI, _PI, _PD, _PD, _PD, _PD, _PD]),
                 "or_move": (C.c_int64, [_PP, C.c_int64, _PI, _PD, _PD]),
                 "or_init_maxwellian": (None, [_PP, C.c_int64, C.c_double, _PD, C.c_double, _PD, _PD, _PD, _PD]),
@@ -253,6 +254,19 @@ def relax(p: dict, kind, ft, f, rho, U, T):
     """In place on f, rho, U, T (interior points)."""
     q = params(p)
     lib().or_relax(C.byref(q), ft.shape[0], _i(_i32(kind)), _d(_f64(ft)), _d(f), _d(rho), _d(U), _d(T))
+
+
+def transport_relax_points(p: dict, idx, cnt, col, st: dict, U, f):
+    """f^{n+1} and (rho, U, T) of the listed interior points after one transport + relaxation."""
+    q = params(p)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    f = _f64(f)
+    dim = p["dim"]
+    out = np.empty((len(idx),) + f.shape[1:])
+    mom = np.empty((len(idx), dim + 2))
+    lib().or_transport_relax_points(C.byref(q), len(idx), idx.ctypes.data_as(_PL), _i(_i32(cnt)), _i(_i32(col)),
+                                    _d(_f64(st["abar"])), _d(_f64(st["frame"])), _d(_f64(U)), _d(f), _d(out), _d(mom))
+    return out, mom[:, 0], mom[:, 1:1 + dim], mom[:, 1 + dim]
 
 
 def boundary(p: dict, kind, normal, cnt, col, st: dict, f, rho, U, T) -> int:

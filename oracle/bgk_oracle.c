@@ -467,31 +467,39 @@ static double upwind_coef(int dim, const double* ab, const double* fr, const dou
   return K;
 }
 
-/* ft_i = f_i - dt Q(f)_i for interior i, Q = sum_j K_ij(v - U_i) (f_j - f_i);
- * U enters only with ale = 1.  Wall rows are copied. */
+/* ft_i = f_i - dt Q(f)_i at one interior point i, Q = sum_j K_ij(v - U_i) (f_j - f_i);
+ * U enters only with ale = 1.  vel is the velocity grid [NV][dim]. */
+static void transport_point(const or_params* p, int64_t i, const int32_t* cnt, const int32_t* col,
+                            const double* abar, const double* frame, const double* U, const double* f,
+                            const double* vel, double* fti) {
+  int dim = p->dim, cap = p->max_nbrs, nc = ncomp_of(dim);
+  int64_t NV = nvel_of(dim, p->nv), row = nc * NV;
+  const double* fi = f + i * row;
+  for (int64_t k = 0; k < NV; ++k) {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < dim; ++a) c[a] = vel[k * dim + a] - (p->ale ? U[i * dim + a] : 0.0);
+    double Q[2] = {0.0, 0.0};
+    for (int s = 0; s < cnt[i]; ++s) {
+      int64_t slot = i * cap + s;
+      const double* fj = f + (int64_t)col[slot] * row;
+      double K = upwind_coef(dim, abar + slot * dim, frame + slot * dim * dim, c);
+      for (int q = 0; q < nc; ++q) Q[q] += K * (fj[q * NV + k] - fi[q * NV + k]);
+    }
+    for (int q = 0; q < nc; ++q) fti[q * NV + k] = fi[q * NV + k] - p->dt * Q[q];
+  }
+}
+
+/* Transport at every interior point; wall rows are copied. */
 void or_transport(const or_params* p, int64_t n, const int32_t* kind, const int32_t* cnt,
                   const int32_t* col, const double* abar, const double* frame, const double* U,
                   const double* f, double* ft) {
-  int dim = p->dim, cap = p->max_nbrs, nc = ncomp_of(dim);
-  int64_t NV = nvel_of(dim, p->nv), row = nc * NV;
+  int dim = p->dim;
+  int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
   or_velocity_grid(dim, p->nv, p->vmax, vel);
   for (int64_t i = 0; i < n; ++i) {
-    const double* fi = f + i * row;
-    double* fti = ft + i * row;
-    if (kind[i] != 0) { memcpy(fti, fi, sizeof(double) * row); continue; }
-    for (int64_t k = 0; k < NV; ++k) {
-      double c[3] = {0.0, 0.0, 0.0};
-      for (int a = 0; a < dim; ++a) c[a] = vel[k * dim + a] - (p->ale ? U[i * dim + a] : 0.0);
-      double Q[2] = {0.0, 0.0};
-      for (int s = 0; s < cnt[i]; ++s) {
-        int64_t slot = i * cap + s;
-        const double* fj = f + (int64_t)col[slot] * row;
-        double K = upwind_coef(dim, abar + slot * dim, frame + slot * dim * dim, c);
-        for (int q = 0; q < nc; ++q) Q[q] += K * (fj[q * NV + k] - fi[q * NV + k]);
-      }
-      for (int q = 0; q < nc; ++q) fti[q * NV + k] = fi[q * NV + k] - p->dt * Q[q];
-    }
+    if (kind[i] != 0) { memcpy(ft + i * row, f + i * row, sizeof(double) * row); continue; }
+    transport_point(p, i, cnt, col, abar, frame, U, f, vel, ft + i * row);
   }
   free(vel);
 }
@@ -504,24 +512,48 @@ void or_moments(const or_params* p, int64_t n, const double* f, double* rho, dou
   for (int64_t i = 0; i < n; ++i) or_moments_point(p, f + i * row, rho + i, U + i * dim, T + i);
 }
 
-/* f^{n+1} = (tau ft + dt M^{n+1}) / (tau + dt) at interior points, M^{n+1} from the
- * moments of ft (Eqs. fullmoment1a, moment1a, moment1b).  Writes the moments to rho, U, T. */
+/* f^{n+1} = (tau ft + dt M^{n+1}) / (tau + dt) at one point, M^{n+1} from the moments
+ * of ft (Eqs. fullmoment1a, moment1a, moment1b); the moments go to rho, U[dim], T. */
+static void relax_point(const or_params* p, const double* fti, double* fi, double* M, double* rho,
+                        double* U, double* T) {
+  int64_t row = ncomp_of(p->dim) * nvel_of(p->dim, p->nv);
+  or_moments_point(p, fti, rho, U, T);
+  if (p->tau_mode == 2) { memcpy(fi, fti, sizeof(double) * row); return; }
+  double tau = or_tau(p, *rho, *T);
+  or_maxwellian(p, *rho, U, *T, M);
+  for (int64_t q = 0; q < row; ++q) fi[q] = (tau * fti[q] + p->dt * M[q]) / (tau + p->dt);
+}
+
+/* Relaxation at every interior point; writes the moments of ft to rho, U, T. */
 void or_relax(const or_params* p, int64_t n, const int32_t* kind, const double* ft, double* f,
               double* rho, double* U, double* T) {
   int dim = p->dim;
-  int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
+  int64_t row = ncomp_of(dim) * nvel_of(dim, p->nv);
   double* M = (double*)malloc(sizeof(double) * row);
   for (int64_t i = 0; i < n; ++i) {
     if (kind[i] != 0) continue;
-    const double* fti = ft + i * row;
-    double* fi = f + i * row;
-    or_moments_point(p, fti, rho + i, U + i * dim, T + i);
-    if (p->tau_mode == 2) { memcpy(fi, fti, sizeof(double) * row); continue; }
-    double tau = or_tau(p, rho[i], T[i]);
-    or_maxwellian(p, rho[i], U + i * dim, T[i], M);
-    for (int64_t q = 0; q < row; ++q) fi[q] = (tau * fti[q] + p->dt * M[q]) / (tau + p->dt);
+    relax_point(p, ft + i * row, f + i * row, M, rho + i, U + i * dim, T + i);
   }
   free(M);
+}
+
+/* Transport and relaxation of the listed interior points only (for spot checks of
+ * large clouds): out[nidx][ncomp][NV] = f^{n+1}, mom_out[nidx][dim+2] = (rho, U, T). */
+void or_transport_relax_points(const or_params* p, int64_t nidx, const int64_t* idx, const int32_t* cnt,
+                               const int32_t* col, const double* abar, const double* frame,
+                               const double* U, const double* f, double* out, double* mom_out) {
+  int dim = p->dim;
+  int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
+  double* vel = (double*)malloc(sizeof(double) * NV * dim);
+  double* ft = (double*)malloc(sizeof(double) * row);
+  double* M = (double*)malloc(sizeof(double) * row);
+  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  for (int64_t q = 0; q < nidx; ++q) {
+    double* mo = mom_out + q * (dim + 2);
+    transport_point(p, idx[q], cnt, col, abar, frame, U, f, vel, ft);
+    relax_point(p, ft, out + q * row, M, mo, mo + 1, mo + 1 + dim);
+  }
+  free(vel); free(ft); free(M);
 }
 
 /* ---- diffuse-reflection walls (Sec. 5.1, 5.2; Table 3) ---- */

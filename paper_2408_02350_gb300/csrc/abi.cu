@@ -1,0 +1,639 @@
+// C ABI of libbgk (include/bgk.h): context, buffers, launch order of one time step.
+//
+// One time step of a case (Sec. 3.2, read in the order neighbours/stencils ->
+// transport -> moments -> relaxation -> walls -> motion):
+//   [ale or first step] cell lists, neighbour lists, WLS stencils
+//   k_transport   f[cur] -> f[1-cur] at interior points (transport, moments, relaxation)
+//   k_walls       f[1-cur] at wall points (reconstruction + diffuse reflection)
+//   [ale]         k_move: x += dt U^{n+1}
+// All launches go to the caller's stream; nothing synchronises inside bgk_step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bgk.h"
+#include "bgk_internal.cuh"
+
+using namespace bgk;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct EvPair {
+  cudaEvent_t a, b;
+  int kid;
+};
+
+struct CaseHost {
+  bgk_params p;
+  CaseView cv;
+  void* f[2];
+  int cur;
+  bool stencils_valid;
+  size_t s_bytes, c_bytes;  // storage and compute element sizes
+};
+
+}  // namespace
+
+struct bgk_ctx {
+  std::vector<CaseHost> cases;
+  std::vector<void*> allocs;
+  DevStatus* status = nullptr;
+  std::string err;
+  int64_t steps = 0, launches = 0;
+  bool timing = false;
+  std::vector<EvPair> ev;
+  size_t ev_used = 0;
+  double t_ms[K_COUNT] = {0, 0, 0, 0, 0};
+  int64_t t_n[K_COUNT] = {0, 0, 0, 0, 0};
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+};
+
+namespace {
+
+int fail(bgk_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_init_error = buf;
+  return code;
+}
+
+#define CK(ctx, call)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail((ctx), BGK_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKL(ctx)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess) return fail((ctx), BGK_E_CUDA, "kernel launch: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dalloc(bgk_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = count ? count * sizeof(T) : sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BGK_E_NOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return BGK_OK;
+}
+
+int dalloc_bytes(bgk_ctx* ctx, void** p, size_t bytes) {
+  unsigned char* q = nullptr;
+  int st = dalloc(ctx, &q, bytes);
+  *p = q;
+  return st;
+}
+
+int ensure_staging(bgk_ctx* ctx, size_t bytes) {
+  if (ctx->staging_bytes >= bytes) return BGK_OK;
+  if (ctx->staging) cudaFree(ctx->staging);
+  ctx->staging = nullptr;
+  ctx->staging_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->staging, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BGK_E_NOMEM, "staging cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->staging_bytes = bytes;
+  return BGK_OK;
+}
+
+int check_params(const bgk_params& p, int64_t n, const char** why) {
+  if (p.dim != 2 && p.dim != 3) { *why = "dim must be 2 or 3"; return 0; }
+  if (p.nv < 2 || p.nv > 64) { *why = "nv must be in [2, 64]"; return 0; }
+  int64_t NV = p.dim == 2 ? (int64_t)p.nv * p.nv : (int64_t)p.nv * p.nv * p.nv;
+  if (NV > 8192) { *why = "nv^dim must be <= 8192"; return 0; }
+  if (!(p.vmax > 0) || !(p.dt > 0) || !(p.h > 0) || !(p.alpha > 0) || !(p.wall_T > 0)) {
+    *why = "vmax, dt, h, alpha, wall_T must be positive";
+    return 0;
+  }
+  if (p.tau_mode < 0 || p.tau_mode > 2) { *why = "tau_mode must be 0, 1 or 2"; return 0; }
+  if (p.tau_mode != 2 && !(p.kn > 0)) { *why = "kn must be positive"; return 0; }
+  if (p.storage < 0 || p.storage > 2) { *why = "storage must be 0 (f64), 1 (f32) or 2 (bf16)"; return 0; }
+  if (p.max_nbrs < 1 || p.max_nbrs > 512) { *why = "max_nbrs must be in [1, 512]"; return 0; }
+  if (n < 1 || n > (int64_t)1 << 30) { *why = "point count must be in [1, 2^30]"; return 0; }
+  if (p.guard < 0 || p.guard >= 0.5) { *why = "guard must be in [0, 0.5)"; return 0; }
+  return 1;
+}
+
+void refresh_view(CaseHost& c) {
+  c.cv.f_in = c.f[c.cur];
+  c.cv.f_out = c.f[1 - c.cur];
+}
+
+int timed_begin(bgk_ctx* ctx, int kid, cudaStream_t s, EvPair** out) {
+  *out = nullptr;
+  if (!ctx->timing) return BGK_OK;
+  if (ctx->ev_used == ctx->ev.size()) {
+    EvPair e;
+    CK(ctx, cudaEventCreate(&e.a));
+    CK(ctx, cudaEventCreate(&e.b));
+    e.kid = kid;
+    ctx->ev.push_back(e);
+  }
+  EvPair* e = &ctx->ev[ctx->ev_used++];
+  e->kid = kid;
+  CK(ctx, cudaEventRecord(e->a, s));
+  *out = e;
+  return BGK_OK;
+}
+
+int timed_end(bgk_ctx* ctx, EvPair* e, cudaStream_t s) {
+  if (e) CK(ctx, cudaEventRecord(e->b, s));
+  return BGK_OK;
+}
+
+int collect_timing(bgk_ctx* ctx) {
+  for (size_t q = 0; q < ctx->ev_used; ++q) {
+    EvPair& e = ctx->ev[q];
+    CK(ctx, cudaEventSynchronize(e.b));
+    float ms = 0.0f;
+    CK(ctx, cudaEventElapsedTime(&ms, e.a, e.b));
+    ctx->t_ms[e.kid] += ms;
+    ctx->t_n[e.kid] += 1;
+  }
+  ctx->ev_used = 0;
+  return BGK_OK;
+}
+
+int build_lists(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+  EvPair* e;
+  int st;
+  CK(ctx, cudaMemsetAsync(&ctx->status->nnz, 0, sizeof(unsigned long long), s));
+  if ((st = timed_begin(ctx, K_NBR, s, &e))) return st;
+  ctx->launches += launch_neighbours(c.cv, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  if ((st = timed_begin(ctx, K_STENCIL, s, &e))) return st;
+  ctx->launches += launch_stencils(c.cv, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  c.stencils_valid = true;
+  return BGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bgk_version(void) { return BGK_ABI_VERSION; }
+
+int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, const double* x,
+             const int32_t* kind, const double* normal, bgk_ctx** out) {
+  if (!out) return fail(nullptr, BGK_E_INVAL, "bgk_init: out is NULL");
+  *out = nullptr;
+  if (!p || !n_points || !x || !kind || !normal || n_cases < 1)
+    return fail(nullptr, BGK_E_INVAL, "bgk_init: NULL argument or n_cases < 1");
+  for (int c = 0; c < n_cases; ++c) {
+    const char* why = nullptr;
+    if (!check_params(p[c], n_points[c], &why)) return fail(nullptr, BGK_E_INVAL, "bgk_init: case %d: %s", c, why);
+  }
+  bgk_ctx* ctx = new (std::nothrow) bgk_ctx();
+  if (!ctx) return fail(nullptr, BGK_E_NOMEM, "bgk_init: host allocation failed");
+  int st = BGK_OK;
+  auto bail = [&](int code) {
+    g_init_error = ctx->err;
+    bgk_free(ctx);
+    return code;
+  };
+  if ((st = dalloc(ctx, &ctx->status, 1))) return bail(st);
+  if (cudaMemset(ctx->status, 0, sizeof(DevStatus)) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset status"));
+  int64_t off = 0;
+  ctx->cases.resize(n_cases);
+  for (int ci = 0; ci < n_cases; ++ci) {
+    CaseHost& c = ctx->cases[ci];
+    const bgk_params& q = p[ci];
+    const int64_t n = n_points[ci];
+    const int dim = q.dim;
+    c.p = q;
+    c.cur = 0;
+    c.stencils_valid = false;
+    CaseView& v = c.cv;
+    memset(&v, 0, sizeof(v));
+    v.dim = dim;
+    v.nv = q.nv;
+    v.NV = dim == 2 ? q.nv * q.nv : q.nv * q.nv * q.nv;
+    v.NVp = (v.NV + 3) / 4 * 4;
+    v.ncomp = dim == 2 ? 2 : 1;
+    v.cap = q.max_nbrs;
+    v.n = (int32_t)n;
+    v.ale = q.ale;
+    v.periodic = q.periodic;
+    v.tau_mode = q.tau_mode;
+    v.lid_wall = q.lid_wall;
+    v.storage = q.storage;
+    v.dt = q.dt;
+    v.h = q.h;
+    v.alpha = q.alpha;
+    v.kn = q.kn;
+    v.wall_T = q.wall_T;
+    v.guard = q.guard;
+    v.dv = 2.0 * q.vmax / (double)(q.nv - 1);
+    for (int a = 0; a < 3; ++a) v.lid_u[a] = q.lid_u[a];
+    v.nc = (int)std::floor(1.0 / (q.h * (1.0 + 1e-9)));
+    if (v.nc < 1) v.nc = 1;
+    if (v.nc > 4096) v.nc = 4096;
+    int64_t ncell = 1;
+    for (int a = 0; a < dim; ++a) ncell *= v.nc;
+    if (ncell > (int64_t)1 << 26) return bail(fail(ctx, BGK_E_INVAL, "case %d: too many cells (h too small)", ci));
+    v.ncell = (int32_t)ncell;
+    c.s_bytes = q.storage == 0 ? 8 : (q.storage == 1 ? 4 : 2);
+    c.c_bytes = q.storage == 0 ? 8 : 4;
+
+    // interior / wall partition of the input (ascending index)
+    std::vector<int32_t> inner, wall;
+    for (int64_t i = 0; i < n; ++i) {
+      if (kind[off + i] == 0) inner.push_back((int32_t)i);
+      else wall.push_back((int32_t)i);
+    }
+    if (q.periodic && !wall.empty()) return bail(fail(ctx, BGK_E_INVAL, "case %d: periodic box with wall points", ci));
+    v.n_int = (int32_t)inner.size();
+    v.n_wall = (int32_t)wall.size();
+
+    double* dx = nullptr;
+    int32_t *dkind = nullptr, *dint = nullptr, *dwall = nullptr;
+    double* dnorm = nullptr;
+    if ((st = dalloc(ctx, &dx, n * dim))) return bail(st);
+    if ((st = dalloc(ctx, &dkind, n))) return bail(st);
+    if ((st = dalloc(ctx, &dnorm, n * dim))) return bail(st);
+    if ((st = dalloc(ctx, &dint, inner.size()))) return bail(st);
+    if ((st = dalloc(ctx, &dwall, wall.size()))) return bail(st);
+    if (cudaMemcpy(dx, x + off * dim, sizeof(double) * n * dim, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dkind, kind + off, sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dnorm, normal + off * dim, sizeof(double) * n * dim, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (inner.size() && cudaMemcpy(dint, inner.data(), sizeof(int32_t) * inner.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (wall.size() && cudaMemcpy(dwall, wall.data(), sizeof(int32_t) * wall.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+      return bail(fail(ctx, BGK_E_CUDA, "case %d: geometry upload failed", ci));
+    v.x = dx;
+    v.kind = dkind;
+    v.normal = dnorm;
+    v.int_idx = dint;
+    v.wall_idx = dwall;
+
+    if ((st = dalloc(ctx, &v.vnodes, q.nv))) return bail(st);
+    if ((st = dalloc(ctx, &v.xf, n * dim))) return bail(st);
+    if ((st = dalloc(ctx, &v.cell_of, n))) return bail(st);
+    if ((st = dalloc(ctx, &v.cell_start, ncell + 1))) return bail(st);
+    if ((st = dalloc(ctx, &v.cell_cnt, ncell))) return bail(st);
+    if ((st = dalloc(ctx, &v.cell_pts, n))) return bail(st);
+    if ((st = dalloc(ctx, &v.cnt, n))) return bail(st);
+    if ((st = dalloc(ctx, &v.col, n * v.cap))) return bail(st);
+    if ((st = dalloc_bytes(ctx, &v.P, (size_t)n * v.cap * dim * dim * c.c_bytes))) return bail(st);
+    if ((st = dalloc_bytes(ctx, &v.recon, (size_t)n * v.cap * c.c_bytes))) return bail(st);
+    if ((st = dalloc(ctx, &v.wcls, (size_t)v.n_wall * v.NVp))) return bail(st);
+    if ((st = dalloc_bytes(ctx, &v.wvn, (size_t)v.n_wall * v.NVp * c.c_bytes))) return bail(st);
+    if ((st = dalloc(ctx, &v.winv, v.n_wall))) return bail(st);
+    if ((st = dalloc_bytes(ctx, &v.mw, (size_t)2 * v.NVp * c.c_bytes))) return bail(st);
+    const size_t fbytes = (size_t)n * v.ncomp * v.NVp * c.s_bytes;
+    for (int b = 0; b < 2; ++b) {
+      if ((st = dalloc_bytes(ctx, &c.f[b], fbytes))) return bail(st);
+      if (cudaMemset(c.f[b], 0, fbytes) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset f"));
+    }
+    if ((st = dalloc(ctx, &v.mom, (size_t)n * MOM_STRIDE))) return bail(st);
+    if (cudaMemset(v.mom, 0, sizeof(double) * n * MOM_STRIDE) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset mom"));
+    v.status = ctx->status;
+    refresh_view(c);
+    ctx->launches += launch_init_tables(v, 0);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+      return bail(fail(ctx, BGK_E_CUDA, "case %d: table initialisation failed", ci));
+    off += n;
+  }
+  DevStatus hs;
+  if (cudaMemcpy(&hs, ctx->status, sizeof(hs), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bail(fail(ctx, BGK_E_CUDA, "status read failed"));
+  if (hs.flags & ST_SINGULAR) return bail(fail(ctx, BGK_E_SINGULAR, "a wall point has no leaving velocity with positive flux"));
+  *out = ctx;
+  return BGK_OK;
+}
+
+int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, void* stream) {
+  if (!ctx || !u0) return BGK_E_INVAL;
+  if (!(rho0 > 0) || !(T0 > 0)) return fail(ctx, BGK_E_INVAL, "bgk_set_maxwellian: rho0 and T0 must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& c : ctx->cases) {
+    refresh_view(c);
+    ctx->launches += launch_set_maxwellian(c.cv, rho0, u0, T0, s);
+    ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
+    CKL(ctx);
+  }
+  return BGK_OK;
+}
+
+int bgk_set_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype, int32_t on_device, void* stream) {
+  if (!ctx || !f || ci < 0 || ci >= (int)ctx->cases.size() || dtype < 0 || dtype > 2)
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_set_f: bad argument") : BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CaseHost& c = ctx->cases[ci];
+  refresh_view(c);
+  const size_t esz = dtype == 0 ? 8 : (dtype == 1 ? 4 : 2);
+  const size_t bytes = (size_t)c.cv.n * c.cv.ncomp * c.cv.NV * esz;
+  const void* src = f;
+  if (!on_device) {
+    int st = ensure_staging(ctx, bytes);
+    if (st) return st;
+    CK(ctx, cudaMemcpyAsync(ctx->staging, f, bytes, cudaMemcpyHostToDevice, s));
+    src = ctx->staging;
+  }
+  ctx->launches += launch_pack_f(c.cv, src, dtype, c.f[c.cur], s);
+  ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
+  CKL(ctx);
+  if (!on_device) CK(ctx, cudaStreamSynchronize(s));
+  return BGK_OK;
+}
+
+int bgk_get_f(bgk_ctx* ctx, int32_t ci, void* f, int32_t dtype, int32_t on_device, void* stream) {
+  if (!ctx || !f || ci < 0 || ci >= (int)ctx->cases.size() || dtype < 0 || dtype > 2)
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_get_f: bad argument") : BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CaseHost& c = ctx->cases[ci];
+  refresh_view(c);
+  const size_t esz = dtype == 0 ? 8 : (dtype == 1 ? 4 : 2);
+  const size_t bytes = (size_t)c.cv.n * c.cv.ncomp * c.cv.NV * esz;
+  if (on_device) {
+    ctx->launches += launch_unpack_f(c.cv, c.f[c.cur], f, dtype, s);
+    CKL(ctx);
+    return BGK_OK;
+  }
+  int st = ensure_staging(ctx, bytes);
+  if (st) return st;
+  ctx->launches += launch_unpack_f(c.cv, c.f[c.cur], ctx->staging, dtype, s);
+  CKL(ctx);
+  CK(ctx, cudaMemcpyAsync(f, ctx->staging, bytes, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  return BGK_OK;
+}
+
+int bgk_neighbours(bgk_ctx* ctx, void* stream) {
+  if (!ctx) return BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& c : ctx->cases) {
+    refresh_view(c);
+    int st = build_lists(ctx, c, s);
+    if (st) return st;
+  }
+  return BGK_OK;
+}
+
+int bgk_get_neighbours(bgk_ctx* ctx, int32_t ci, int64_t* rowptr, int32_t* col, int64_t cap, int64_t* nnz) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !rowptr || !nnz)
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_get_neighbours: bad argument") : BGK_E_INVAL;
+  CaseHost& c = ctx->cases[ci];
+  CK(ctx, cudaDeviceSynchronize());
+  const int n = c.cv.n, K = c.cv.cap;
+  std::vector<int32_t> cnt(n), ell((size_t)n * K);
+  CK(ctx, cudaMemcpy(cnt.data(), c.cv.cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  CK(ctx, cudaMemcpy(ell.data(), c.cv.col, sizeof(int32_t) * ell.size(), cudaMemcpyDeviceToHost));
+  int64_t z = 0;
+  rowptr[0] = 0;
+  for (int i = 0; i < n; ++i) { z += cnt[i]; rowptr[i + 1] = z; }
+  *nnz = z;
+  if (!col) return BGK_OK;
+  if (cap < z) return fail(ctx, BGK_E_INVAL, "bgk_get_neighbours: cap %lld < nnz %lld", (long long)cap, (long long)z);
+  for (int i = 0; i < n; ++i) memcpy(col + rowptr[i], ell.data() + (size_t)i * K, sizeof(int32_t) * cnt[i]);
+  return BGK_OK;
+}
+
+int bgk_get_stencils(bgk_ctx* ctx, int32_t ci, double* P, double* recon, int64_t cap) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !P || !recon)
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_get_stencils: bad argument") : BGK_E_INVAL;
+  CaseHost& c = ctx->cases[ci];
+  CK(ctx, cudaDeviceSynchronize());
+  const int n = c.cv.n, dd = c.cv.dim * c.cv.dim;
+  std::vector<int32_t> cnt(n);
+  CK(ctx, cudaMemcpy(cnt.data(), c.cv.cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> rp(n + 1, 0);
+  for (int i = 0; i < n; ++i) rp[i + 1] = rp[i] + cnt[i];
+  const int64_t z = rp[n];
+  if (cap < z) return fail(ctx, BGK_E_INVAL, "bgk_get_stencils: cap %lld < nnz %lld", (long long)cap, (long long)z);
+  int64_t* drp = nullptr;
+  double *dP = nullptr, *dR = nullptr;
+  CK(ctx, cudaMalloc(&drp, sizeof(int64_t) * (n + 1)));
+  CK(ctx, cudaMalloc(&dP, sizeof(double) * std::max<int64_t>(z, 1) * dd));
+  CK(ctx, cudaMalloc(&dR, sizeof(double) * std::max<int64_t>(z, 1)));
+  cudaMemcpy(drp, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+  ctx->launches += launch_stencils_csr(c.cv, drp, dP, dR, 0);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(P, dP, sizeof(double) * z * dd, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(recon, dR, sizeof(double) * z, cudaMemcpyDeviceToHost);
+  cudaFree(drp);
+  cudaFree(dP);
+  cudaFree(dR);
+  if (e != cudaSuccess) return fail(ctx, BGK_E_CUDA, "bgk_get_stencils: %s", cudaGetErrorString(e));
+  return BGK_OK;
+}
+
+int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
+  if (!ctx || nsteps < 0) return ctx ? fail(ctx, BGK_E_INVAL, "bgk_step: nsteps < 0") : BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  EvPair* e;
+  for (int step = 0; step < nsteps; ++step) {
+    for (auto& c : ctx->cases) {
+      refresh_view(c);
+      if (c.cv.ale || !c.stencils_valid)
+        if ((st = build_lists(ctx, c, s))) return st;
+      if ((st = timed_begin(ctx, K_TRANSPORT, s, &e))) return st;
+      ctx->launches += launch_transport(c.cv, s);
+      CKL(ctx);
+      if ((st = timed_end(ctx, e, s))) return st;
+      if ((st = timed_begin(ctx, K_WALLS, s, &e))) return st;
+      ctx->launches += launch_walls(c.cv, s);
+      CKL(ctx);
+      if ((st = timed_end(ctx, e, s))) return st;
+      if (c.cv.ale) {
+        if ((st = timed_begin(ctx, K_MOVE, s, &e))) return st;
+        ctx->launches += launch_move(c.cv, s);
+        CKL(ctx);
+        if ((st = timed_end(ctx, e, s))) return st;
+      }
+      c.cur = 1 - c.cur;
+      refresh_view(c);
+    }
+    ctx->steps += 1;
+  }
+  return BGK_OK;
+}
+
+int bgk_moments(bgk_ctx* ctx, int32_t ci, double* rho, double* u, double* T, int32_t on_device, void* stream) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size())
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_moments: bad argument") : BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CaseHost& c = ctx->cases[ci];
+  const size_t n = c.cv.n, sp = sizeof(double) * MOM_STRIDE;
+  if (rho) CK(ctx, cudaMemcpy2DAsync(rho, sizeof(double), c.cv.mom, sp, sizeof(double), n, cudaMemcpyDefault, s));
+  if (u)
+    for (int a = 0; a < c.cv.dim; ++a)
+      CK(ctx, cudaMemcpy2DAsync(u + a, sizeof(double) * c.cv.dim, c.cv.mom + 1 + a, sp, sizeof(double), n, cudaMemcpyDefault, s));
+  if (T) CK(ctx, cudaMemcpy2DAsync(T, sizeof(double), c.cv.mom + 4, sp, sizeof(double), n, cudaMemcpyDefault, s));
+  if (!on_device) CK(ctx, cudaStreamSynchronize(s));
+  return BGK_OK;
+}
+
+int bgk_get_positions(bgk_ctx* ctx, int32_t ci, double* x, int32_t on_device, void* stream) {
+  if (!ctx || !x || ci < 0 || ci >= (int)ctx->cases.size())
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_get_positions: bad argument") : BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CaseHost& c = ctx->cases[ci];
+  CK(ctx, cudaMemcpyAsync(x, c.cv.x, sizeof(double) * c.cv.n * c.cv.dim, cudaMemcpyDefault, s));
+  if (!on_device) CK(ctx, cudaStreamSynchronize(s));
+  return BGK_OK;
+}
+
+int bgk_sync(bgk_ctx* ctx, void* stream) {
+  if (!ctx) return BGK_E_INVAL;
+  CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  CK(ctx, cudaGetLastError());
+  DevStatus hs;
+  CK(ctx, cudaMemcpy(&hs, ctx->status, sizeof(hs), cudaMemcpyDeviceToHost));
+  if (hs.flags) {
+    CK(ctx, cudaMemset(&ctx->status->flags, 0, sizeof(int32_t)));
+    if (hs.flags & ST_OVERFLOW) return fail(ctx, BGK_E_NBR_OVERFLOW, "a point has more than max_nbrs neighbours");
+    if (hs.flags & ST_SINGULAR) return fail(ctx, BGK_E_SINGULAR, "singular WLS system (too few or degenerate neighbours)");
+    if (hs.flags & ST_NONFINITE) return fail(ctx, BGK_E_NONFINITE, "non-finite or non-positive density or temperature");
+    if (hs.flags & ST_TIMEOUT) return fail(ctx, BGK_E_TIMEOUT, "a bounded device wait gave up");
+  }
+  return BGK_OK;
+}
+
+static const uint64_t kMagic = 0x31544154534b4742ull;  // "BGKSTAT1"
+
+int bgk_get_state(bgk_ctx* ctx, void* blob, size_t cap, size_t* used) {
+  if (!ctx || !used) return BGK_E_INVAL;
+  size_t need = 4 * sizeof(uint64_t);
+  for (auto& c : ctx->cases)
+    need += 4 * sizeof(int64_t) + sizeof(double) * c.cv.n * c.cv.dim +
+            (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes + sizeof(double) * c.cv.n * MOM_STRIDE;
+  *used = need;
+  if (!blob) return BGK_OK;
+  if (cap < need) return fail(ctx, BGK_E_INVAL, "bgk_get_state: cap %zu < %zu", cap, need);
+  CK(ctx, cudaDeviceSynchronize());
+  unsigned char* o = static_cast<unsigned char*>(blob);
+  uint64_t hdr[4] = {kMagic, (uint64_t)BGK_ABI_VERSION, (uint64_t)ctx->cases.size(), (uint64_t)ctx->steps};
+  memcpy(o, hdr, sizeof(hdr));
+  o += sizeof(hdr);
+  for (auto& c : ctx->cases) {
+    int64_t ch[4] = {c.cv.n, c.cv.dim, c.cv.NVp, c.p.storage};
+    memcpy(o, ch, sizeof(ch));
+    o += sizeof(ch);
+    size_t b = sizeof(double) * c.cv.n * c.cv.dim;
+    CK(ctx, cudaMemcpy(o, c.cv.x, b, cudaMemcpyDeviceToHost));
+    o += b;
+    b = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
+    CK(ctx, cudaMemcpy(o, c.f[c.cur], b, cudaMemcpyDeviceToHost));
+    o += b;
+    b = sizeof(double) * c.cv.n * MOM_STRIDE;
+    CK(ctx, cudaMemcpy(o, c.cv.mom, b, cudaMemcpyDeviceToHost));
+    o += b;
+  }
+  return BGK_OK;
+}
+
+int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
+  if (!ctx || !blob) return BGK_E_INVAL;
+  size_t need = 0;
+  bgk_get_state(ctx, nullptr, 0, &need);
+  if (size != need) return fail(ctx, BGK_E_STATE, "bgk_set_state: blob size %zu != %zu", size, need);
+  const unsigned char* o = static_cast<const unsigned char*>(blob);
+  uint64_t hdr[4];
+  memcpy(hdr, o, sizeof(hdr));
+  o += sizeof(hdr);
+  if (hdr[0] != kMagic || hdr[1] != (uint64_t)BGK_ABI_VERSION || hdr[2] != ctx->cases.size())
+    return fail(ctx, BGK_E_STATE, "bgk_set_state: blob does not match this context");
+  CK(ctx, cudaDeviceSynchronize());
+  for (auto& c : ctx->cases) {
+    int64_t ch[4];
+    memcpy(ch, o, sizeof(ch));
+    o += sizeof(ch);
+    if (ch[0] != c.cv.n || ch[1] != c.cv.dim || ch[2] != c.cv.NVp || ch[3] != c.p.storage)
+      return fail(ctx, BGK_E_STATE, "bgk_set_state: case layout mismatch");
+    size_t b = sizeof(double) * c.cv.n * c.cv.dim;
+    CK(ctx, cudaMemcpy(c.cv.x, o, b, cudaMemcpyHostToDevice));
+    o += b;
+    b = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
+    CK(ctx, cudaMemcpy(c.f[c.cur], o, b, cudaMemcpyHostToDevice));
+    o += b;
+    b = sizeof(double) * c.cv.n * MOM_STRIDE;
+    CK(ctx, cudaMemcpy(c.cv.mom, o, b, cudaMemcpyHostToDevice));
+    o += b;
+    c.stencils_valid = false;
+  }
+  ctx->steps = (int64_t)hdr[3];
+  return BGK_OK;
+}
+
+int bgk_set_timing(bgk_ctx* ctx, int32_t enable) {
+  if (!ctx) return BGK_E_INVAL;
+  int st = collect_timing(ctx);
+  if (st) return st;
+  ctx->timing = enable != 0;
+  // pre-create event pairs so that timed regions do not pay for cudaEventCreate
+  while (ctx->timing && ctx->ev.size() < 4096) {
+    EvPair e;
+    CK(ctx, cudaEventCreate(&e.a));
+    CK(ctx, cudaEventCreate(&e.b));
+    e.kid = 0;
+    ctx->ev.push_back(e);
+  }
+  for (int k = 0; k < K_COUNT; ++k) { ctx->t_ms[k] = 0.0; ctx->t_n[k] = 0; }
+  return BGK_OK;
+}
+
+int bgk_get_timing(bgk_ctx* ctx, int32_t which, double* total_ms, int64_t* launches) {
+  if (!ctx || which < 0 || which >= K_COUNT || !total_ms || !launches) return BGK_E_INVAL;
+  int st = collect_timing(ctx);
+  if (st) return st;
+  *total_ms = ctx->t_ms[which];
+  *launches = ctx->t_n[which];
+  return BGK_OK;
+}
+
+int bgk_get_stats(bgk_ctx* ctx, bgk_stats* out) {
+  if (!ctx || !out) return BGK_E_INVAL;
+  DevStatus hs;
+  memset(&hs, 0, sizeof(hs));
+  cudaMemcpy(&hs, ctx->status, sizeof(hs), cudaMemcpyDeviceToHost);
+  out->steps = ctx->steps;
+  out->launches = ctx->launches;
+  out->clamps = (int64_t)hs.clamps;
+  out->nnz = (int64_t)hs.nnz;
+  out->nv_pad = ctx->cases.empty() ? 0 : ctx->cases[0].cv.NVp;
+  out->n_cases = (int32_t)ctx->cases.size();
+  return BGK_OK;
+}
+
+const char* bgk_last_error(const bgk_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+void bgk_free(bgk_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  for (auto& e : ctx->ev) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->staging) cudaFree(ctx->staging);
+  delete ctx;
+}
+
+}  // extern "C"

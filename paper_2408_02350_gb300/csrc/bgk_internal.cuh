@@ -1,0 +1,85 @@
+// Internal declarations shared by the CUDA translation units of libbgk.
+// Device data of one problem ("case") and the host-side launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace bgk {
+
+// Device status bits (reported by bgk_sync).
+enum : int32_t { ST_OVERFLOW = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
+
+struct DevStatus {
+  int32_t flags;
+  int32_t pad;
+  unsigned long long clamps;
+  unsigned long long nnz;
+};
+
+// Moments are stored per point as MOM_STRIDE doubles: rho, U[3], T.
+constexpr int MOM_STRIDE = 5;
+
+// Everything a kernel needs about one case, passed by value.  All pointers are
+// device pointers owned by the context.
+struct CaseView {
+  int32_t dim, nv, NV, NVp, ncomp, cap;
+  int32_t n, n_int, n_wall;
+  int32_t ale, periodic, tau_mode, lid_wall, storage;
+  int32_t nc, ncell;  // cells per axis, total cells
+  double dt, h, alpha, kn, wall_T, guard, dv;
+  double lid_u[3];
+
+  double* vnodes;          // [nv] velocity nodes (FP64)
+  double* x;               // [n][dim]
+  const int32_t* kind;     // [n]
+  const double* normal;    // [n][dim]
+  const int32_t* int_idx;  // [n_int] interior point indices, ascending
+  const int32_t* wall_idx; // [n_wall] wall point indices, ascending
+
+  float* xf;            // [n][dim] FP32 copy of x (neighbour-search prefilter)
+  int32_t* cell_of;     // [n]
+  int32_t* cell_start;  // [ncell + 1]
+  int32_t* cell_cnt;    // [ncell]
+  int32_t* cell_pts;    // [n]
+
+  int32_t* cnt;  // [n]
+  int32_t* col;  // [n][cap]
+  void* P;       // [n][cap][dim*dim] projected frame vectors, compute type
+  void* recon;   // [n][cap] wall reconstruction weights, compute type
+
+  // wall tables (fixed walls): per wall slot w = 0..n_wall-1
+  int8_t* wcls;    // [n_wall][NVp] 1 leaving (v.n > 0), 0 arriving
+  void* wvn;       // [n_wall][NVp] |v.n|, compute type
+  double* winv;    // [n_wall] 1 / sum_{v.n>0} (v.n) M_w(v)
+  void* mw;        // [2][NVp] wall Maxwellian G1 (or M) with rho = 1: [0] wall at rest, [1] lid
+
+  void* f_in;    // [n][ncomp][NVp] storage type
+  void* f_out;   // [n][ncomp][NVp] storage type
+  double* mom;   // [n][MOM_STRIDE]
+  DevStatus* status;
+};
+
+// Launchers (stream-ordered; each returns the number of kernels launched).
+int launch_init_tables(const CaseView& cv, cudaStream_t s);
+int launch_neighbours(const CaseView& cv, cudaStream_t s);
+int launch_stencils(const CaseView& cv, cudaStream_t s);
+int launch_transport(const CaseView& cv, cudaStream_t s);
+int launch_walls(const CaseView& cv, cudaStream_t s);
+int launch_move(const CaseView& cv, cudaStream_t s);
+int launch_set_maxwellian(const CaseView& cv, double rho0, const double* u0, double T0, cudaStream_t s);
+int launch_moments(const CaseView& cv, const void* f, cudaStream_t s);
+// Convert between a dense user layout [n][ncomp][NV] of type src_dtype and the
+// internal padded storage [n][ncomp][NVp].
+int launch_pack_f(const CaseView& cv, const void* src, int src_dtype, void* dst, cudaStream_t s);
+int launch_unpack_f(const CaseView& cv, const void* src, void* dst, int dst_dtype, cudaStream_t s);
+// Stencils of every neighbour slot in CSR order, converted to double (device
+// destination arrays P[nnz][dim*dim], recon[nnz]; rowptr[n+1] on the device).
+int launch_stencils_csr(const CaseView& cv, const int64_t* rowptr, double* P, double* recon, cudaStream_t s);
+
+// Kernel ids for timing.
+enum KernelId { K_TRANSPORT = 0, K_WALLS = 1, K_NBR = 2, K_STENCIL = 3, K_MOVE = 4, K_COUNT = 5 };
+
+}  // namespace bgk

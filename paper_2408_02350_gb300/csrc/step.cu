@@ -1,0 +1,709 @@
+// Per-step kernels of the meshfree BGK scheme (Sec. 3.2, 3.4.2, 5).
+//
+// k_transport: one CTA per interior point i; each thread owns NCH chunks of 4
+//   consecutive velocities.  The neighbour list and stencil of i are staged
+//   in shared memory; for every neighbour j the thread reads f_j for its
+//   velocities (16-byte loads, a warp reads 512 contiguous bytes per chunk)
+//   and accumulates
+//     m_ij(v) = sum_d min(c.P_d, 0),  acc += m_ij f_j,  sk += m_ij,
+//   with c = v - U_i^n (ALE) or v.  Since the upwind coefficient is
+//   K_ij = sum_d (c.P_d - |c.P_d|) = 2 m_ij, the transported value is
+//     f~_i = f_i - dt sum_j K_ij (f_j - f_i) = f_i - 2 dt (acc - sk f_i).
+//   The same CTA then sums the moments of f~_i over all velocities (warp
+//   shuffles, cross-warp totals in double by one thread), forms rho, U, T,
+//   tau and the Maxwellian, and writes f^{n+1} = (tau f~ + dt M)/(tau + dt)
+//   to the other buffer: one read of f_i, neighbour reads served mostly from
+//   L2, one write of f_i^{n+1}.
+// k_walls: one CTA per wall point; arriving velocities (v.n <= 0) get the WLS
+//   reconstruction from interior f^{n+1}; leaving velocities get
+//   rho_w M_w(v) with rho_w from zero net mass flux.
+// k_move: x += dt U^{n+1} at interior points (FP64, no fused multiply-add).
+#include "bgk_internal.cuh"
+#include "device_common.cuh"
+
+namespace bgk {
+
+static inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
+__host__ __device__ static inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+constexpr int RED_BYTES = 32 * 8 * 8;   // block-reduction scratch: 8 values x 32 warps, double
+constexpr int NODE_BYTES = 64 * 8;      // velocity nodes, up to 64 per axis
+
+// Finalise the moments from raw sums R = sum g, Mx = sum v g, E = sum |v|^2 g (+ sum h)
+// (quadrature weight dv^dim applied to rho only; it cancels in U and T).
+template <int DIM>
+__device__ __forceinline__ void finish_moments(const double* tot, double wv, double* rho, double* U, double* T) {
+  const double R = tot[0];
+  double u2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { U[a] = tot[1 + a] / R; u2 += U[a] * U[a]; }
+  *T = (tot[DIM + 1] - R * u2) / (3.0 * R);
+  *rho = R * wv;
+}
+
+template <typename C>
+__device__ __forceinline__ C expc(C x);
+template <> __device__ __forceinline__ float expc<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double expc<double>(double x) { return exp(x); }
+
+template <typename C> __device__ __forceinline__ C minc(C a, C b);
+template <> __device__ __forceinline__ float minc<float>(float a, float b) { return fminf(a, b); }
+template <> __device__ __forceinline__ double minc<double>(double a, double b) { return fmin(a, b); }
+
+// Sum NVAL per-thread values: warp shuffles in T, then thread 0 adds the warp
+// totals in double.  Result in out[] of every thread.
+template <int NVAL, typename T>
+__device__ __forceinline__ void block_sum0(const T (&v)[NVAL], double (&out)[NVAL], double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NVAL; ++q) {
+    T s = warp_sum(v[q]);
+    if (lane == 0) scratch[q * 32 + warp] = (double)s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NVAL; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nwarps; ++w) s += scratch[q * 32 + w];
+      scratch[q * 32] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NVAL; ++q) out[q] = scratch[q * 32];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// transport + moments + relaxation
+// ---------------------------------------------------------------------------
+template <typename S, typename C, int DIM, int NCH, bool ALE>
+__global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int DD = DIM * DIM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* s_red = reinterpret_cast<double*>(smem);
+  C* s_v = reinterpret_cast<C*>(smem + RED_BYTES);
+  int32_t* s_col = reinterpret_cast<int32_t*>(smem + RED_BYTES + NODE_BYTES);
+  C* s_P = reinterpret_cast<C*>(smem + RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * cv.cap));
+
+  const int i = cv.int_idx[blockIdx.x];
+  const int m = cv.cnt[i];
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const int nchunk = NVp >> 2;
+  {
+    const int32_t* col = cv.col + (int64_t)i * cv.cap;
+    const C* P = reinterpret_cast<const C*>(cv.P) + (int64_t)i * cv.cap * DD;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) s_col[t] = col[t];
+    for (int t = threadIdx.x; t < m * DD; t += blockDim.x) s_P[t] = P[t];
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (C)cv.vnodes[t];
+  }
+  __syncthreads();
+
+  C U[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) U[a] = ALE ? (C)cv.mom[(int64_t)i * MOM_STRIDE + 1 + a] : (C)0;
+
+  // convective velocities c = v - U of this thread's velocities
+  C cvel[NCH][4][DIM];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int chunk = threadIdx.x + q * blockDim.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k = 4 * chunk + e;
+      int kk = k < NV ? k : 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        cvel[q][e][a] = k < NV ? s_v[kk % nv] - U[a] : (C)0;
+        kk /= nv;
+      }
+    }
+  }
+
+  C acc[NCH][NC][4], sk[NCH][4];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      sk[q][e] = (C)0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[q][c][e] = (C)0;
+    }
+
+  const S* fbase = reinterpret_cast<const S*>(cv.f_in);
+  const int64_t rowlen = (int64_t)NC * NVp;
+  for (int s = 0; s < m; ++s) {
+    const int j = s_col[s];
+    C P[DD];
+#pragma unroll
+    for (int t = 0; t < DD; ++t) P[t] = s_P[s * DD + t];
+    const S* fj = fbase + (int64_t)j * rowlen;
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      const int chunk = threadIdx.x + q * blockDim.x;
+      if (chunk < nchunk) {
+        C fv[NC][4];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ld4(fj + (int64_t)c * NVp + 4 * chunk, fv[c]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          C mk = (C)0;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            C p = cvel[q][e][0] * P[d * DIM + 0];
+#pragma unroll
+            for (int a = 1; a < DIM; ++a) p += cvel[q][e][a] * P[d * DIM + a];
+            mk += minc(p, (C)0);
+          }
+          sk[q][e] += mk;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[q][c][e] += mk * fv[c][e];
+        }
+      }
+    }
+  }
+
+  // f~ = f_i - 2 dt (acc - sk f_i) and one-pass raw moment sums
+  const S* fi = fbase + (int64_t)i * rowlen;
+  const C two_dt = (C)(2.0 * cv.dt);
+  C ft[NCH][NC][4];
+  C part[DIM + 2];
+#pragma unroll
+  for (int t = 0; t < DIM + 2; ++t) part[t] = (C)0;
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int chunk = threadIdx.x + q * blockDim.x;
+    if (chunk < nchunk) {
+      C fiv[NC][4];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ld4(fi + (int64_t)c * NVp + 4 * chunk, fiv[c]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ft[q][c][e] = fiv[c][e] - two_dt * (acc[q][c][e] - sk[q][e] * fiv[c][e]);
+        const int k = 4 * chunk + e;
+        if (k < NV) {
+          int kk = k;
+          C v2 = (C)0;
+          const C g = ft[q][0][e];
+          part[0] += g;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            const C va = s_v[kk % nv];
+            kk /= nv;
+            part[1 + a] += va * g;
+            v2 += va * va;
+          }
+          part[DIM + 1] += v2 * g;
+          if (NC == 2) part[DIM + 1] += ft[q][NC - 1][e];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ft[q][c][e] = (C)0;
+    }
+  }
+  double tot[DIM + 2];
+  block_sum0<DIM + 2, C>(part, tot, s_red);
+
+  // moments, tau and relaxation coefficients (one thread, FP64), broadcast through shared memory
+  C* s_fin = reinterpret_cast<C*>(s_red + 6 * 32);  // past the slots block_sum0 uses (5 x 32)
+  if (threadIdx.x == 0) {
+    double rho, Un[3] = {0, 0, 0}, T;
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    finish_moments<DIM>(tot, wv, &rho, Un, &T);
+    double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
+    mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
+    double a = 1.0, b = 0.0, pref = 0.0, inv2T = 0.0;
+    if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T)) {
+      set_status(cv.status, ST_NONFINITE);
+    } else if (cv.tau_mode != 2) {
+      const double pi = 3.14159265358979323846;
+      const double tau = cv.tau_mode == 1 ? sqrt(2.0 / pi) * cv.kn : sqrt(2.0 / pi) * cv.kn / (rho * sqrt(T));
+      a = tau / (tau + cv.dt);
+      b = cv.dt / (tau + cv.dt);
+      pref = DIM == 2 ? rho / (2.0 * pi * T) : rho / pow(2.0 * pi * T, 1.5);
+      inv2T = 1.0 / (2.0 * T);
+    }
+    s_fin[0] = (C)a; s_fin[1] = (C)b; s_fin[2] = (C)pref; s_fin[3] = (C)inv2T; s_fin[4] = (C)T;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s_fin[5 + d] = (C)Un[d];
+  }
+  __syncthreads();
+  const C ca = s_fin[0], cb = s_fin[1], pref = s_fin[2], inv2T = s_fin[3], Tn = s_fin[4];
+  C Un[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) Un[d] = s_fin[5 + d];
+
+  S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * rowlen;
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int chunk = threadIdx.x + q * blockDim.x;
+    if (chunk < nchunk) {
+      C out[NC][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = 4 * chunk + e;
+        if (k < NV) {
+          int kk = k;
+          C c2 = (C)0;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            const C d = s_v[kk % nv] - Un[a];
+            kk /= nv;
+            c2 += d * d;
+          }
+          const C M = pref * expc<C>(-c2 * inv2T);
+          out[0][e] = ca * ft[q][0][e] + cb * M;
+          if (NC == 2) out[NC - 1][e] = ca * ft[q][NC - 1][e] + cb * Tn * M;
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) out[c][e] = (C)0;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, out[c]);
+    }
+  }
+}
+
+template <typename S, typename C, int DIM, int NCH>
+static void launch_transport_t(const CaseView& cv, int threads, size_t smem, cudaStream_t s) {
+  if (cv.ale) {
+    auto k = k_transport<S, C, DIM, NCH, true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<cv.n_int, threads, smem, s>>>(cv);
+  } else {
+    auto k = k_transport<S, C, DIM, NCH, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<cv.n_int, threads, smem, s>>>(cv);
+  }
+}
+
+template <typename S, typename C, int DIM>
+static void launch_transport_d(const CaseView& cv, cudaStream_t s) {
+  const int nchunk = cv.NVp / 4;
+  int nch = 1;
+  while ((nchunk + nch - 1) / nch > 256) nch *= 2;
+  const int threads = (((nchunk + nch - 1) / nch) + 31) / 32 * 32;
+  const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * cv.cap) + sizeof(C) * cv.cap * DIM * DIM;
+  switch (nch) {
+    case 1: launch_transport_t<S, C, DIM, 1>(cv, threads, smem, s); break;
+    case 2: launch_transport_t<S, C, DIM, 2>(cv, threads, smem, s); break;
+    case 4: launch_transport_t<S, C, DIM, 4>(cv, threads, smem, s); break;
+    default: launch_transport_t<S, C, DIM, 8>(cv, threads, smem, s); break;
+  }
+}
+
+int launch_transport(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_int == 0) return 0;
+  if (cv.dim == 2) {
+    if (cv.storage == 0) launch_transport_d<double, double, 2>(cv, s);
+    else if (cv.storage == 1) launch_transport_d<float, float, 2>(cv, s);
+    else launch_transport_d<__nv_bfloat16, float, 2>(cv, s);
+  } else {
+    if (cv.storage == 0) launch_transport_d<double, double, 3>(cv, s);
+    else if (cv.storage == 1) launch_transport_d<float, float, 3>(cv, s);
+    else launch_transport_d<__nv_bfloat16, float, 3>(cv, s);
+  }
+  return 1;
+}
+
+// ---------------------------------------------------------------------------
+// walls
+// ---------------------------------------------------------------------------
+template <typename S, typename C, int DIM>
+__global__ void __launch_bounds__(256) k_walls(const CaseView cv) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* s_red = reinterpret_cast<double*>(smem);
+  C* s_v = reinterpret_cast<C*>(smem + RED_BYTES);
+  int32_t* s_j = reinterpret_cast<int32_t*>(smem + RED_BYTES + NODE_BYTES);
+  C* s_r = reinterpret_cast<C*>(smem + RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)));
+  const int w = blockIdx.x;
+  const int b = cv.wall_idx[w];
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  if (threadIdx.x == 0) {
+    const int m = cv.cnt[b];
+    const int32_t* col = cv.col + (int64_t)b * cv.cap;
+    const C* R = reinterpret_cast<const C*>(cv.recon) + (int64_t)b * cv.cap;
+    int mi = 0;
+    for (int s = 0; s < m; ++s)
+      if (cv.kind[col[s]] == 0) { s_j[1 + mi] = col[s]; s_r[mi] = R[s]; ++mi; }
+    s_j[0] = mi;
+  }
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (C)cv.vnodes[t];
+  __syncthreads();
+  const int mi = s_j[0];
+  const int64_t rowlen = (int64_t)NC * NVp;
+  S* f = reinterpret_cast<S*>(cv.f_out);
+  S* fb = f + (int64_t)b * rowlen;
+  const int8_t* cls = cv.wcls + (int64_t)w * NVp;
+  const C* vn = reinterpret_cast<const C*>(cv.wvn) + (int64_t)w * NVp;
+  const C* Mw = reinterpret_cast<const C*>(cv.mw) + (cv.kind[b] == cv.lid_wall ? NVp : 0);
+
+  C flux[1] = {(C)0};
+  C part[DIM + 2];
+#pragma unroll
+  for (int t = 0; t < DIM + 2; ++t) part[t] = (C)0;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    if (cls[k] == 0) {
+      C g[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) g[c] = (C)0;
+      for (int s = 0; s < mi; ++s) {
+        const S* fj = f + (int64_t)s_j[1 + s] * rowlen;
+        const C r = s_r[s];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) g[c] += r * ld1(fj + (int64_t)c * NVp + k);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) st1(fb + (int64_t)c * NVp + k, g[c]);
+      flux[0] += vn[k] * g[0];
+      int kk = k;
+      C v2 = (C)0;
+      part[0] += g[0];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const C va = s_v[kk % nv];
+        kk /= nv;
+        part[1 + a] += va * g[0];
+        v2 += va * va;
+      }
+      part[DIM + 1] += v2 * g[0];
+      if (NC == 2) part[DIM + 1] += g[NC - 1];
+    }
+  }
+  double ftot[1];
+  block_sum0<1, C>(flux, ftot, s_red);
+  const double rho_w = ftot[0] * cv.winv[w];
+  const C crw = (C)rho_w, cT = (C)cv.wall_T;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    if (cls[k] != 0) {
+      const C g0 = crw * Mw[k];
+      st1(fb + k, g0);
+      if (NC == 2) st1(fb + NVp + k, cT * g0);
+      int kk = k;
+      C v2 = (C)0;
+      part[0] += g0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const C va = s_v[kk % nv];
+        kk /= nv;
+        part[1 + a] += va * g0;
+        v2 += va * va;
+      }
+      part[DIM + 1] += v2 * g0;
+      if (NC == 2) part[DIM + 1] += cT * g0;
+    }
+  }
+  double tot[DIM + 2];
+  block_sum0<DIM + 2, C>(part, tot, s_red);
+  if (threadIdx.x == 0) {
+    double rho, Un[3] = {0, 0, 0}, T;
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    finish_moments<DIM>(tot, wv, &rho, Un, &T);
+    double* mo = cv.mom + (int64_t)b * MOM_STRIDE;
+    mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
+    if (!(rho_w >= 0.0) || !isfinite(rho_w)) set_status(cv.status, ST_NONFINITE);
+  }
+}
+
+int launch_walls(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_wall == 0) return 0;
+  const int threads = 256;
+  const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)) + sizeof(double) * cv.cap;
+  if (cv.dim == 2) {
+    if (cv.storage == 0) k_walls<double, double, 2><<<cv.n_wall, threads, smem, s>>>(cv);
+    else if (cv.storage == 1) k_walls<float, float, 2><<<cv.n_wall, threads, smem, s>>>(cv);
+    else k_walls<__nv_bfloat16, float, 2><<<cv.n_wall, threads, smem, s>>>(cv);
+  } else {
+    if (cv.storage == 0) k_walls<double, double, 3><<<cv.n_wall, threads, smem, s>>>(cv);
+    else if (cv.storage == 1) k_walls<float, float, 3><<<cv.n_wall, threads, smem, s>>>(cv);
+    else k_walls<__nv_bfloat16, float, 3><<<cv.n_wall, threads, smem, s>>>(cv);
+  }
+  return 1;
+}
+
+// ---------------------------------------------------------------------------
+// wall tables (fixed walls): classification, |v.n|, 1/sum_{v.n>0} (v.n) M_w
+// and the unit-density wall Maxwellians, all evaluated in FP64
+// ---------------------------------------------------------------------------
+template <typename C, int DIM>
+__global__ void k_wall_tables(CaseView cv) {
+  __shared__ double s_sum[32];
+  const int w = blockIdx.x;
+  const int b = cv.wall_idx[w];
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  double nb[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) nb[a] = cv.normal[(int64_t)b * DIM + a];
+  const bool lid = cv.kind[b] == cv.lid_wall;
+  const double pi = 3.14159265358979323846, T = cv.wall_T;
+  const double pref = DIM == 2 ? 1.0 / (2.0 * pi * T) : 1.0 / pow(2.0 * pi * T, 1.5);
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < NVp; k += blockDim.x) {
+    int8_t cl = 0;
+    double avn = 0.0;
+    if (k < NV) {
+      int kk = k;
+      double vn = 0.0, c2 = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double va = cv.vnodes[kk % nv];
+        kk /= nv;
+        vn = __dadd_rn(vn, __dmul_rn(va, nb[a]));
+        const double c = va - (lid ? cv.lid_u[a] : 0.0);
+        c2 += c * c;
+      }
+      cl = vn > 0.0 ? 1 : 0;
+      avn = fabs(vn);
+      if (cl) acc += vn * (pref * exp(-c2 / (2.0 * T)));
+    }
+    cv.wcls[(int64_t)w * NVp + k] = cl;
+    reinterpret_cast<C*>(cv.wvn)[(int64_t)w * NVp + k] = (C)avn;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) s += s_sum[q];
+    cv.winv[w] = s > 0.0 ? 1.0 / s : 0.0;
+    if (!(s > 0.0)) set_status(cv.status, ST_SINGULAR);
+  }
+}
+
+template <typename C, int DIM>
+__global__ void k_mw_table(CaseView cv) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cv.NVp) return;
+  const double pi = 3.14159265358979323846, T = cv.wall_T;
+  const double pref = DIM == 2 ? 1.0 / (2.0 * pi * T) : 1.0 / pow(2.0 * pi * T, 1.5);
+  for (int lid = 0; lid < 2; ++lid) {
+    double M = 0.0;
+    if (k < cv.NV) {
+      int kk = k;
+      double c2 = 0.0;
+      for (int a = 0; a < DIM; ++a) {
+        const double c = cv.vnodes[kk % cv.nv] - (lid ? cv.lid_u[a] : 0.0);
+        kk /= cv.nv;
+        c2 += c * c;
+      }
+      M = pref * exp(-c2 / (2.0 * T));
+    }
+    reinterpret_cast<C*>(cv.mw)[lid * cv.NVp + k] = (C)M;
+  }
+}
+
+// Velocity nodes v_j = -vmax + j dv in the centred form (j - (nv-1)/2) dv, exactly
+// symmetric about zero (Sec. 3.3).
+__global__ void k_nodes(CaseView cv) {
+  const int j = threadIdx.x;
+  if (j < cv.nv) cv.vnodes[j] = __dmul_rn(__dadd_rn((double)j, -0.5 * (double)(cv.nv - 1)), cv.dv);
+}
+
+int launch_init_tables(const CaseView& cv, cudaStream_t s) {
+  int n = 1;
+  k_nodes<<<1, 64, 0, s>>>(cv);
+  const bool f64 = cv.storage == 0;
+  if (cv.dim == 2) {
+    if (f64) k_mw_table<double, 2><<<grid_for(cv.NVp, 256), 256, 0, s>>>(cv);
+    else k_mw_table<float, 2><<<grid_for(cv.NVp, 256), 256, 0, s>>>(cv);
+  } else {
+    if (f64) k_mw_table<double, 3><<<grid_for(cv.NVp, 256), 256, 0, s>>>(cv);
+    else k_mw_table<float, 3><<<grid_for(cv.NVp, 256), 256, 0, s>>>(cv);
+  }
+  ++n;
+  if (cv.n_wall > 0) {
+    if (cv.dim == 2) {
+      if (f64) k_wall_tables<double, 2><<<cv.n_wall, 256, 0, s>>>(cv);
+      else k_wall_tables<float, 2><<<cv.n_wall, 256, 0, s>>>(cv);
+    } else {
+      if (f64) k_wall_tables<double, 3><<<cv.n_wall, 256, 0, s>>>(cv);
+      else k_wall_tables<float, 3><<<cv.n_wall, 256, 0, s>>>(cv);
+    }
+    ++n;
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------------------
+// point motion (Eqs. originalALE1, ALE1)
+// ---------------------------------------------------------------------------
+__global__ void k_move(CaseView cv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cv.n_int) return;
+  const int i = cv.int_idx[t];
+  unsigned long long nclamp = 0;
+  for (int a = 0; a < cv.dim; ++a) {
+    double* xa = cv.x + (int64_t)i * cv.dim + a;
+    double y = __dadd_rn(*xa, __dmul_rn(cv.dt, cv.mom[(int64_t)i * MOM_STRIDE + 1 + a]));
+    if (cv.periodic) {
+      if (y >= 1.0) y = __dadd_rn(y, -1.0);
+      else if (y < 0.0) y = __dadd_rn(y, 1.0);
+    } else if (y < cv.guard) { y = cv.guard; ++nclamp; }
+    else if (y > 1.0 - cv.guard) { y = 1.0 - cv.guard; ++nclamp; }
+    *xa = y;
+  }
+  if (nclamp) atomicAdd(&cv.status->clamps, nclamp);
+}
+
+int launch_move(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_int == 0) return 0;
+  k_move<<<grid_for(cv.n_int, 256), 256, 0, s>>>(cv);
+  return 1;
+}
+
+// ---------------------------------------------------------------------------
+// initial Maxwellian, moments of a given f, layout conversion
+// ---------------------------------------------------------------------------
+template <typename S, int DIM>
+__global__ void k_set_maxwellian(CaseView cv, double rho0, double u0, double u1, double u2, double T0) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)cv.n * cv.NVp;
+  if (t >= total) return;
+  const int i = (int)(t / cv.NVp), k = (int)(t % cv.NVp);
+  const double pi = 3.14159265358979323846;
+  double M = 0.0;
+  if (k < cv.NV) {
+    const double U[3] = {u0, u1, u2};
+    int kk = k;
+    double c2 = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+      const double c = cv.vnodes[kk % cv.nv] - U[a];
+      kk /= cv.nv;
+      c2 += c * c;
+    }
+    const double pref = DIM == 2 ? rho0 / (2.0 * pi * T0) : rho0 / pow(2.0 * pi * T0, 1.5);
+    M = pref * exp(-c2 / (2.0 * T0));
+  }
+  S* f = reinterpret_cast<S*>(cv.f_in) + (int64_t)i * NC * cv.NVp;
+  st1(f + k, (decltype(ld1(f)))M);
+  if (NC == 2) st1(f + cv.NVp + k, (decltype(ld1(f)))(T0 * M));
+}
+
+int launch_set_maxwellian(const CaseView& cv, double rho0, const double* u0, double T0, cudaStream_t s) {
+  const int64_t total = (int64_t)cv.n * cv.NVp;
+  const int g = (int)((total + 255) / 256);
+  if (cv.dim == 2) {
+    if (cv.storage == 0) k_set_maxwellian<double, 2><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], 0.0, T0);
+    else if (cv.storage == 1) k_set_maxwellian<float, 2><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], 0.0, T0);
+    else k_set_maxwellian<__nv_bfloat16, 2><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], 0.0, T0);
+  } else {
+    if (cv.storage == 0) k_set_maxwellian<double, 3><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], u0[2], T0);
+    else if (cv.storage == 1) k_set_maxwellian<float, 3><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], u0[2], T0);
+    else k_set_maxwellian<__nv_bfloat16, 3><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], u0[2], T0);
+  }
+  return 1;
+}
+
+// Moments of every point of f (internal layout), one CTA per point.
+template <typename S, typename C, int DIM>
+__global__ void k_moments(CaseView cv, const S* f) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  __shared__ double s_red[8 * 32];
+  const int i = blockIdx.x;
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const S* fi = f + (int64_t)i * NC * NVp;
+  C part[DIM + 2];
+#pragma unroll
+  for (int t = 0; t < DIM + 2; ++t) part[t] = (C)0;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    const C g = ld1(fi + k);
+    int kk = k;
+    C v2 = (C)0;
+    part[0] += g;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const C va = (C)cv.vnodes[kk % nv];
+      kk /= nv;
+      part[1 + a] += va * g;
+      v2 += va * va;
+    }
+    part[DIM + 1] += v2 * g;
+    if (NC == 2) part[DIM + 1] += ld1(fi + NVp + k);
+  }
+  double tot[DIM + 2];
+  block_sum0<DIM + 2, C>(part, tot, s_red);
+  if (threadIdx.x == 0) {
+    double rho, Un[3] = {0, 0, 0}, T;
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    finish_moments<DIM>(tot, wv, &rho, Un, &T);
+    double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
+    mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
+  }
+}
+
+int launch_moments(const CaseView& cv, const void* f, cudaStream_t s) {
+  if (cv.dim == 2) {
+    if (cv.storage == 0) k_moments<double, double, 2><<<cv.n, 256, 0, s>>>(cv, (const double*)f);
+    else if (cv.storage == 1) k_moments<float, float, 2><<<cv.n, 256, 0, s>>>(cv, (const float*)f);
+    else k_moments<__nv_bfloat16, float, 2><<<cv.n, 256, 0, s>>>(cv, (const __nv_bfloat16*)f);
+  } else {
+    if (cv.storage == 0) k_moments<double, double, 3><<<cv.n, 256, 0, s>>>(cv, (const double*)f);
+    else if (cv.storage == 1) k_moments<float, float, 3><<<cv.n, 256, 0, s>>>(cv, (const float*)f);
+    else k_moments<__nv_bfloat16, float, 3><<<cv.n, 256, 0, s>>>(cv, (const __nv_bfloat16*)f);
+  }
+  return 1;
+}
+
+template <typename A, typename B>
+__global__ void k_pack(const A* src, B* dst, int64_t rows, int NV, int NVp) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * NVp) return;
+  const int64_t r = t / NVp;
+  const int k = (int)(t % NVp);
+  const float fz = 0.0f;
+  if (k < NV) st1(dst + t, (decltype(ld1(dst)))ld1(src + r * NV + k));
+  else st1(dst + t, (decltype(ld1(dst)))fz);
+}
+
+template <typename A, typename B>
+__global__ void k_unpack(const A* src, B* dst, int64_t rows, int NV, int NVp) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * NV) return;
+  const int64_t r = t / NV;
+  const int k = (int)(t % NV);
+  st1(dst + t, (decltype(ld1(dst)))ld1(src + r * NVp + k));
+}
+
+template <typename A>
+static void pack_from(const CaseView& cv, const A* src, void* dst, cudaStream_t s) {
+  const int64_t rows = (int64_t)cv.n * cv.ncomp;
+  const int g = (int)((rows * cv.NVp + 255) / 256);
+  if (cv.storage == 0) k_pack<A, double><<<g, 256, 0, s>>>(src, (double*)dst, rows, cv.NV, cv.NVp);
+  else if (cv.storage == 1) k_pack<A, float><<<g, 256, 0, s>>>(src, (float*)dst, rows, cv.NV, cv.NVp);
+  else k_pack<A, __nv_bfloat16><<<g, 256, 0, s>>>(src, (__nv_bfloat16*)dst, rows, cv.NV, cv.NVp);
+}
+
+template <typename B>
+static void unpack_to(const CaseView& cv, const void* src, B* dst, cudaStream_t s) {
+  const int64_t rows = (int64_t)cv.n * cv.ncomp;
+  const int g = (int)((rows * cv.NV + 255) / 256);
+  if (cv.storage == 0) k_unpack<double, B><<<g, 256, 0, s>>>((const double*)src, dst, rows, cv.NV, cv.NVp);
+  else if (cv.storage == 1) k_unpack<float, B><<<g, 256, 0, s>>>((const float*)src, dst, rows, cv.NV, cv.NVp);
+  else k_unpack<__nv_bfloat16, B><<<g, 256, 0, s>>>((const __nv_bfloat16*)src, dst, rows, cv.NV, cv.NVp);
+}
+
+int launch_pack_f(const CaseView& cv, const void* src, int src_dtype, void* dst, cudaStream_t s) {
+  if (src_dtype == 0) pack_from(cv, (const double*)src, dst, s);
+  else if (src_dtype == 1) pack_from(cv, (const float*)src, dst, s);
+  else pack_from(cv, (const __nv_bfloat16*)src, dst, s);
+  return 1;
+}
+
+int launch_unpack_f(const CaseView& cv, const void* src, void* dst, int dst_dtype, cudaStream_t s) {
+  if (dst_dtype == 0) unpack_to(cv, src, (double*)dst, s);
+  else if (dst_dtype == 1) unpack_to(cv, src, (float*)dst, s);
+  else unpack_to(cv, src, (__nv_bfloat16*)dst, s);
+  return 1;
+}
+
+}  // namespace bgk

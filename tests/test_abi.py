@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every symbol include/bgk.h declares (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import bgk_inputs as bi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_02350_gb300 import _build
+    _build.build()
+    import paper_2408_02350_gb300 as g
+    return g
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bgk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bgk_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_expected_entry_points():
+    names = _declared()
+    for must in ("bgk_init", "bgk_neighbours", "bgk_step", "bgk_moments", "bgk_free", "bgk_sync"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    h = C.CDLL(lib.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(h, n)]
+    assert not missing, missing
+    assert set(_declared()) <= set(lib.exported_symbols()) | {"bgk_version"}
+    assert lib.bgk_version() == 1
+
+
+def test_params_struct_layout_matches_header(lib):
+    # bgk_params: 10 int32 + 3 doubles ... checked by size and field offsets against the C layout rules
+    q = lib.bgk_params
+    assert q.dt.offset % 8 == 0 and q.lid_u.offset % 8 == 0
+    assert C.sizeof(q) == q.lid_u.offset + 24
+
+
+@pytest.mark.parametrize("field,value", [("dim", 4), ("nv", 1), ("nv", 65), ("storage", 3), ("max_nbrs", 0),
+                                         ("dt", 0.0), ("h", -1.0), ("tau_mode", 5), ("kn", 0.0)])
+def test_init_rejects_bad_parameters_before_touching_the_device(lib, field, value):
+    p = bi.config("cavity2d_n41_v16_f64", n=5)
+    cl = bi.cloud_for(p)
+    q = lib.params_from(p)
+    setattr(q, field, value)
+    with pytest.raises(lib.BGKError) as e:
+        lib.bgk_init([q], [len(cl["kind"])], cl["x"], cl["kind"], cl["normal"])
+    assert e.value.code == lib.BGK_E_INVAL
+    assert "bgk_init" in lib.bgk_last_error(None)
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2408_02350_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.sub(r"(#|//).*", "", text).lower() or f.endswith(".md"), f
