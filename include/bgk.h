@@ -171,6 +171,26 @@ const char* bgk_last_error(const bgk_ctx* ctx);
 /* Release the context and all device memory it owns.  NULL is ignored. */
 void bgk_free(bgk_ctx* ctx);
 
+/* Neighbour lists for callers that cannot allocate device memory (code under a
+ * memory manager that owns the device heap, or code that must not allocate
+ * after start-up).  The paper has no counterpart: this is the neighbour search
+ * of bgk_neighbours (same test, same ascending order, bit-identical lists)
+ * written into caller-owned buffers, with no context and no allocation.
+ *   x    device, [n][dim] double positions (unit box; minimum image if periodic)
+ *   cnt  device, [n] int32 output: neighbours kept per point (<= cap)
+ *   col  device, [n][cap] int32 output: neighbour indices, ascending per row
+ * The cell-list scratch is a fixed array of about 3.7 MB in device global
+ * memory, present on every GPU that loads the library until exit.  Limits:
+ * n <= 131072 points, at most 131072 cells (cells per axis = floor(1/h)),
+ * cap <= 443; larger sizes return BGK_E_INVAL without doing any work.  The
+ * first call on a device looks up the array's address (make it before any
+ * stream capture).  Every call clears what must start at zero; calls that
+ * overlap on the GPU share the scratch and race.  Stream-ordered; with
+ * check = 1 the call waits for the stream and returns BGK_E_NBR_OVERFLOW when
+ * some point had more than cap neighbours (its row is then truncated). */
+int bgk_neighbours_noalloc(int32_t dim, int64_t n, const double* x, double h, int32_t periodic,
+                           int32_t cap, int32_t* cnt, int32_t* col, int32_t check, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

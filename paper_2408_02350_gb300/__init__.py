@@ -74,6 +74,8 @@ _SIGS = {
     "bgk_get_stats": (C.c_int, [_P, C.POINTER(bgk_stats)]),
     "bgk_last_error": (C.c_char_p, [_P]),
     "bgk_free": (None, [_P]),
+    "bgk_neighbours_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
+                                         C.c_int32, _P]),
 }
 
 _lib = None
@@ -233,6 +235,18 @@ def bgk_last_error(ctx) -> str:
 
 def bgk_free(ctx) -> None:
     lib().bgk_free(ctx)
+
+
+def bgk_neighbours_noalloc(dim: int, n: int, x, h: float, periodic: int, cap: int, cnt, col, check: int = 1,
+                           stream=None) -> None:
+    """Neighbour lists into caller-owned device tensors, without any device allocation.
+
+    For callers that cannot allocate device memory.  x: [n, dim] float64, cnt: [n]
+    int32, col: [n, cap] int32, all on the current CUDA device."""
+    code = lib().bgk_neighbours_noalloc(dim, n, _ptr(x), h, periodic, cap, _ptr(cnt), _ptr(col), check,
+                                        _stream_ptr(stream))
+    if code != BGK_OK:
+        raise BGKError(code, "bgk_neighbours_noalloc")
 
 
 # ---- convenience ----
