@@ -32,12 +32,19 @@ OK, E_OVERFLOW, E_SINGULAR, E_INVAL, E_NOMEM = 0, 1, 2, 3, 4
 def build(force: bool = False) -> str:
     """Compile bgk_oracle.c into oracle/_build/liboracle.so (gcc -O2, no FMA contraction)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+    import hashlib
+    import platform
+    stamp = hashlib.sha256(open(_SRC, "rb").read() + platform.machine().encode()).hexdigest()
+    stamp_path = _OUT + ".stamp"
+    old = open(stamp_path).read() if os.path.exists(stamp_path) else ""
+    if force or old != stamp or not os.path.exists(_OUT):
         tmp = _OUT + ".%d.tmp" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
                "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _OUT)
+        with open(stamp_path, "w") as fh:
+            fh.write(stamp)
     return _OUT
 
 

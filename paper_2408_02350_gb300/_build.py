@@ -1,7 +1,9 @@
 """Build libbgk.so (the CUDA library behind include/bgk.h) in-tree with nvcc for sm_103a."""
 from __future__ import annotations
 
+import hashlib
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -29,10 +31,26 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _stamp(paths: list[str], extra: list[str] | None) -> str:
+    """Content hash of the sources, flags and host architecture the library is built from."""
+    h = hashlib.sha256()
+    for p in sorted(paths):
+        h.update(p.encode())
+        h.update(open(p, "rb").read())
+    h.update(" ".join(ARCH + FLAGS + (extra or [])).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(ROOT, "include", "bgk.h"))
+    stamp_path = os.path.join(BUILD, "stamp")
+    stamp = _stamp([os.path.join(CSRC, s) for s in SOURCES] + headers, extra)
+    old = open(stamp_path).read() if os.path.exists(stamp_path) else ""
+    if old != stamp or not os.path.exists(LIB):
+        force = True
     nvcc = _nvcc()
     jobs = []
     for src in SOURCES:
@@ -57,6 +75,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         tmp = LIB + ".%d.tmp" % os.getpid()
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
         os.replace(tmp, LIB)
+    with open(stamp_path, "w") as fh:
+        fh.write(stamp)
     return LIB
 
 

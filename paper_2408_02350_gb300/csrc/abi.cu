@@ -291,6 +291,7 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
 
     if ((st = dalloc(ctx, &v.vnodes, q.nv))) return bail(st);
     if ((st = dalloc(ctx, &v.xf, n * dim))) return bail(st);
+    if ((st = dalloc(ctx, &v.xlo, n * dim))) return bail(st);
     if ((st = dalloc(ctx, &v.cell_of, n))) return bail(st);
     if ((st = dalloc(ctx, &v.cell_start, ncell + 1))) return bail(st);
     if ((st = dalloc(ctx, &v.cell_cnt, ncell))) return bail(st);
@@ -586,7 +587,7 @@ int bgk_set_timing(bgk_ctx* ctx, int32_t enable) {
   if (st) return st;
   ctx->timing = enable != 0;
   // pre-create event pairs so that timed regions do not pay for cudaEventCreate
-  while (ctx->timing && ctx->ev.size() < 4096) {
+  while (ctx->timing && ctx->ev.size() < 8192) {
     EvPair e;
     CK(ctx, cudaEventCreate(&e.a));
     CK(ctx, cudaEventCreate(&e.b));

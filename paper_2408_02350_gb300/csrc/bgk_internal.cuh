@@ -39,7 +39,8 @@ struct CaseView {
   const int32_t* int_idx;  // [n_int] interior point indices, ascending
   const int32_t* wall_idx; // [n_wall] wall point indices, ascending
 
-  float* xf;            // [n][dim] FP32 copy of x (neighbour-search prefilter)
+  float* xf;            // [n][dim] FP32 rounding of x (neighbour-search prefilter, high part)
+  float* xlo;           // [n][dim] FP32 x - xf (low part): xf + xlo carries x to ~2^-48
   int32_t* cell_of;     // [n]
   int32_t* cell_start;  // [ncell + 1]
   int32_t* cell_cnt;    // [ncell]

@@ -300,16 +300,308 @@ static void launch_transport_d(const CaseView& cv, cudaStream_t s) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// transport + moments + relaxation, FP32 arithmetic (FP32 or BF16 storage):
+// one warp per interior point.  Each lane owns 4 consecutive velocities of
+// every 128-velocity slice; the warps of a CTA handle consecutive points, whose
+// shared neighbour rows are often served from L1.  f~ of
+// a slice is written to the output row and re-read after the moments, which are
+// warp-shuffle sums of per-lane Kahan-compensated slice sums (no CTA barrier).
+// With ROW4 (nv % 4 == 0) a lane's 4 velocities share (v_y, v_z), so the
+// projection c.P_d costs one FMA per velocity: c.P_d = c_x P_dx + (c_y P_dy + c_z P_dz).
+// ---------------------------------------------------------------------------
+// Quotient k / n for 0 <= k < 2^13, 1 <= n <= 64 by a float reciprocal: (k + 1/2)/n lies at least
+// 1/(2n) away from an integer and the float error is below (k/n + 1) 2^-23, so truncation is exact.
+__device__ __forceinline__ int fdiv_small(int k, float inv_n) { return (int)(((float)k + 0.5f) * inv_n); }
+
+// Velocity components of the 4 velocities k0..k0+3.  With ROW4 (nv % 4 == 0, k0 % 4 == 0)
+// they share every component but the first.
+template <int DIM, bool ROW4>
+__device__ __forceinline__ void chunk_velocities(int k0, int nv, int NV, float inv_nv, const float* s_v,
+                                                 float (&vel)[4][DIM], bool (&kin)[4]) {
+  if (ROW4) {
+    int q = fdiv_small(k0, inv_nv);
+    const int kx0 = k0 - q * nv;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { vel[e][0] = s_v[kx0 + e]; kin[e] = k0 + e < NV; }
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) {
+      const int q2 = fdiv_small(q, inv_nv);
+      const float va = s_v[q - q2 * nv];
+      q = q2;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) vel[e][a] = va;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int kk = k0 + e;
+      kin[e] = kk < NV;
+      if (!kin[e]) kk = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const int q = fdiv_small(kk, inv_nv);
+        vel[e][a] = s_v[kk - q * nv];
+        kk = q;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 min0(float2 p) { return make_float2(fminf(p.x, 0.0f), fminf(p.y, 0.0f)); }
+
+template <typename S, int DIM, bool ALE, bool ROW4>
+__global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int DD = DIM * DIM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const float inv_nv = 1.0f / (float)nv;
+  float* s_v = reinterpret_cast<float*>(smem);
+  int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256) + warp * cap;
+  float* s_P = reinterpret_cast<float*>(smem + 256 + align16(sizeof(int32_t) * cap * W)) + (size_t)warp * cap * DD;
+
+  const int t = blockIdx.x * W + warp;
+  const bool active = t < cv.n_int;
+  const int i = active ? cv.int_idx[t] : 0;
+  const int m = active ? cv.cnt[i] : 0;
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = (float)cv.vnodes[q];
+  {
+    const int32_t* col = cv.col + (int64_t)i * cap;
+    const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
+    for (int q = lane; q < m; q += 32) s_col[q] = col[q];
+    for (int q = lane; q < m * DD; q += 32) s_P[q] = P[q];
+  }
+  __syncthreads();
+
+  float U[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) U[a] = (ALE && active) ? (float)cv.mom[(int64_t)i * MOM_STRIDE + 1 + a] : 0.0f;
+
+  const int nchunk = NVp >> 2;
+  const int nslice = (nchunk + 31) >> 5;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  const S* fbase = reinterpret_cast<const S*>(cv.f_in);
+  const S* fi = fbase + (int64_t)i * rowlen;
+  S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * rowlen;
+  const float two_dt = (float)(2.0 * cv.dt);
+
+  float msum[DIM + 2], mcmp[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) { msum[q] = 0.0f; mcmp[q] = 0.0f; }
+
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    const bool valid = active && chunk < nchunk;
+    float vel[4][DIM];
+    bool kin[4];
+    chunk_velocities<DIM, ROW4>(4 * chunk, nv, NV, inv_nv, s_v, vel, kin);
+    float acc[NC][4], sk[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      sk[e] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c][e] = 0.0f;
+    }
+    if (valid) {
+      const S* fj0 = fbase + 4 * chunk;
+      if (ROW4) {
+        // velocity pairs (0,1), (2,3) in packed FP32x2 arithmetic
+        const float2 cx01 = f2(vel[0][0] - U[0], vel[1][0] - U[0]);
+        const float2 cx23 = f2(vel[2][0] - U[0], vel[3][0] - U[0]);
+        float crest[DIM - 1];
+#pragma unroll
+        for (int a = 1; a < DIM; ++a) crest[a - 1] = vel[0][a] - U[a];
+        float2 sk01 = f2(0.0f, 0.0f), sk23 = f2(0.0f, 0.0f);
+        float2 a01[NC], a23[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { a01[c] = f2(0.0f, 0.0f); a23[c] = f2(0.0f, 0.0f); }
+#pragma unroll 2
+        for (int s = 0; s < m; ++s) {
+          const int j = s_col[s];
+          float P[DD];
+#pragma unroll
+          for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
+          const S* fj = fj0 + (int64_t)j * rowlen;
+          float fv[NC][4];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ld4(fj + (int64_t)c * NVp, fv[c]);
+          float2 mk01, mk23;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            float b = crest[0] * P[d * DIM + 1];
+#pragma unroll
+            for (int a = 2; a < DIM; ++a) b = fmaf(crest[a - 1], P[d * DIM + a], b);
+            const float2 px = f2(P[d * DIM], P[d * DIM]), bb = f2(b, b);
+            const float2 m01 = min0(__ffma2_rn(cx01, px, bb));
+            const float2 m23 = min0(__ffma2_rn(cx23, px, bb));
+            if (d == 0) { mk01 = m01; mk23 = m23; }
+            else { mk01 = __fadd2_rn(mk01, m01); mk23 = __fadd2_rn(mk23, m23); }
+          }
+          sk01 = __fadd2_rn(sk01, mk01);
+          sk23 = __fadd2_rn(sk23, mk23);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            a01[c] = __ffma2_rn(mk01, f2(fv[c][0], fv[c][1]), a01[c]);
+            a23[c] = __ffma2_rn(mk23, f2(fv[c][2], fv[c][3]), a23[c]);
+          }
+        }
+        sk[0] = sk01.x; sk[1] = sk01.y; sk[2] = sk23.x; sk[3] = sk23.y;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { acc[c][0] = a01[c].x; acc[c][1] = a01[c].y; acc[c][2] = a23[c].x; acc[c][3] = a23[c].y; }
+      } else {
+        float cvel[4][DIM];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) cvel[e][a] = vel[e][a] - U[a];
+#pragma unroll 2
+        for (int s = 0; s < m; ++s) {
+          const int j = s_col[s];
+          float P[DD];
+#pragma unroll
+          for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
+          const S* fj = fj0 + (int64_t)j * rowlen;
+          float fv[NC][4];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ld4(fj + (int64_t)c * NVp, fv[c]);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float mk = 0.0f;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              float p = cvel[e][0] * P[d * DIM];
+#pragma unroll
+              for (int a = 1; a < DIM; ++a) p = fmaf(cvel[e][a], P[d * DIM + a], p);
+              mk = d == 0 ? fminf(p, 0.0f) : mk + fminf(p, 0.0f);
+            }
+            sk[e] += mk;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c][e] = fmaf(mk, fv[c][e], acc[c][e]);
+          }
+        }
+      }
+      // f~ = f_i - 2 dt (acc - sk f_i); slice moment sums, Kahan-added to the running sums
+      float fiv[NC][4], ft[NC][4];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ld4(fi + (int64_t)c * NVp + 4 * chunk, fiv[c]);
+      float ps[DIM + 2];
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? fiv[c][e] - two_dt * (acc[c][e] - sk[e] * fiv[c][e]) : 0.0f;
+        const float g = ft[0][e];
+        float v2 = 0.0f;
+        ps[0] += g;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
+        ps[DIM + 1] = fmaf(v2, g, ps[DIM + 1]);
+        if (NC == 2) ps[DIM + 1] += ft[NC - 1][e];
+      }
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) {
+        const float y = ps[q] - mcmp[q];
+        const float tt = msum[q] + y;
+        mcmp[q] = (tt - msum[q]) - y;
+        msum[q] = tt;
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, ft[c]);
+    }
+  }
+
+  // moments of f~ (all lanes get the warp totals)
+  float tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
+  const float R = tot[0];
+  float Un[DIM], u2 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { Un[a] = tot[1 + a] / R; u2 = fmaf(Un[a], Un[a], u2); }
+  const float Tn = (tot[DIM + 1] - R * u2) / (3.0f * R);
+  const float wv = (float)(DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
+  const float rho = R * wv;
+  if (!active) return;
+  if (lane == 0) {
+    double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
+    mo[0] = rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mo[1 + a] = a < DIM ? (double)Un[a < DIM ? a : 0] : 0.0;
+    mo[4] = Tn;
+    if (!(rho > 0.0f) || !(Tn > 0.0f) || !isfinite(rho) || !isfinite(Tn)) set_status(cv.status, ST_NONFINITE);
+  }
+  float ca = 1.0f, cb = 0.0f, pref = 0.0f, nl2 = 0.0f;
+  if (cv.tau_mode != 2 && rho > 0.0f && Tn > 0.0f) {
+    const float kn = (float)cv.kn, dtf = (float)cv.dt;
+    const float tau = cv.tau_mode == 1 ? 0.7978845608f * kn : 0.7978845608f * kn / (rho * sqrtf(Tn));
+    ca = tau / (tau + dtf);
+    cb = dtf / (tau + dtf);
+    const float twopiT = 6.283185307f * Tn;
+    pref = cb * (DIM == 2 ? rho / twopiT : rho / (twopiT * sqrtf(twopiT)));
+    nl2 = -0.5f / Tn;
+  }
+  const float cbT = Tn;
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    if (chunk >= nchunk) break;
+    float vel[4][DIM];
+    bool kin[4];
+    chunk_velocities<DIM, ROW4>(4 * chunk, nv, NV, inv_nv, s_v, vel, kin);
+    float ft[NC][4], out[NC][4];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ld4(fo + (int64_t)c * NVp + 4 * chunk, ft[c]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float c2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float d = vel[e][a] - Un[a];
+        c2 = fmaf(d, d, c2);
+      }
+      const float bM = kin[e] ? pref * __expf(nl2 * c2) : 0.0f;  // dt/(tau+dt) * M(v)
+      out[0][e] = kin[e] ? fmaf(ca, ft[0][e], bM) : 0.0f;
+      if (NC == 2) out[NC - 1][e] = kin[e] ? fmaf(ca, ft[NC - 1][e], cbT * bM) : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, out[c]);
+  }
+}
+
+template <typename S, int DIM>
+static void launch_transport_wp(const CaseView& cv, cudaStream_t s) {
+  const int W = 8, threads = 32 * W;
+  const size_t smem = 256 + align16(sizeof(int32_t) * cv.cap * W) + sizeof(float) * cv.cap * DIM * DIM * W;
+  const int grid = (cv.n_int + W - 1) / W;
+  const bool row4 = cv.nv % 4 == 0;
+#define BGK_LAUNCH_WP(ALE, ROW4)                                                          \
+  {                                                                                       \
+    auto k = k_transport_wp<S, DIM, ALE, ROW4>;                                           \
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+    k<<<grid, threads, smem, s>>>(cv);                                                    \
+  }
+  if (cv.ale) {
+    if (row4) BGK_LAUNCH_WP(true, true) else BGK_LAUNCH_WP(true, false)
+  } else {
+    if (row4) BGK_LAUNCH_WP(false, true) else BGK_LAUNCH_WP(false, false)
+  }
+#undef BGK_LAUNCH_WP
+}
+
 int launch_transport(const CaseView& cv, cudaStream_t s) {
   if (cv.n_int == 0) return 0;
   if (cv.dim == 2) {
     if (cv.storage == 0) launch_transport_d<double, double, 2>(cv, s);
-    else if (cv.storage == 1) launch_transport_d<float, float, 2>(cv, s);
-    else launch_transport_d<__nv_bfloat16, float, 2>(cv, s);
+    else if (cv.storage == 1) launch_transport_wp<float, 2>(cv, s);
+    else launch_transport_wp<__nv_bfloat16, 2>(cv, s);
   } else {
     if (cv.storage == 0) launch_transport_d<double, double, 3>(cv, s);
-    else if (cv.storage == 1) launch_transport_d<float, float, 3>(cv, s);
-    else launch_transport_d<__nv_bfloat16, float, 3>(cv, s);
+    else if (cv.storage == 1) launch_transport_wp<float, 3>(cv, s);
+    else launch_transport_wp<__nv_bfloat16, 3>(cv, s);
   }
   return 1;
 }

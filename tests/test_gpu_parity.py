@@ -80,7 +80,11 @@ def test_neighbour_lists_periodic_random_cloud(g):
     _cmp_lists(g, s, x, p["h"], True, 64)
 
 
-@pytest.mark.parametrize("dim,n,storage,tol", [(2, 21, "f64", 1e-12), (3, 9, "f64", 1e-12), (2, 21, "f32", 2e-6)])
+# FP32 path: separations, weights and the normal matrices are FP32 (the WLS solve is FP64);
+# one-sided wall extrapolations have condition numbers of ~30 (2D) to ~100 (3D), so their
+# weights carry up to ~100 x 1e-7 relative error: bar 5e-5.
+@pytest.mark.parametrize("dim,n,storage,tol", [(2, 21, "f64", 1e-12), (3, 9, "f64", 1e-12), (2, 21, "f32", 5e-5),
+                                               (3, 9, "f32", 5e-5)])
 def test_stencils_match(g, dim, n, storage, tol):
     name = "cavity2d_n41_v16_f64" if dim == 2 else "cavity3d_n41_v16_f32"
     p = bi.config(name, n=n, nv=4, storage=storage)
