@@ -140,6 +140,41 @@ def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
                       % (nsteps, p["n"], p["dim"], p["nv"], p["dim"], n, dt)}
 
 
+def adjoint_cost(g, torch, stream) -> dict:
+    """Forward step and adjoint step times on the adjoint workload, event-timed per kernel."""
+    p = bi.config("adjoint2d_n101_v24_f32")
+    cl = bi.cloud_for(p)
+    s = g.Solver([p], [cl])
+    s.set_maxwellian(stream=stream)
+    s.step(3, stream=stream)
+    s.sync(stream)
+    n, NV = len(cl["kind"]), p["nv"] ** 2
+    nvp = s.stats()["nv_pad"]
+    lam = torch.randn((n, 2, nvp), dtype=torch.float32, device="cuda") * 1e-3
+    lam2 = torch.zeros_like(lam)
+    dth = torch.zeros(4, dtype=torch.float64, device="cuda")
+    g.bgk_adjoint_step(s.ctx, 0, lam, lam2, dth, stream)  # allocates work buffers
+    K = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(K, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / K
+    e0.record(stream)
+    for _ in range(K):
+        g.bgk_adjoint_step(s.ctx, 0, lam, lam2, dth, stream)
+        lam, lam2 = lam2, lam
+    e1.record(stream)
+    torch.cuda.synchronize()
+    adj = e0.elapsed_time(e1) / K
+    s.sync(stream)
+    s.close()
+    return {"workload": "adjoint2d_n101_v24_f32", "points": n, "velocities": NV, "ms_forward_step": fwd,
+            "ms_adjoint_step": adj, "ratio": adj / fwd}
+
+
 def run_reference(args, p: dict) -> None:
     """Reference arm: the FP64 CPU oracle timed on host cores, each step a bounded sample."""
     rank, world, _ = _dist_env()
@@ -180,6 +215,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--n", type=int, default=None, help="override points per axis (profiling runs)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-step cost measurement")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
     p = bi.config(args.workload, **({"n": args.n} if args.n else {}))
@@ -287,6 +323,11 @@ def main():
                 "ms_per_step": ms64 / k64}
         s64.close()
 
+    # ---- discrete adjoint cost on the adjoint workload (101^2 x 24^2, FP32, fixed points) ----
+    adj = None
+    if not args.no_adjoint and world == 1:
+        adj = adjoint_cost(g, torch, stream)
+
     # ---- roofline of the dominant kernel (transport + moments + relaxation) ----
     peaks = _peaks()
     rowptr, _ = s.get_neighbours()
@@ -320,7 +361,7 @@ def main():
                 "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": args.e2e_steps},
-                "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64}
+                "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, 1)
         print(json.dumps(line), flush=True)

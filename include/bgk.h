@@ -154,11 +154,40 @@ int bgk_sync(bgk_ctx* ctx, void* stream);
 int bgk_get_state(bgk_ctx* ctx, void* blob, size_t cap, size_t* used);
 int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size);
 
+/* Change the physical parameters of case c: kn, tau_mode, dt, wall_T, lid_u,
+ * lid_wall, ale and guard (the wall tables are rebuilt); the geometry, the
+ * velocity grid, the storage and the neighbour settings must stay the same
+ * (BGK_E_INVAL otherwise).  Synchronous. */
+int bgk_set_params(bgk_ctx* ctx, int32_t c, const bgk_params* p);
+
+/* Objective of the current state of case c, not in the paper: the x-momentum flux
+ * through the lid plane averaged over the lid points,
+ * J = (1/|lid|) sum_{b in lid} sum_k v_x v_n g_b(v_k) dv^dim  (v_n the last velocity
+ * component, normal to the lid; g = g1 in 2D, f in 3D).  J (device, one double) is
+ * incremented by J; when lam is not NULL, lam += scale dJ/df.  lam has the internal
+ * layout [n][ncomp][NVp] (NVp from bgk_get_stats) of the compute type: double
+ * for BGK_F64 storage, float otherwise.  Stream-ordered. */
+int bgk_objective(bgk_ctx* ctx, int32_t c, double* J, void* lam, double scale, void* stream);
+
+/* One step of the discrete adjoint of bgk_step for fixed points (ale = 0), not in
+ * the paper: with the current state f^n of case c and lam_in = dJ/df^{n+1},
+ * lam_out = (df^{n+1}/df^n)^T lam_in, and dtheta (device, 4 doubles) is
+ * incremented by [dJ/du_lid (3 components), dJ/dKn] through this step.  The
+ * vector-Jacobian product differentiates every sub-step of Sec. 3.2: the linear
+ * upwind transport (transposed through the symmetric neighbour relation), the
+ * relaxation through rho, U, T, tau(rho, T; Kn) and M, and the walls through the
+ * reconstruction weights and the zero-mass-flux density rho_w, whose wall
+ * Maxwellian depends on u_lid.  lam_in and lam_out are distinct device buffers
+ * with the layout of bgk_objective.  The state f is not changed.  Work buffers
+ * (three copies of f) are allocated on the first call.  Stream-ordered;
+ * BGK_E_STATE when ale = 1. */
+int bgk_adjoint_step(bgk_ctx* ctx, int32_t c, const void* lam_in, void* lam_out, double* dtheta, void* stream);
+
 /* Per-kernel timing with CUDA events on the launching stream: enable = 1
  * brackets every launch of the transport kernel with an event pair.
  * bgk_get_timing synchronises and returns the summed device time (ms) and
  * launch count of kernel `which` (0 = transport+relaxation, 1 = wall, 2 =
- * neighbour build, 3 = stencils, 4 = motion) since timing was enabled. */
+ * neighbour build, 3 = stencils, 4 = motion, 5 = adjoint step) since timing was enabled. */
 int bgk_set_timing(bgk_ctx* ctx, int32_t enable);
 int bgk_get_timing(bgk_ctx* ctx, int32_t which, double* total_ms, int64_t* launches);
 

@@ -104,6 +104,8 @@ def lib():
                 "or_move": (C.c_int64, [_PP, C.c_int64, _PI, _PD, _PD]),
                 "or_init_maxwellian": (None, [_PP, C.c_int64, C.c_double, _PD, C.c_double, _PD, _PD, _PD, _PD]),
                 "or_run": (C.c_int, [_PP, C.c_int64, _PD, _PI, _PD, _PD, _PD, _PD, _PD, C.c_int32, _PL]),
+                "or_adjoint_step": (C.c_int, [_PP, C.c_int64, _PI, _PD, _PI, _PI, _PD, _PD, _PD, _PD, _PD, _PD, _PD]),
+                "or_objective": (C.c_double, [_PP, C.c_int64, _PI, _PD, _PD, C.c_double]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(h, name)
@@ -287,6 +289,26 @@ def move(p: dict, kind, U, x) -> int:
     return lib().or_move(C.byref(q), x.shape[0], _i(_i32(kind)), _d(_f64(U)), _d(x))
 
 
+def adjoint_step(p: dict, kind, normal, cnt, col, st: dict, f, lam1):
+    """(lam0, dtheta): lam0 = (dPhi/df)^T lam1 at state f; dtheta = [dJ/du_lid (3), dJ/dKn]."""
+    q = params(p)
+    f, lam1 = _f64(f), _f64(lam1)
+    lam0 = np.empty_like(f)
+    dth = np.zeros(4)
+    lib().or_adjoint_step(C.byref(q), f.shape[0], _i(_i32(kind)), _d(_f64(normal)), _i(_i32(cnt)), _i(_i32(col)),
+                          _d(_f64(st["abar"])), _d(_f64(st["frame"])), _d(_f64(st["recon"])), _d(f), _d(lam1),
+                          _d(lam0), _d(dth))
+    return lam0, dth
+
+
+def objective(p: dict, kind, f, lam=None, scale: float = 1.0) -> float:
+    """Lid x-momentum flux of state f; adds scale * dJ/df to lam when given."""
+    q = params(p)
+    f = _f64(f)
+    lp = _d(lam) if lam is not None else None
+    return lib().or_objective(C.byref(q), f.shape[0], _i(_i32(kind)), _d(f), lp, scale)
+
+
 class Simulation:
     """State (x, f, rho, U, T) of one point cloud advanced by ``or_run``."""
 
@@ -309,6 +331,29 @@ class Simulation:
         self.clamps = 0
         self.steps = 0
         assert self.f.size == n * row
+
+    def gradient(self, nsteps: int):
+        """J = (1/N) sum_{n=1..N} J(f^n) from the current state, and its gradient with respect to
+        (u_lid, Kn) and to the current f, by storing every state and sweeping the adjoint backwards.
+        Fixed points only.  The state is advanced by nsteps."""
+        assert not self.p.get("ale"), "the adjoint is for fixed points"
+        cnt, col = neighbours(self.x, self.p["h"], bool(self.p.get("periodic")), int(self.p.get("max_nbrs", 48)))
+        st = stencils(self.p, self.x, self.kind, cnt, col)
+        states = [self.f.copy()]
+        J = 0.0
+        for _ in range(nsteps):
+            self.run(1)
+            states.append(self.f.copy())
+            J += objective(self.p, self.kind, self.f) / nsteps
+        lam = np.zeros_like(self.f)
+        objective(self.p, self.kind, states[nsteps], lam, 1.0 / nsteps)
+        dth = np.zeros(4)
+        for k in range(nsteps - 1, -1, -1):
+            lam, d = adjoint_step(self.p, self.kind, self.normal, cnt, col, st, states[k], lam)
+            dth += d
+            if k >= 1:
+                objective(self.p, self.kind, states[k], lam, 1.0 / nsteps)
+        return J, dth, lam
 
     def run(self, nsteps: int) -> None:
         cl = np.zeros(1, dtype=np.int64)

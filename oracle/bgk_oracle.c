@@ -647,6 +647,200 @@ void or_init_maxwellian(const or_params* p, int64_t n, double rho0, const double
   or_moments(p, n, f, rho, U, T);
 }
 
+
+/* ---- discrete adjoint of one step (fixed points, ale = 0) ----
+ *
+ * Not in the paper: the vector-Jacobian product of the step map
+ * f^{n+1} = Phi(f^n; u_lid, Kn) written out from the forward sub-steps above,
+ * for gradients of an objective J(f^1..f^N).  Given f^n and lam1 = dJ/df^{n+1}
+ * it returns lam0 = (dPhi/df^n)^T lam1 and adds to dtheta[0..2] the derivative
+ * with respect to the lid velocity and to dtheta[3] the one with respect to Kn.
+ * Transport is linear for fixed points (K does not depend on f); relaxation is
+ * differentiated through rho, U, T, tau and M; walls through the reconstruction
+ * weights and rho_w = F / N (F the arriving normal mass flux, N the
+ * normalisation of the wall Maxwellian, which depends on u_lid). */
+int or_adjoint_step(const or_params* p, int64_t n, const int32_t* kind, const double* normal,
+                    const int32_t* cnt, const int32_t* col, const double* abar, const double* frame,
+                    const double* recon, const double* f, const double* lam1, double* lam0, double* dtheta) {
+  const double pi = 3.14159265358979323846;
+  int dim = p->dim, cap = p->max_nbrs, nc = ncomp_of(dim);
+  int64_t NV = nvel_of(dim, p->nv), row = nc * NV;
+  double wv = quad_weight(p);
+  double Dm = dim == 2 ? 2.0 : 3.0; /* exponent of 2 pi T in the Maxwellian prefactor */
+  double* vel = (double*)malloc(sizeof(double) * NV * dim);
+  double* ft = (double*)malloc(sizeof(double) * n * row);
+  double* y = (double*)malloc(sizeof(double) * n * row);
+  double* lamy = (double*)calloc(n * row, sizeof(double));
+  double* lamft = (double*)calloc(n * row, sizeof(double));
+  double* Mw = (double*)malloc(sizeof(double) * row);
+  double* M = (double*)malloc(sizeof(double) * row);
+  double rho_, U_[3], T_;
+  or_velocity_grid(dim, p->nv, p->vmax, vel);
+
+  /* forward recomputation of the step's intermediates */
+  double zero3[3] = {0.0, 0.0, 0.0};
+  (void)zero3;
+  or_transport(p, n, kind, cnt, col, abar, frame, zero3, f, ft);
+  memcpy(y, ft, sizeof(double) * n * row);
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != 0) continue;
+    relax_point(p, ft + i * row, y + i * row, M, &rho_, U_, &T_);
+  }
+
+  /* walls, backward: lamy (interior rows) = lam1 + contributions of the wall values */
+  for (int64_t i = 0; i < n; ++i)
+    if (kind[i] == 0) memcpy(lamy + i * row, lam1 + i * row, sizeof(double) * row);
+  for (int64_t b = 0; b < n && !p->periodic; ++b) {
+    if (kind[b] == 0) continue;
+    const double* nb = normal + b * dim;
+    double uw[3] = {0.0, 0.0, 0.0};
+    int lid = kind[b] == p->lid_wall;
+    if (lid) for (int a = 0; a < dim; ++a) uw[a] = p->lid_u[a];
+    or_maxwellian(p, 1.0, uw, p->wall_T, Mw);
+    /* F, N and rho_w of the forward wall step */
+    double F = 0.0, N = 0.0, dN[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = 0; k < NV; ++k) {
+      double vn = 0.0;
+      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      if (vn <= 0.0) {
+        double g = 0.0;
+        for (int s = 0; s < cnt[b]; ++s) {
+          int64_t slot = b * cap + s;
+          if (kind[col[slot]] != 0) continue;
+          g += recon[slot] * y[(int64_t)col[slot] * row + k];
+        }
+        F += -vn * g;
+      } else {
+        N += vn * Mw[k];
+        for (int a = 0; a < dim; ++a) dN[a] += vn * Mw[k] * (vel[k * dim + a] - uw[a]) / p->wall_T;
+      }
+    }
+    double rho_w = F / N;
+    /* mu = dJ/drho_w, and the lid-velocity derivative of the leaving values */
+    const double* lb = lam1 + b * row;
+    double mu = 0.0, du[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = 0; k < NV; ++k) {
+      double vn = 0.0;
+      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      if (vn <= 0.0) continue;
+      for (int q = 0; q < nc; ++q) {
+        mu += lb[q * NV + k] * Mw[q * NV + k];
+        for (int a = 0; a < dim; ++a)
+          du[a] += lb[q * NV + k] * rho_w * Mw[q * NV + k] * (vel[k * dim + a] - uw[a]) / p->wall_T;
+      }
+    }
+    if (lid)
+      for (int a = 0; a < dim; ++a) dtheta[a] += du[a] - mu * rho_w / N * dN[a];
+    /* arriving values f_b = sum_j r_bj y_j, and rho_w depends on them through F */
+    for (int64_t k = 0; k < NV; ++k) {
+      double vn = 0.0;
+      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      if (vn > 0.0) continue;
+      double l0 = lb[k] + mu * (-vn) / N;
+      for (int s = 0; s < cnt[b]; ++s) {
+        int64_t slot = b * cap + s;
+        int32_t j = col[slot];
+        if (kind[j] != 0) continue;
+        lamy[(int64_t)j * row + k] += recon[slot] * l0;
+        if (nc == 2) lamy[(int64_t)j * row + NV + k] += recon[slot] * lb[NV + k];
+      }
+    }
+  }
+
+  /* relaxation, backward, at interior points */
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != 0) continue;
+    const double* fti = ft + i * row;
+    const double* ly = lamy + i * row;
+    double* lf = lamft + i * row;
+    double rho, U[3] = {0.0, 0.0, 0.0}, T;
+    or_moments_point(p, fti, &rho, U, &T);
+    double R = rho / wv;
+    if (p->tau_mode == 2) { memcpy(lf, ly, sizeof(double) * row); continue; }
+    double tau = or_tau(p, rho, T);
+    double a = tau / (tau + p->dt), b = p->dt / (tau + p->dt);
+    double dadtau = p->dt / ((tau + p->dt) * (tau + p->dt));
+    or_maxwellian(p, rho, U, T, M);
+    /* L = sum lam_y (a ft + b M): derivatives with respect to rho, U, T, Kn */
+    double Af = 0.0, AM = 0.0, g_rho = 0.0, g_U[3] = {0.0, 0.0, 0.0}, g_T = 0.0;
+    for (int64_t k = 0; k < NV; ++k) {
+      double c2 = 0.0;
+      for (int d = 0; d < dim; ++d) { double c = vel[k * dim + d] - U[d]; c2 += c * c; }
+      double m0 = M[k];
+      for (int q = 0; q < nc; ++q) { Af += ly[q * NV + k] * fti[q * NV + k]; AM += ly[q * NV + k] * M[q * NV + k]; }
+      double lm = ly[k] + (nc == 2 ? T * ly[NV + k] : 0.0); /* M_1 = T M_0 */
+      g_rho += b * lm * m0 / rho;
+      for (int d = 0; d < dim; ++d) g_U[d] += b * lm * m0 * (vel[k * dim + d] - U[d]) / T;
+      g_T += b * lm * m0 * (c2 / (2.0 * T * T) - Dm / (2.0 * T));
+      if (nc == 2) g_T += b * ly[NV + k] * m0;
+    }
+    double dLda = Af - AM;
+    if (p->tau_mode == 0) {
+      g_rho += dLda * dadtau * (-tau / rho);
+      g_T += dLda * dadtau * (-tau / (2.0 * T));
+    }
+    dtheta[3] += dLda * dadtau * tau / p->kn;
+    /* chain to ft through rho = wv R, U = M/R, T = (E - R|U|^2)/(3R) */
+    for (int64_t k = 0; k < NV; ++k) {
+      double c2 = 0.0, gu = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        double c = vel[k * dim + d] - U[d];
+        c2 += c * c;
+        gu += g_U[d] * c / R;
+      }
+      lf[k] = a * ly[k] + g_rho * wv + gu + g_T * (c2 - 3.0 * T) / (3.0 * R);
+      if (nc == 2) lf[NV + k] = a * ly[NV + k] + g_T / (3.0 * R);
+    }
+  }
+
+  /* transport, backward: ft_i = f_i (1 + dt sum_j K_ij) - dt sum_j K_ij f_j, scattered */
+  memset(lam0, 0, sizeof(double) * n * row);
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != 0) continue;
+    for (int64_t k = 0; k < NV; ++k) {
+      double c[3] = {0.0, 0.0, 0.0};
+      for (int a = 0; a < dim; ++a) c[a] = vel[k * dim + a];
+      for (int s = 0; s < cnt[i]; ++s) {
+        int64_t slot = i * cap + s;
+        int64_t j = col[slot];
+        double K = upwind_coef(dim, abar + slot * dim, frame + slot * dim * dim, c);
+        for (int q = 0; q < nc; ++q) {
+          double l = lamft[i * row + q * NV + k];
+          lam0[i * row + q * NV + k] += p->dt * K * l;
+          lam0[j * row + q * NV + k] -= p->dt * K * l;
+        }
+      }
+      for (int q = 0; q < nc; ++q) lam0[i * row + q * NV + k] += lamft[i * row + q * NV + k];
+    }
+  }
+  free(vel); free(ft); free(y); free(lamy); free(lamft); free(Mw); free(M);
+  return OR_OK;
+}
+
+/* Objective of one state: the x-momentum flux through the lid plane averaged over the
+ * lid points, J = (1/|lid|) sum_{b in lid} sum_k v_x v_n g_b(v_k) dv^dim (v_n the last
+ * velocity component, normal to the lid); lam += scale dJ/df when lam is not NULL. */
+double or_objective(const or_params* p, int64_t n, const int32_t* kind, const double* f, double* lam, double scale) {
+  int dim = p->dim;
+  int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
+  double wv = quad_weight(p);
+  double* vel = (double*)malloc(sizeof(double) * NV * dim);
+  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  int64_t nlid = 0;
+  for (int64_t b = 0; b < n; ++b) nlid += kind[b] == p->lid_wall;
+  double J = 0.0;
+  for (int64_t b = 0; b < n && nlid > 0; ++b) {
+    if (kind[b] != p->lid_wall) continue;
+    for (int64_t k = 0; k < NV; ++k) {
+      double w = vel[k * dim] * vel[k * dim + dim - 1] * wv / (double)nlid;
+      J += w * f[b * row + k];
+      if (lam) lam[b * row + k] += scale * w;
+    }
+  }
+  free(vel);
+  return J;
+}
+
 /* ---- full time steps ---- */
 
 /* nsteps steps in place on (x, f, rho, U, T).  rho/U/T hold the moments of the

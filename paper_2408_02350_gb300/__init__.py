@@ -22,7 +22,7 @@ BGK_OK, BGK_E_INVAL, BGK_E_NOMEM, BGK_E_CUDA, BGK_E_SINGULAR = 0, 1, 2, 3, 4
 BGK_E_NBR_OVERFLOW, BGK_E_NONFINITE, BGK_E_TIMEOUT, BGK_E_STATE = 5, 6, 7, 8
 BGK_F64, BGK_F32, BGK_BF16 = 0, 1, 2
 STORAGE = {"f64": BGK_F64, "f32": BGK_F32, "bf16": BGK_BF16}
-K_TRANSPORT, K_WALLS, K_NBR, K_STENCIL, K_MOVE = 0, 1, 2, 3, 4
+K_TRANSPORT, K_WALLS, K_NBR, K_STENCIL, K_MOVE, K_ADJOINT = 0, 1, 2, 3, 4, 5
 
 _STATUS_NAMES = {1: "BGK_E_INVAL", 2: "BGK_E_NOMEM", 3: "BGK_E_CUDA", 4: "BGK_E_SINGULAR",
                  5: "BGK_E_NBR_OVERFLOW", 6: "BGK_E_NONFINITE", 7: "BGK_E_TIMEOUT", 8: "BGK_E_STATE"}
@@ -74,6 +74,9 @@ _SIGS = {
     "bgk_get_stats": (C.c_int, [_P, C.POINTER(bgk_stats)]),
     "bgk_last_error": (C.c_char_p, [_P]),
     "bgk_free": (None, [_P]),
+    "bgk_set_params": (C.c_int, [_P, C.c_int32, C.POINTER(bgk_params)]),
+    "bgk_objective": (C.c_int, [_P, C.c_int32, _P, _P, C.c_double, _P]),
+    "bgk_adjoint_step": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "bgk_neighbours_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
                                          C.c_int32, _P]),
 }
@@ -235,6 +238,21 @@ def bgk_last_error(ctx) -> str:
 
 def bgk_free(ctx) -> None:
     lib().bgk_free(ctx)
+
+
+def bgk_set_params(ctx, case: int, params) -> None:
+    q = params if isinstance(params, bgk_params) else params_from(params)
+    _check(lib().bgk_set_params(ctx, case, C.byref(q)), ctx)
+
+
+def bgk_objective(ctx, case: int, J=None, lam=None, scale: float = 1.0, stream=None) -> None:
+    """J (device float64 tensor of one element) += lid flux; lam (device, internal layout) += scale dJ/df."""
+    _check(lib().bgk_objective(ctx, case, _ptr(J) if J is not None else None, _ptr(lam) if lam is not None else None,
+                               scale, _stream_ptr(stream)), ctx)
+
+
+def bgk_adjoint_step(ctx, case: int, lam_in, lam_out, dtheta, stream=None) -> None:
+    _check(lib().bgk_adjoint_step(ctx, case, _ptr(lam_in), _ptr(lam_out), _ptr(dtheta), _stream_ptr(stream)), ctx)
 
 
 def bgk_neighbours_noalloc(dim: int, n: int, x, h: float, periodic: int, cap: int, cnt, col, check: int = 1,

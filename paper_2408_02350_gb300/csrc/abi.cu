@@ -38,6 +38,15 @@ struct CaseHost {
   int cur;
   bool stencils_valid;
   size_t s_bytes, c_bytes;  // storage and compute element sizes
+  // discrete adjoint (allocated on first use)
+  void* adj_ft = nullptr;
+  void* adj_y = nullptr;
+  void* adj_lft = nullptr;
+  double* adj_wmu = nullptr;
+  int32_t* tslot = nullptr;
+  int32_t* wall_of = nullptr;
+  bool tslot_valid = false;
+  int32_t nlid = 0;
 };
 
 }  // namespace
@@ -51,8 +60,8 @@ struct bgk_ctx {
   bool timing = false;
   std::vector<EvPair> ev;
   size_t ev_used = 0;
-  double t_ms[K_COUNT] = {0, 0, 0, 0, 0};
-  int64_t t_n[K_COUNT] = {0, 0, 0, 0, 0};
+  double t_ms[K_COUNT] = {0, 0, 0, 0, 0, 0};
+  int64_t t_n[K_COUNT] = {0, 0, 0, 0, 0, 0};
   void* staging = nullptr;
   size_t staging_bytes = 0;
 };
@@ -188,6 +197,7 @@ int build_lists(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
   CKL(ctx);
   if ((st = timed_end(ctx, e, s))) return st;
   c.stencils_valid = true;
+  c.tslot_valid = false;
   return BGK_OK;
 }
 
@@ -268,6 +278,13 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     if (q.periodic && !wall.empty()) return bail(fail(ctx, BGK_E_INVAL, "case %d: periodic box with wall points", ci));
     v.n_int = (int32_t)inner.size();
     v.n_wall = (int32_t)wall.size();
+    c.nlid = 0;
+    for (int64_t i = 0; i < n; ++i) c.nlid += kind[off + i] == q.lid_wall && q.lid_wall != 0;
+    std::vector<int32_t> wall_of(n, -1);
+    for (size_t w = 0; w < wall.size(); ++w) wall_of[wall[w]] = (int32_t)w;
+    if ((st = dalloc(ctx, &c.wall_of, n))) return bail(st);
+    if (cudaMemcpy(c.wall_of, wall_of.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(ctx, BGK_E_CUDA, "case %d: wall map upload failed", ci));
 
     double* dx = nullptr;
     int32_t *dkind = nullptr, *dint = nullptr, *dwall = nullptr;
@@ -578,6 +595,76 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
     c.stencils_valid = false;
   }
   ctx->steps = (int64_t)hdr[3];
+  return BGK_OK;
+}
+
+int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
+  if (!ctx || !p || ci < 0 || ci >= (int)ctx->cases.size())
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_set_params: bad argument") : BGK_E_INVAL;
+  CaseHost& c = ctx->cases[ci];
+  const bgk_params& o = c.p;
+  const char* why = nullptr;
+  if (!check_params(*p, c.cv.n, &why)) return fail(ctx, BGK_E_INVAL, "bgk_set_params: %s", why);
+  if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
+      p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic)
+    return fail(ctx, BGK_E_INVAL, "bgk_set_params: only kn, tau_mode, dt, wall_T, lid_u, lid_wall, ale, guard may change");
+  CK(ctx, cudaDeviceSynchronize());
+  c.p = *p;
+  CaseView& v = c.cv;
+  v.kn = p->kn;
+  v.tau_mode = p->tau_mode;
+  v.dt = p->dt;
+  v.wall_T = p->wall_T;
+  v.lid_wall = p->lid_wall;
+  v.ale = p->ale;
+  v.guard = p->guard;
+  for (int a = 0; a < 3; ++a) v.lid_u[a] = p->lid_u[a];
+  refresh_view(c);
+  ctx->launches += launch_init_tables(v, 0);
+  CKL(ctx);
+  CK(ctx, cudaDeviceSynchronize());
+  return BGK_OK;
+}
+
+int bgk_objective(bgk_ctx* ctx, int32_t ci, double* J, void* lam, double scale, void* stream) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size())
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_objective: bad argument") : BGK_E_INVAL;
+  CaseHost& c = ctx->cases[ci];
+  refresh_view(c);
+  ctx->launches += launch_objective(c.cv, c.nlid, J, lam, scale, (cudaStream_t)stream);
+  CKL(ctx);
+  return BGK_OK;
+}
+
+int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out, double* dtheta, void* stream) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !lam_in || !lam_out || !dtheta || lam_in == lam_out)
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_adjoint_step: bad argument") : BGK_E_INVAL;
+  CaseHost& c = ctx->cases[ci];
+  if (c.cv.ale) return fail(ctx, BGK_E_STATE, "bgk_adjoint_step: the adjoint is for fixed points (ale = 0)");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  refresh_view(c);
+  if (!c.stencils_valid && (st = build_lists(ctx, c, s))) return st;
+  const size_t fl = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.c_bytes;
+  if (!c.adj_ft) {
+    if ((st = dalloc_bytes(ctx, &c.adj_ft, fl))) return st;
+    if ((st = dalloc_bytes(ctx, &c.adj_y, fl))) return st;
+    if ((st = dalloc_bytes(ctx, &c.adj_lft, fl))) return st;
+    if ((st = dalloc(ctx, &c.adj_wmu, std::max<int64_t>(c.cv.n_wall, 1)))) return st;
+    if ((st = dalloc(ctx, &c.tslot, (size_t)c.cv.n * c.cv.cap))) return st;
+    CK(ctx, cudaMemset(c.adj_lft, 0, fl));
+  }
+  if (!c.tslot_valid) {
+    ctx->launches += launch_tslot(c.cv, c.tslot, s);
+    CKL(ctx);
+    c.tslot_valid = true;
+  }
+  EvPair* e;
+  if ((st = timed_begin(ctx, K_ADJOINT, s, &e))) return st;
+  ctx->launches += launch_adjoint(c.cv, lam_in, lam_out, dtheta, c.adj_ft, c.adj_y, c.adj_lft, c.adj_wmu, c.tslot,
+                                  c.wall_of, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
   return BGK_OK;
 }
 

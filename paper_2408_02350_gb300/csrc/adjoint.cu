@@ -1,0 +1,511 @@
+// Discrete adjoint of one time step (fixed points) and the lid-flux objective.
+//
+// The step map f^{n+1} = Phi(f^n; u_lid, Kn) of the forward kernels is
+//   f~ = L f            positive upwind transport, linear for fixed points
+//   y  = a f~ + b M     relaxation, (rho, U, T) = moments(f~), a = tau/(tau+dt), b = 1 - a
+//   f^{n+1} = [y at interior points; W(y) at wall points]
+// with W the WLS reconstruction of arriving velocities and rho_w M_w on leaving
+// ones, rho_w = F / N (F the arriving normal mass flux, N the normalisation of
+// the unit-density wall Maxwellian, which depends on u_lid).  Given the state
+// f^n and lam1 = dJ/df^{n+1}, one adjoint step computes lam0 = (dPhi/df^n)^T lam1
+// and adds dJ/du_lid and dJ/dKn to a device accumulator, in four kernels:
+//   k_adj_prep       recompute f~ and y from f^n (interior points)
+//   k_adj_walls      per wall point: mu = dJ/drho_w and the lid-velocity derivative
+//   k_adj_relax      per interior point: lam_y = lam1 + wall terms, then the VJP of
+//                    the relaxation through rho, U, T, tau and M (Kn derivative)
+//   k_adj_transport  lam0 = L^T lam_f~ as a gather: the neighbour relation is
+//                    symmetric, and tslot[p][t] is the slot of p in the row of its
+//                    t-th neighbour, so each point sums its own contributions.
+#include <cuda_runtime.h>
+
+#include "bgk_internal.cuh"
+#include "device_common.cuh"
+
+namespace bgk {
+
+namespace {
+constexpr int RED = 16 * 32;  // doubles of block-reduction scratch (16 values x 32 warps)
+
+inline int grid_for(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+template <int NVAL>
+__device__ __forceinline__ void block_reduce(double (&v)[NVAL], double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NVAL; ++q) {
+    double s = warp_sum(v[q]);
+    if (lane == 0) scratch[q * 32 + warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NVAL) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += scratch[threadIdx.x * 32 + w];
+    scratch[threadIdx.x * 32] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NVAL; ++q) v[q] = scratch[q * 32];
+  __syncthreads();
+}
+
+template <typename C> __device__ __forceinline__ C cmin(C a, C b) { return a < b ? a : b; }
+__device__ __forceinline__ float cexp(float x) { return expf(x); }
+__device__ __forceinline__ double cexp(double x) { return exp(x); }
+
+// velocity components of node k
+template <int DIM>
+__device__ __forceinline__ void vel_of(int k, int nv, const double* nodes, double (&v)[DIM]) {
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { v[a] = nodes[k % nv]; k /= nv; }
+}
+}  // namespace
+
+// transpose slot map: tslot[p][t] = position of p in the row of col[p][t] (-1 if absent)
+__global__ void k_tslot(CaseView cv, int32_t* tslot) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= cv.n) return;
+  const int cap = cv.cap, m = cv.cnt[p];
+  for (int t = 0; t < m; ++t) {
+    const int i = cv.col[(int64_t)p * cap + t];
+    const int32_t* row = cv.col + (int64_t)i * cap;
+    int lo = 0, hi = cv.cnt[i] - 1, pos = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int v = row[mid];
+      if (v == p) { pos = mid; break; }
+      if (v < p) lo = mid + 1; else hi = mid - 1;
+    }
+    tslot[(int64_t)p * cap + t] = pos;
+  }
+}
+
+// f~ and y = relax(f~) at interior points (compute type C, internal layout)
+template <typename S, typename C, int DIM>
+__global__ void __launch_bounds__(256) k_adj_prep(CaseView cv, C* FT, C* Y) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int DD = DIM * DIM;
+  __shared__ double s_red[RED];
+  __shared__ double s_nodes[64];
+  __shared__ double s_fin[8];
+  const int i = cv.int_idx[blockIdx.x];
+  const int m = cv.cnt[i], cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = cv.vnodes[t];
+  __syncthreads();
+  const S* f = reinterpret_cast<const S*>(cv.f_in);
+  const C* P = reinterpret_cast<const C*>(cv.P) + (int64_t)i * cap * DD;
+  const int32_t* row = cv.col + (int64_t)i * cap;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  const C two_dt = (C)(2.0 * cv.dt);
+  C cpart[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) cpart[q] = (C)0;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    C v[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) v[a] = (C)vd[a];
+    C acc[NC], sk = (C)0, fi[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { acc[c] = (C)0; fi[c] = ld1(f + (int64_t)i * rowlen + (int64_t)c * NVp + k); }
+    for (int s = 0; s < m; ++s) {
+      const int j = row[s];
+      C mk = (C)0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        C pd = (C)0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) pd += v[a] * P[s * DD + d * DIM + a];
+        mk += cmin(pd, (C)0);
+      }
+      sk += mk;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] += mk * ld1(f + (int64_t)j * rowlen + (int64_t)c * NVp + k);
+    }
+    C v2 = (C)0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const C ft = fi[c] - two_dt * (acc[c] - sk * fi[c]);
+      FT[(int64_t)i * rowlen + (int64_t)c * NVp + k] = ft;
+      if (c == 0) {
+        cpart[0] += ft;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) { cpart[1 + a] += v[a] * ft; v2 += v[a] * v[a]; }
+        cpart[DIM + 1] += v2 * ft;
+      } else {
+        cpart[DIM + 1] += ft;
+      }
+    }
+  }
+  double part[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) part[q] = (double)cpart[q];
+  block_reduce<DIM + 2>(part, s_red);
+  if (threadIdx.x == 0) {
+    const double R = part[0];
+    double U[3] = {0, 0, 0}, u2 = 0.0;
+    for (int a = 0; a < DIM; ++a) { U[a] = part[1 + a] / R; u2 += U[a] * U[a]; }
+    const double T = (part[DIM + 1] - R * u2) / (3.0 * R);
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double rho = R * wv, pi = 3.14159265358979323846;
+    double a = 1.0, b = 0.0;
+    if (cv.tau_mode != 2) {
+      const double tau = cv.tau_mode == 1 ? sqrt(2.0 / pi) * cv.kn : sqrt(2.0 / pi) * cv.kn / (rho * sqrt(T));
+      a = tau / (tau + cv.dt);
+      b = cv.dt / (tau + cv.dt);
+    }
+    s_fin[0] = a; s_fin[1] = b; s_fin[2] = rho; s_fin[3] = T;
+    for (int q = 0; q < 3; ++q) s_fin[4 + q] = U[q];
+  }
+  __syncthreads();
+  const C a = (C)s_fin[0], b = (C)s_fin[1], T = (C)s_fin[3];
+  const double pi = 3.14159265358979323846;
+  const C pref = (C)(DIM == 2 ? s_fin[2] / (2.0 * pi * s_fin[3]) : s_fin[2] / pow(2.0 * pi * s_fin[3], 1.5));
+  const C nl2 = (C)(-0.5 / s_fin[3]);
+  C Uc[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) Uc[d] = (C)s_fin[4 + d];
+  for (int k = threadIdx.x; k < NVp; k += blockDim.x) {
+    if (k >= NV) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) Y[(int64_t)i * rowlen + (int64_t)c * NVp + k] = (C)0;
+      continue;
+    }
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    C c2 = (C)0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) { const C cc = (C)vd[d] - Uc[d]; c2 += cc * cc; }
+    const C M0 = pref * cexp(nl2 * c2);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const C ft = FT[(int64_t)i * rowlen + (int64_t)c * NVp + k];
+      Y[(int64_t)i * rowlen + (int64_t)c * NVp + k] = a * ft + b * (c == 0 ? M0 : T * M0);
+    }
+  }
+}
+
+// per wall point: wmu[w] = (dJ/drho_w) / N, and the lid-velocity derivative (lid points)
+template <typename C, int DIM>
+__global__ void __launch_bounds__(256) k_adj_walls(CaseView cv, const C* Y, const C* lam1, double* wmu, double* dtheta) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  __shared__ double s_red[RED];
+  __shared__ double s_nodes[64];
+  __shared__ double s_F;
+  const int w = blockIdx.x;
+  const int b = cv.wall_idx[w];
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = cv.vnodes[t];
+  __syncthreads();
+  const int8_t* cls = cv.wcls + (int64_t)w * NVp;
+  const C* vn = reinterpret_cast<const C*>(cv.wvn) + (int64_t)w * NVp;
+  const bool lid = cv.kind[b] == cv.lid_wall;
+  const C* Mw = reinterpret_cast<const C*>(cv.mw) + (lid ? NVp : 0);
+  const C* R = reinterpret_cast<const C*>(cv.recon) + (int64_t)b * cap;
+  const int32_t* row = cv.col + (int64_t)b * cap;
+  const int m = cv.cnt[b];
+  const double invN = cv.winv[w], Tw = cv.wall_T;
+  double uw[3] = {0, 0, 0};
+  if (lid)
+    for (int a = 0; a < DIM; ++a) uw[a] = cv.lid_u[a];
+  // F = sum over arriving velocities of |v.n| g_b, g_b = sum_j r_bj y_j
+  double acc[1 + 2 * DIM + 1];
+  for (int q = 0; q < 2 + 2 * DIM; ++q) acc[q] = 0.0;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    if (cls[k] != 0) continue;
+    double g = 0.0;
+    for (int s = 0; s < m; ++s) {
+      const int j = row[s];
+      if (cv.kind[j] != 0) continue;
+      g += (double)R[s] * (double)Y[(int64_t)j * rowlen + k];
+    }
+    acc[0] += (double)vn[k] * g;
+  }
+  // mu = sum_{leaving} sum_c lam_c Mw_c ; du_a and dN_a for the lid
+  const C* lb = lam1 + (int64_t)b * rowlen;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    if (cls[k] == 0) continue;
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    const double m0 = (double)Mw[k];
+    double lm = (double)lb[k] * m0;
+    if (NC == 2) lm += (double)lb[NVp + k] * Tw * m0;
+    acc[1] += lm;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const double ca = (vd[a] - uw[a]) / Tw;
+      acc[2 + a] += lm * ca;                         // sum lam_c Mw_c (v_a - u_a)/T
+      acc[2 + DIM + a] += (double)vn[k] * m0 * ca;   // dN/du_a
+    }
+  }
+  block_reduce<2 + 2 * DIM>(acc, s_red);
+  if (threadIdx.x == 0) {
+    const double F = acc[0], mu = acc[1], rho_w = F * invN;
+    wmu[w] = mu * invN;
+    if (lid)
+      for (int a = 0; a < DIM; ++a) atomicAdd(&dtheta[a], rho_w * acc[2 + a] - mu * rho_w * invN * acc[2 + DIM + a]);
+  }
+  (void)s_F;
+}
+
+// per interior point: lam_f~ = VJP of the relaxation applied to lam_y
+template <typename C, int DIM>
+__global__ void __launch_bounds__(256) k_adj_relax(CaseView cv, const C* FT, const C* lam1, const double* wmu,
+                                                   const int32_t* tslot, const int32_t* wall_of, C* LFT, double* dtheta) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  __shared__ double s_red[RED];
+  __shared__ double s_nodes[64];
+  __shared__ double s_fin[16];
+  const int i = cv.int_idx[blockIdx.x];
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp, m = cv.cnt[i];
+  const int64_t rowlen = (int64_t)NC * NVp;
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = cv.vnodes[t];
+  __syncthreads();
+  const C* ft = FT + (int64_t)i * rowlen;
+  // moments of f~
+  C cpart[DIM + 2];
+  for (int q = 0; q < DIM + 2; ++q) cpart[q] = (C)0;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    C v2 = (C)0;
+    const C g = ft[k];
+    cpart[0] += g;
+    for (int a = 0; a < DIM; ++a) { cpart[1 + a] += (C)vd[a] * g; v2 += (C)(vd[a] * vd[a]); }
+    cpart[DIM + 1] += v2 * g;
+    if (NC == 2) cpart[DIM + 1] += ft[NVp + k];
+  }
+  double part[DIM + 2];
+  for (int q = 0; q < DIM + 2; ++q) part[q] = (double)cpart[q];
+  block_reduce<DIM + 2>(part, s_red);
+  const double pi = 3.14159265358979323846;
+  if (threadIdx.x == 0) {
+    const double R = part[0];
+    double U[3] = {0, 0, 0}, u2 = 0.0;
+    for (int a = 0; a < DIM; ++a) { U[a] = part[1 + a] / R; u2 += U[a] * U[a]; }
+    const double T = (part[DIM + 1] - R * u2) / (3.0 * R);
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double rho = R * wv;
+    double tau = 0.0, a = 1.0, b = 0.0, dadtau = 0.0;
+    if (cv.tau_mode != 2) {
+      tau = cv.tau_mode == 1 ? sqrt(2.0 / pi) * cv.kn : sqrt(2.0 / pi) * cv.kn / (rho * sqrt(T));
+      a = tau / (tau + cv.dt);
+      b = cv.dt / (tau + cv.dt);
+      dadtau = cv.dt / ((tau + cv.dt) * (tau + cv.dt));
+    }
+    s_fin[0] = R; s_fin[1] = T; s_fin[2] = rho; s_fin[3] = tau; s_fin[4] = a; s_fin[5] = b; s_fin[6] = dadtau;
+    s_fin[7] = DIM == 2 ? rho / (2.0 * pi * T) : rho / pow(2.0 * pi * T, 1.5);
+    for (int q = 0; q < 3; ++q) s_fin[8 + q] = U[q];
+  }
+  __syncthreads();
+  const C T = (C)s_fin[1], pref = (C)s_fin[7], nl2 = (C)(-0.5 / s_fin[1]);
+  C U[DIM];
+  for (int d = 0; d < DIM; ++d) U[d] = (C)s_fin[8 + d];
+  // lam_y = lam1 + contributions of wall neighbours through their reconstruction; sums for the VJP
+  const C* l1 = lam1 + (int64_t)i * rowlen;
+  C* lf = LFT + (int64_t)i * rowlen;
+  C cs[5 + DIM];  // Af, AM, Sm, Smc2, Sl1, Smc[DIM]
+  for (int q = 0; q < 5 + DIM; ++q) cs[q] = (C)0;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    C ly[NC];
+    for (int c = 0; c < NC; ++c) ly[c] = l1[(int64_t)c * NVp + k];
+    for (int t = 0; t < m; ++t) {
+      const int bpt = cv.col[(int64_t)i * cap + t];
+      const int w = wall_of[bpt];
+      if (w < 0) continue;
+      if (cv.wcls[(int64_t)w * NVp + k] != 0) continue;  // leaving velocity of b: not reconstructed
+      const int s = tslot[(int64_t)i * cap + t];
+      if (s < 0) continue;
+      const C r = reinterpret_cast<const C*>(cv.recon)[(int64_t)bpt * cap + s];
+      const C* lb = lam1 + (int64_t)bpt * rowlen;
+      ly[0] += r * (lb[k] + (C)wmu[w] * reinterpret_cast<const C*>(cv.wvn)[(int64_t)w * NVp + k]);
+      if (NC == 2) ly[NC - 1] += r * lb[NVp + k];
+    }
+    for (int c = 0; c < NC; ++c) lf[(int64_t)c * NVp + k] = ly[c];
+    if (cv.tau_mode == 2) continue;
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    C c2 = (C)0;
+    for (int d = 0; d < DIM; ++d) { const C cc = (C)vd[d] - U[d]; c2 += cc * cc; }
+    const C M0 = pref * cexp(nl2 * c2);
+    cs[0] += ly[0] * ft[k];
+    cs[1] += ly[0] * M0;
+    if (NC == 2) {
+      cs[0] += ly[NC - 1] * ft[NVp + k];
+      cs[1] += ly[NC - 1] * T * M0;
+    }
+    const C lm = ly[0] + (NC == 2 ? T * ly[NC - 1] : (C)0);
+    cs[2] += lm * M0;
+    cs[3] += lm * M0 * c2;
+    if (NC == 2) cs[4] += ly[NC - 1] * M0;
+    for (int d = 0; d < DIM; ++d) cs[5 + d] += lm * M0 * ((C)vd[d] - U[d]);
+  }
+  if (cv.tau_mode == 2) return;  // lam_f~ = lam_y already written
+  double sums[5 + DIM];
+  for (int q = 0; q < 5 + DIM; ++q) sums[q] = (double)cs[q];
+  block_reduce<5 + DIM>(sums, s_red);
+  if (threadIdx.x == 0) {
+    const double R = s_fin[0], Td = s_fin[1], rho = s_fin[2], tau = s_fin[3], b = s_fin[5], dadtau = s_fin[6];
+    const double Dm = DIM == 2 ? 2.0 : 3.0;
+    const double dLda = sums[0] - sums[1];
+    double g_rho = b * sums[2] / rho;
+    double g_T = b * (sums[3] / (2.0 * Td * Td) - Dm * sums[2] / (2.0 * Td)) + b * sums[4];
+    if (cv.tau_mode == 0) {
+      g_rho += dLda * dadtau * (-tau / rho);
+      g_T += dLda * dadtau * (-tau / (2.0 * Td));
+    }
+    atomicAdd(&dtheta[3], dLda * dadtau * tau / cv.kn);
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    s_fin[12] = g_rho * wv - g_T * Td / R;  // constant part: g_rho wv - 3 T g_T / (3R)
+    s_fin[13] = g_T / (3.0 * R);            // coefficient of |v - U|^2, and the h term
+    for (int d = 0; d < DIM; ++d) s_red[d] = b * sums[5 + d] / Td / R;  // g_U_d / R
+  }
+  __syncthreads();
+  const C a = (C)s_fin[4], k0 = (C)s_fin[12], kc2 = (C)s_fin[13];
+  C gu[DIM];
+  for (int d = 0; d < DIM; ++d) gu[d] = (C)s_red[d];
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    C c2 = (C)0, g = k0;
+    for (int d = 0; d < DIM; ++d) {
+      const C cc = (C)vd[d] - U[d];
+      c2 += cc * cc;
+      g += gu[d] * cc;
+    }
+    const C ly0 = lf[k];
+    lf[k] = a * ly0 + g + kc2 * c2;
+    if (NC == 2) lf[NVp + k] = a * lf[NVp + k] + kc2;
+  }
+}
+
+// lam0 = L^T lam_f~ (gather over the symmetric neighbour relation)
+template <typename C, int DIM>
+__global__ void __launch_bounds__(256) k_adj_transport(CaseView cv, const C* LFT, const int32_t* tslot, C* lam0) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int DD = DIM * DIM;
+  __shared__ double s_nodes[64];
+  const int p = blockIdx.x;
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp, m = cv.cnt[p];
+  const int64_t rowlen = (int64_t)NC * NVp;
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = cv.vnodes[t];
+  __syncthreads();
+  const bool interior = cv.kind[p] == 0;
+  const C* Pall = reinterpret_cast<const C*>(cv.P);
+  const C two_dt = (C)(2.0 * cv.dt);
+  for (int k = threadIdx.x; k < NVp; k += blockDim.x) {
+    if (k >= NV) {
+      for (int c = 0; c < NC; ++c) lam0[(int64_t)p * rowlen + (int64_t)c * NVp + k] = (C)0;
+      continue;
+    }
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    C v[DIM];
+    for (int a = 0; a < DIM; ++a) v[a] = (C)vd[a];
+    C diag = (C)0, acc[NC];
+    for (int c = 0; c < NC; ++c) acc[c] = (C)0;
+    for (int t = 0; t < m; ++t) {
+      if (interior) {
+        const C* P = Pall + ((int64_t)p * cap + t) * DD;
+        C mk = (C)0;
+        for (int d = 0; d < DIM; ++d) {
+          C pd = (C)0;
+          for (int a = 0; a < DIM; ++a) pd += v[a] * P[d * DIM + a];
+          mk += cmin(pd, (C)0);
+        }
+        diag += mk;
+      }
+      const int i = cv.col[(int64_t)p * cap + t];
+      if (cv.kind[i] != 0) continue;
+      const int s = tslot[(int64_t)p * cap + t];
+      if (s < 0) continue;
+      const C* P = Pall + ((int64_t)i * cap + s) * DD;
+      C mk = (C)0;
+      for (int d = 0; d < DIM; ++d) {
+        C pd = (C)0;
+        for (int a = 0; a < DIM; ++a) pd += v[a] * P[d * DIM + a];
+        mk += cmin(pd, (C)0);
+      }
+      for (int c = 0; c < NC; ++c) acc[c] += mk * LFT[(int64_t)i * rowlen + (int64_t)c * NVp + k];
+    }
+    for (int c = 0; c < NC; ++c) {
+      const C l = interior ? LFT[(int64_t)p * rowlen + (int64_t)c * NVp + k] : (C)0;
+      lam0[(int64_t)p * rowlen + (int64_t)c * NVp + k] = l + two_dt * (diag * l - acc[c]);
+    }
+  }
+}
+
+// objective: J += (1/|lid|) sum_{b in lid} sum_k v_x v_n g_b dv^dim; lam += scale dJ/df
+template <typename S, typename C, int DIM>
+__global__ void __launch_bounds__(256) k_objective(CaseView cv, int nlid, double* J, C* lam, double scale) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  __shared__ double s_red[RED];
+  __shared__ double s_nodes[64];
+  const int b = cv.wall_idx[blockIdx.x];
+  if (cv.kind[b] != cv.lid_wall) return;  // uniform per block
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = cv.vnodes[t];
+  __syncthreads();
+  const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+  const S* fb = reinterpret_cast<const S*>(cv.f_in) + (int64_t)b * NC * NVp;
+  double acc[1] = {0.0};
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    double vd[DIM];
+    vel_of<DIM>(k, nv, s_nodes, vd);
+    const double wk = vd[0] * vd[DIM - 1] * wv / (double)nlid;
+    acc[0] += wk * (double)ld1(fb + k);
+    if (lam) lam[(int64_t)b * NC * NVp + k] += (C)(scale * wk);
+  }
+  block_reduce<1>(acc, s_red);
+  if (threadIdx.x == 0 && J) atomicAdd(J, acc[0]);
+}
+
+int launch_tslot(const CaseView& cv, int32_t* tslot, cudaStream_t s) {
+  k_tslot<<<grid_for(cv.n, 128), 128, 0, s>>>(cv, tslot);
+  return 1;
+}
+
+template <typename S, typename C, int DIM>
+static int adjoint_t(const CaseView& cv, const void* lam1v, void* lam0v, double* dtheta, void* FTv, void* Yv,
+                     void* LFTv, double* wmu, const int32_t* tslot, const int32_t* wall_of, cudaStream_t s) {
+  C* FT = (C*)FTv;
+  C* Y = (C*)Yv;
+  C* LFT = (C*)LFTv;
+  const C* lam1 = (const C*)lam1v;
+  C* lam0 = (C*)lam0v;
+  int n = 0;
+  if (cv.n_int > 0) { k_adj_prep<S, C, DIM><<<cv.n_int, 256, 0, s>>>(cv, FT, Y); ++n; }
+  if (cv.n_wall > 0) { k_adj_walls<C, DIM><<<cv.n_wall, 256, 0, s>>>(cv, Y, lam1, wmu, dtheta); ++n; }
+  if (cv.n_int > 0) { k_adj_relax<C, DIM><<<cv.n_int, 256, 0, s>>>(cv, FT, lam1, wmu, tslot, wall_of, LFT, dtheta); ++n; }
+  k_adj_transport<C, DIM><<<cv.n, 256, 0, s>>>(cv, LFT, tslot, lam0);
+  return n + 1;
+}
+
+int launch_adjoint(const CaseView& cv, const void* lam1, void* lam0, double* dtheta, void* FT, void* Y, void* LFT,
+                   double* wmu, const int32_t* tslot, const int32_t* wall_of, cudaStream_t s) {
+  if (cv.dim == 2) {
+    if (cv.storage == 0) return adjoint_t<double, double, 2>(cv, lam1, lam0, dtheta, FT, Y, LFT, wmu, tslot, wall_of, s);
+    if (cv.storage == 1) return adjoint_t<float, float, 2>(cv, lam1, lam0, dtheta, FT, Y, LFT, wmu, tslot, wall_of, s);
+    return adjoint_t<__nv_bfloat16, float, 2>(cv, lam1, lam0, dtheta, FT, Y, LFT, wmu, tslot, wall_of, s);
+  }
+  if (cv.storage == 0) return adjoint_t<double, double, 3>(cv, lam1, lam0, dtheta, FT, Y, LFT, wmu, tslot, wall_of, s);
+  if (cv.storage == 1) return adjoint_t<float, float, 3>(cv, lam1, lam0, dtheta, FT, Y, LFT, wmu, tslot, wall_of, s);
+  return adjoint_t<__nv_bfloat16, float, 3>(cv, lam1, lam0, dtheta, FT, Y, LFT, wmu, tslot, wall_of, s);
+}
+
+int launch_objective(const CaseView& cv, int nlid, double* J, void* lam, double scale, cudaStream_t s) {
+  if (cv.n_wall == 0 || nlid == 0) return 0;
+  if (cv.dim == 2) {
+    if (cv.storage == 0) k_objective<double, double, 2><<<cv.n_wall, 256, 0, s>>>(cv, nlid, J, (double*)lam, scale);
+    else if (cv.storage == 1) k_objective<float, float, 2><<<cv.n_wall, 256, 0, s>>>(cv, nlid, J, (float*)lam, scale);
+    else k_objective<__nv_bfloat16, float, 2><<<cv.n_wall, 256, 0, s>>>(cv, nlid, J, (float*)lam, scale);
+  } else {
+    if (cv.storage == 0) k_objective<double, double, 3><<<cv.n_wall, 256, 0, s>>>(cv, nlid, J, (double*)lam, scale);
+    else if (cv.storage == 1) k_objective<float, float, 3><<<cv.n_wall, 256, 0, s>>>(cv, nlid, J, (float*)lam, scale);
+    else k_objective<__nv_bfloat16, float, 3><<<cv.n_wall, 256, 0, s>>>(cv, nlid, J, (float*)lam, scale);
+  }
+  return 1;
+}
+
+}  // namespace bgk

@@ -80,7 +80,13 @@ int launch_unpack_f(const CaseView& cv, const void* src, void* dst, int dst_dtyp
 // destination arrays P[nnz][dim*dim], recon[nnz]; rowptr[n+1] on the device).
 int launch_stencils_csr(const CaseView& cv, const int64_t* rowptr, double* P, double* recon, cudaStream_t s);
 
+// Discrete adjoint (adjoint.cu): transpose slot map, one adjoint step, objective.
+int launch_tslot(const CaseView& cv, int32_t* tslot, cudaStream_t s);
+int launch_adjoint(const CaseView& cv, const void* lam1, void* lam0, double* dtheta, void* FT, void* Y, void* LFT,
+                   double* wmu, const int32_t* tslot, const int32_t* wall_of, cudaStream_t s);
+int launch_objective(const CaseView& cv, int nlid, double* J, void* lam, double scale, cudaStream_t s);
+
 // Kernel ids for timing.
-enum KernelId { K_TRANSPORT = 0, K_WALLS = 1, K_NBR = 2, K_STENCIL = 3, K_MOVE = 4, K_COUNT = 5 };
+enum KernelId { K_TRANSPORT = 0, K_WALLS = 1, K_NBR = 2, K_STENCIL = 3, K_MOVE = 4, K_ADJOINT = 5, K_COUNT = 6 };
 
 }  // namespace bgk
