@@ -43,6 +43,8 @@ struct CaseHost {
   void* adj_y = nullptr;
   void* adj_lft = nullptr;
   double* adj_wmu = nullptr;
+  double* adj_mom = nullptr;
+  float* adj_sk = nullptr;
   int32_t* tslot = nullptr;
   int32_t* wall_of = nullptr;
   bool tslot_valid = false;
@@ -651,6 +653,8 @@ int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out
     if ((st = dalloc_bytes(ctx, &c.adj_y, fl))) return st;
     if ((st = dalloc_bytes(ctx, &c.adj_lft, fl))) return st;
     if ((st = dalloc(ctx, &c.adj_wmu, std::max<int64_t>(c.cv.n_wall, 1)))) return st;
+    if ((st = dalloc(ctx, &c.adj_mom, (size_t)c.cv.n * MOM_STRIDE))) return st;
+    if ((st = dalloc(ctx, &c.adj_sk, (size_t)c.cv.n * c.cv.NVp))) return st;
     if ((st = dalloc(ctx, &c.tslot, (size_t)c.cv.n * c.cv.cap))) return st;
     CK(ctx, cudaMemset(c.adj_lft, 0, fl));
   }
@@ -661,8 +665,12 @@ int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out
   }
   EvPair* e;
   if ((st = timed_begin(ctx, K_ADJOINT, s, &e))) return st;
-  ctx->launches += launch_adjoint(c.cv, lam_in, lam_out, dtheta, c.adj_ft, c.adj_y, c.adj_lft, c.adj_wmu, c.tslot,
-                                  c.wall_of, s);
+  if (c.cv.storage != 1)  // FP64 and BF16 storage: generic kernels; FP32 storage: warp-per-point kernels
+    ctx->launches += launch_adjoint(c.cv, lam_in, lam_out, dtheta, c.adj_ft, c.adj_y, c.adj_lft, c.adj_wmu, c.tslot,
+                                    c.wall_of, s);
+  else
+    ctx->launches += launch_adjoint_fp32(c.cv, lam_in, lam_out, dtheta, c.adj_ft, c.adj_y, c.adj_lft, c.adj_wmu,
+                                         c.adj_mom, c.adj_sk, c.tslot, c.wall_of, s);
   CKL(ctx);
   if ((st = timed_end(ctx, e, s))) return st;
   return BGK_OK;

@@ -461,6 +461,335 @@ __global__ void __launch_bounds__(256) k_objective(CaseView cv, int nlid, double
   if (threadIdx.x == 0 && J) atomicAdd(J, acc[0]);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 path: warp-per-point adjoint kernels (lanes own 4 velocities of each
+// 128-velocity slice, as in the forward transport)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int fdiv_small_a(int k, float inv_n) { return (int)(((float)k + 0.5f) * inv_n); }
+
+template <int DIM>
+__device__ __forceinline__ void chunk_vel_a(int k0, int nv, int NV, float inv_nv, const float* s_v, float (&vel)[4][DIM],
+                                            bool (&kin)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    int kk = k0 + e;
+    kin[e] = kk < NV;
+    if (!kin[e]) kk = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int q = fdiv_small_a(kk, inv_nv);
+      vel[e][a] = s_v[kk - q * nv];
+      kk = q;
+    }
+  }
+}
+
+__device__ __forceinline__ void ld4f(const float* p, float v[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void st4f(float* p, const float v[4]) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+
+// lam_f~ at interior points from lam1, the wall terms and the relaxation VJP (FP32)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_adj_relax_wp(CaseView cv, const float* FT, const double* amom, const float* lam1,
+                                                      const double* wmu, const int32_t* tslot, const int32_t* wall_of,
+                                                      float* LFT, double* dtheta) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  float* s_v = reinterpret_cast<float*>(smem);
+  int32_t* s_wb = reinterpret_cast<int32_t*>(smem + 256) + warp * cap * 3;  // (point b, wall slot w, slot of i in b)
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = (float)cv.vnodes[q];
+  __syncthreads();
+  const int t = blockIdx.x * W + warp;
+  if (t >= cv.n_int) return;
+  const int i = cv.int_idx[t];
+  const int m = cv.cnt[i];
+  // wall neighbours of i (usually none)
+  int nwb = 0;
+  for (int q0 = 0; q0 < m; q0 += 32) {
+    const int q = q0 + lane;
+    int b = -1, w = -1, sl = -1;
+    if (q < m) {
+      b = cv.col[(int64_t)i * cap + q];
+      w = wall_of[b];
+      sl = w >= 0 ? tslot[(int64_t)i * cap + q] : -1;
+    }
+    const bool hit = w >= 0 && sl >= 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const int pos = nwb + __popc(bal & ((1u << lane) - 1u));
+      s_wb[3 * pos] = b; s_wb[3 * pos + 1] = w; s_wb[3 * pos + 2] = sl;
+    }
+    nwb += __popc(bal);
+  }
+  __syncwarp();
+  const double* mo = amom + (int64_t)i * MOM_STRIDE;
+  const float rho = (float)mo[0], T = (float)mo[4];
+  float U[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) U[a] = (float)mo[1 + a];
+  const float wv = (float)(DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
+  const float R = rho / wv;
+  float tau = 0.0f, ca = 1.0f, cb = 0.0f, dadtau = 0.0f;
+  if (cv.tau_mode != 2) {
+    const float kn = (float)cv.kn, dtf = (float)cv.dt;
+    tau = cv.tau_mode == 1 ? 0.7978845608f * kn : 0.7978845608f * kn / (rho * sqrtf(T));
+    ca = tau / (tau + dtf);
+    cb = dtf / (tau + dtf);
+    dadtau = dtf / ((tau + dtf) * (tau + dtf));
+  }
+  const float twopiT = 6.283185307f * T;
+  const float pref = DIM == 2 ? rho / twopiT : rho / (twopiT * sqrtf(twopiT));
+  const float nl2 = -0.5f / T;
+  const float inv_nv = 1.0f / (float)nv;
+  const int nchunk = NVp >> 2, nslice = (nchunk + 31) >> 5;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  const float* l1 = lam1 + (int64_t)i * rowlen;
+  const float* ft = FT + (int64_t)i * rowlen;
+  float* lf = LFT + (int64_t)i * rowlen;
+  float cs[5 + DIM];
+#pragma unroll
+  for (int q = 0; q < 5 + DIM; ++q) cs[q] = 0.0f;
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    if (chunk >= nchunk) break;
+    const int k0 = 4 * chunk;
+    float vel[4][DIM];
+    bool kin[4];
+    chunk_vel_a<DIM>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float ly[NC][4], ftv[NC][4];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { ld4f(l1 + (int64_t)c * NVp + k0, ly[c]); ld4f(ft + (int64_t)c * NVp + k0, ftv[c]); }
+    for (int q = 0; q < nwb; ++q) {
+      const int b = s_wb[3 * q], w = s_wb[3 * q + 1], slb = s_wb[3 * q + 2];
+      const float r = reinterpret_cast<const float*>(cv.recon)[(int64_t)b * cap + slb];
+      const float mu = (float)wmu[w];
+      const float* lb = lam1 + (int64_t)b * rowlen + k0;
+      const int8_t* cls = cv.wcls + (int64_t)w * NVp + k0;
+      const float* vn = reinterpret_cast<const float*>(cv.wvn) + (int64_t)w * NVp + k0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (cls[e] != 0) continue;
+        ly[0][e] += r * (lb[e] + mu * vn[e]);
+        if (NC == 2) ly[NC - 1][e] += r * lb[NVp + e];
+      }
+    }
+    if (cv.tau_mode == 2) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) st4f(lf + (int64_t)c * NVp + k0, ly[c]);
+      continue;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (!kin[e]) continue;
+      float c2 = 0.0f;
+      float cc[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) { cc[d] = vel[e][d] - U[d]; c2 = fmaf(cc[d], cc[d], c2); }
+      const float M0 = pref * __expf(nl2 * c2);
+      cs[0] = fmaf(ly[0][e], ftv[0][e], cs[0]);
+      cs[1] = fmaf(ly[0][e], M0, cs[1]);
+      float lm = ly[0][e];
+      if (NC == 2) {
+        cs[0] = fmaf(ly[NC - 1][e], ftv[NC - 1][e], cs[0]);
+        cs[1] = fmaf(ly[NC - 1][e], T * M0, cs[1]);
+        lm = fmaf(T, ly[NC - 1][e], lm);
+        cs[4] = fmaf(ly[NC - 1][e], M0, cs[4]);
+      }
+      const float lmM = lm * M0;
+      cs[2] += lmM;
+      cs[3] = fmaf(lmM, c2, cs[3]);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) cs[5 + d] = fmaf(lmM, cc[d], cs[5 + d]);
+    }
+  }
+  if (cv.tau_mode == 2) return;
+#pragma unroll
+  for (int q = 0; q < 5 + DIM; ++q) cs[q] = warp_sum(cs[q]);
+  const float Dm = DIM == 2 ? 2.0f : 3.0f;
+  const float dLda = cs[0] - cs[1];
+  float g_rho = cb * cs[2] / rho;
+  float g_T = cb * (cs[3] / (2.0f * T * T) - Dm * cs[2] / (2.0f * T)) + cb * cs[4];
+  if (cv.tau_mode == 0) {
+    g_rho += dLda * dadtau * (-tau / rho);
+    g_T += dLda * dadtau * (-tau / (2.0f * T));
+  }
+  if (lane == 0) atomicAdd(&dtheta[3], (double)(dLda * dadtau * tau) / cv.kn);
+  const float k0c = g_rho * wv - g_T * T / R, kc2 = g_T / (3.0f * R);
+  float gu[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) gu[d] = cb * cs[5 + d] / T / R;
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    if (chunk >= nchunk) break;
+    const int k0 = 4 * chunk;
+    float vel[4][DIM];
+    bool kin[4];
+    chunk_vel_a<DIM>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float ly[NC][4];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ld4f(l1 + (int64_t)c * NVp + k0, ly[c]);
+    for (int q = 0; q < nwb; ++q) {  // the wall terms of lam_y again (cheaper than storing lam_y)
+      const int b = s_wb[3 * q], w = s_wb[3 * q + 1], slb = s_wb[3 * q + 2];
+      const float r = reinterpret_cast<const float*>(cv.recon)[(int64_t)b * cap + slb];
+      const float mu = (float)wmu[w];
+      const float* lb = lam1 + (int64_t)b * rowlen + k0;
+      const int8_t* cls = cv.wcls + (int64_t)w * NVp + k0;
+      const float* vn = reinterpret_cast<const float*>(cv.wvn) + (int64_t)w * NVp + k0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (cls[e] != 0) continue;
+        ly[0][e] += r * (lb[e] + mu * vn[e]);
+        if (NC == 2) ly[NC - 1][e] += r * lb[NVp + e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float c2 = 0.0f, gsum = k0c;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const float cc = vel[e][d] - U[d];
+        c2 = fmaf(cc, cc, c2);
+        gsum = fmaf(gu[d], cc, gsum);
+      }
+      ly[0][e] = kin[e] ? fmaf(ca, ly[0][e], fmaf(kc2, c2, gsum)) : 0.0f;
+      if (NC == 2) ly[NC - 1][e] = kin[e] ? fmaf(ca, ly[NC - 1][e], kc2) : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) st4f(lf + (int64_t)c * NVp + k0, ly[c]);
+  }
+}
+
+// lam0 = L^T lam_f~ (FP32, warp per point, packed FP32x2 as in the forward transport)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_adj_transport_wp(CaseView cv, const float* LFT, const float* SK, const int32_t* tslot, float* lam0) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int DD = DIM * DIM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  float* s_v = reinterpret_cast<float*>(smem);
+  float* s_P = reinterpret_cast<float*>(smem + 256) + (size_t)warp * cap * DD;  // coefficient of p in i's stencil
+  int32_t* s_i = reinterpret_cast<int32_t*>(smem + 256 + sizeof(float) * (size_t)W * cap * DD) + warp * cap;
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = (float)cv.vnodes[q];
+  __syncthreads();
+  const int p = blockIdx.x * W + warp;
+  if (p >= cv.n) return;
+  const int m = cv.cnt[p];
+  const bool interior = cv.kind[p] == 0;
+  const float* Pall = reinterpret_cast<const float*>(cv.P);
+  // stage the transposed coefficients (coefficient of p in the stencil of neighbour i)
+  int mt = 0;
+  for (int t0 = 0; t0 < m; t0 += 32) {
+    const int t = t0 + lane;
+    int i = -1, s = -1;
+    if (t < m) {
+      i = cv.col[(int64_t)p * cap + t];
+      s = tslot[(int64_t)p * cap + t];
+    }
+    const bool use = t < m && s >= 0 && cv.kind[i] == 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, use);
+    if (use) {
+      const int pos = mt + __popc(bal & ((1u << lane) - 1u));
+      s_i[pos] = i;
+#pragma unroll
+      for (int q = 0; q < DD; ++q) s_P[pos * DD + q] = Pall[((int64_t)i * cap + s) * DD + q];
+    }
+    mt += __popc(bal);
+  }
+  __syncwarp();
+  const float inv_nv = 1.0f / (float)nv;
+  const int nchunk = NVp >> 2, nslice = (nchunk + 31) >> 5;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  const float two_dt = (float)(2.0 * cv.dt);
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    if (chunk >= nchunk) break;
+    const int k0 = 4 * chunk;
+    float vel[4][DIM];
+    bool kin[4];
+    chunk_vel_a<DIM>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float diag[4] = {0.0f, 0.0f, 0.0f, 0.0f}, acc[NC][4];
+    if (interior) ld4f(SK + (int64_t)p * NVp + k0, diag);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[c][e] = 0.0f;
+    for (int t = 0; t < mt; ++t) {
+      const int i = s_i[t];
+      float li[NC][4];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ld4f(LFT + (int64_t)i * rowlen + (int64_t)c * NVp + k0, li[c]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float mk = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          float pd = vel[e][0] * s_P[t * DD + d * DIM];
+#pragma unroll
+          for (int a = 1; a < DIM; ++a) pd = fmaf(vel[e][a], s_P[t * DD + d * DIM + a], pd);
+          mk += fminf(pd, 0.0f);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c][e] = fmaf(mk, li[c][e], acc[c][e]);
+      }
+    }
+    float own[NC][4], out[NC][4];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (interior) ld4f(LFT + (int64_t)p * rowlen + (int64_t)c * NVp + k0, own[c]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float l = interior ? own[c][e] : 0.0f;
+        out[c][e] = kin[e] ? l + two_dt * (diag[e] * l - acc[c][e]) : 0.0f;
+      }
+      st4f(lam0 + (int64_t)p * rowlen + (int64_t)c * NVp + k0, out[c]);
+    }
+  }
+}
+
+int launch_adjoint_fp32(const CaseView& cv0, const void* lam1, void* lam0, double* dtheta, void* FT, void* Y, void* LFT,
+                        double* wmu, double* amom, float* SK, const int32_t* tslot, const int32_t* wall_of, cudaStream_t s) {
+  // forward recomputation with the step's own kernel: y into Y, f~ into FT, the diagonal
+  // upwind sums into SK, moments into amom
+  CaseView cv = cv0;
+  cv.f_out = Y;
+  cv.ft_out = (float*)FT;
+  cv.sk_out = SK;
+  cv.mom = amom;
+  int n = launch_transport_fp32(cv, s);
+  const int W = 8;
+  if (cv.n_wall > 0) {
+    if (cv.dim == 2) k_adj_walls<float, 2><<<cv.n_wall, 256, 0, s>>>(cv, (const float*)Y, (const float*)lam1, wmu, dtheta);
+    else k_adj_walls<float, 3><<<cv.n_wall, 256, 0, s>>>(cv, (const float*)Y, (const float*)lam1, wmu, dtheta);
+    ++n;
+  }
+  if (cv.n_int > 0) {
+    const size_t smem = 256 + sizeof(int32_t) * (size_t)cv.cap * 3 * W;
+    const int grid = (cv.n_int + W - 1) / W;
+    if (cv.dim == 2) k_adj_relax_wp<2><<<grid, 32 * W, smem, s>>>(cv, (const float*)FT, amom, (const float*)lam1, wmu, tslot, wall_of, (float*)LFT, dtheta);
+    else k_adj_relax_wp<3><<<grid, 32 * W, smem, s>>>(cv, (const float*)FT, amom, (const float*)lam1, wmu, tslot, wall_of, (float*)LFT, dtheta);
+    ++n;
+  }
+  {
+    const int DD = cv.dim * cv.dim;
+    const size_t smem = 256 + sizeof(float) * (size_t)W * cv.cap * DD + sizeof(int32_t) * (size_t)W * cv.cap;
+    const int grid = (cv.n + W - 1) / W;
+    if (cv.dim == 2) {
+      cudaFuncSetAttribute(k_adj_transport_wp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_adj_transport_wp<2><<<grid, 32 * W, smem, s>>>(cv, (const float*)LFT, SK, tslot, (float*)lam0);
+    } else {
+      cudaFuncSetAttribute(k_adj_transport_wp<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_adj_transport_wp<3><<<grid, 32 * W, smem, s>>>(cv, (const float*)LFT, SK, tslot, (float*)lam0);
+    }
+    ++n;
+  }
+  return n;
+}
+
 int launch_tslot(const CaseView& cv, int32_t* tslot, cudaStream_t s) {
   k_tslot<<<grid_for(cv.n, 128), 128, 0, s>>>(cv, tslot);
   return 1;

@@ -59,6 +59,8 @@ struct CaseView {
 
   void* f_in;    // [n][ncomp][NVp] storage type
   void* f_out;   // [n][ncomp][NVp] storage type
+  float* ft_out; // optional [n][ncomp][NVp] copy of the transported f~ (FP32 path, adjoint recomputation)
+  float* sk_out; // optional [n][NVp] sum_j min-terms of the upwind coefficients (diagonal of the transport)
   double* mom;   // [n][MOM_STRIDE]
   DevStatus* status;
 };
@@ -68,6 +70,8 @@ int launch_init_tables(const CaseView& cv, cudaStream_t s);
 int launch_neighbours(const CaseView& cv, cudaStream_t s);
 int launch_stencils(const CaseView& cv, cudaStream_t s);
 int launch_transport(const CaseView& cv, cudaStream_t s);
+// FP32 warp-per-point transport + relaxation (used by the adjoint's forward recomputation)
+int launch_transport_fp32(const CaseView& cv, cudaStream_t s);
 int launch_walls(const CaseView& cv, cudaStream_t s);
 int launch_move(const CaseView& cv, cudaStream_t s);
 int launch_set_maxwellian(const CaseView& cv, double rho0, const double* u0, double T0, cudaStream_t s);
@@ -84,6 +88,8 @@ int launch_stencils_csr(const CaseView& cv, const int64_t* rowptr, double* P, do
 int launch_tslot(const CaseView& cv, int32_t* tslot, cudaStream_t s);
 int launch_adjoint(const CaseView& cv, const void* lam1, void* lam0, double* dtheta, void* FT, void* Y, void* LFT,
                    double* wmu, const int32_t* tslot, const int32_t* wall_of, cudaStream_t s);
+int launch_adjoint_fp32(const CaseView& cv, const void* lam1, void* lam0, double* dtheta, void* FT, void* Y, void* LFT,
+                        double* wmu, double* amom, float* SK, const int32_t* tslot, const int32_t* wall_of, cudaStream_t s);
 int launch_objective(const CaseView& cv, int nlid, double* J, void* lam, double scale, cudaStream_t s);
 
 // Kernel ids for timing.

@@ -512,6 +512,11 @@ __global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, ft[c]);
+      if (cv.ft_out) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) st4(cv.ft_out + (int64_t)i * rowlen + (int64_t)c * NVp + 4 * chunk, ft[c]);
+        st4(cv.sk_out + (int64_t)i * NVp + 4 * chunk, sk);
+      }
     }
   }
 
@@ -590,6 +595,18 @@ static void launch_transport_wp(const CaseView& cv, cudaStream_t s) {
     if (row4) BGK_LAUNCH_WP(false, true) else BGK_LAUNCH_WP(false, false)
   }
 #undef BGK_LAUNCH_WP
+}
+
+int launch_transport_fp32(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_int == 0) return 0;
+  if (cv.dim == 2) {
+    if (cv.storage == 1) launch_transport_wp<float, 2>(cv, s);
+    else launch_transport_wp<__nv_bfloat16, 2>(cv, s);
+  } else {
+    if (cv.storage == 1) launch_transport_wp<float, 3>(cv, s);
+    else launch_transport_wp<__nv_bfloat16, 3>(cv, s);
+  }
+  return 1;
 }
 
 int launch_transport(const CaseView& cv, cudaStream_t s) {
