@@ -175,6 +175,34 @@ def adjoint_cost(g, torch, stream) -> dict:
             "ms_adjoint_step": adj, "ratio": adj / fwd}
 
 
+def batched_cost(g, torch, stream, steps: int = 20) -> dict:
+    """64 independent 2D cavities (sides 41..121, 16..32 velocity nodes, FP32): batched + graph vs per case."""
+    ps = bi.batched_cases(64)
+    cls = [bi.cloud_for(p) for p in ps]
+    s = g.Solver(ps, cls)
+    s.set_maxwellian(stream=stream)
+    upd = sum(len(c["kind"]) * p["nv"] ** 2 for p, c in zip(ps, cls))
+    out = {"workload": "batched2d_64", "cases": len(ps), "updates_per_step": upd}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for mode, key in ((0, "per_case"), (2, "batched_graph")):
+        g.bgk_set_batching(s.ctx, mode)
+        if mode == 2:
+            g.bgk_autotune(s.ctx, stream)
+        s.step(3, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[key] = {"ms_per_step": ms, "value": upd / (ms * 1e-3), "unit": UNIT}
+    st = s.stats()
+    out["tuned"] = {"warps": st["batch_warps"], "grid": st["batch_grid"]}
+    s.sync(stream)
+    s.close()
+    return out
+
+
 def run_reference(args, p: dict) -> None:
     """Reference arm: the FP64 CPU oracle timed on host cores, each step a bounded sample."""
     rank, world, _ = _dist_env()
@@ -216,6 +244,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--n", type=int, default=None, help="override points per axis (profiling runs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-step cost measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-cavity batched measurement")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
     p = bi.config(args.workload, **({"n": args.n} if args.n else {}))
@@ -328,6 +357,10 @@ def main():
     if not args.no_adjoint and world == 1:
         adj = adjoint_cost(g, torch, stream)
 
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = batched_cost(g, torch, stream)
+
     # ---- roofline of the dominant kernel (transport + moments + relaxation) ----
     peaks = _peaks()
     rowptr, _ = s.get_neighbours()
@@ -361,7 +394,7 @@ def main():
                 "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": args.e2e_steps},
-                "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj}
+                "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj, "batched": batched}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, 1)
         print(json.dumps(line), flush=True)

@@ -85,6 +85,10 @@ typedef struct bgk_stats {
   int64_t nnz;            /* neighbour pairs of the last build (valid after bgk_sync) */
   int32_t nv_pad;         /* padded velocity stride of the internal f layout */
   int32_t n_cases;
+  int32_t batch_mode;     /* stepping mode in effect: 0 per case, 1 batched kernels, 2 batched kernels in a graph */
+  int32_t batch_warps;    /* warps per CTA of the batched transport (bgk_autotune) */
+  int32_t batch_grid;     /* CTAs of the persistent batched transport, 0 = one per tile (bgk_autotune) */
+  int32_t pad_;
 } bgk_stats;
 
 /* Library ABI version (BGK_ABI_VERSION). */
@@ -183,11 +187,27 @@ int bgk_objective(bgk_ctx* ctx, int32_t c, double* J, void* lam, double scale, v
  * BGK_E_STATE when ale = 1. */
 int bgk_adjoint_step(bgk_ctx* ctx, int32_t c, const void* lam_in, void* lam_out, double* dtheta, void* stream);
 
+/* How bgk_step advances several cases (not in the paper, which steps one cavity):
+ * mode 0 launches the kernels of each case in turn; mode 1 advances all cases
+ * with one persistent transport launch over a (case, point) work list and one
+ * wall launch over a (case, wall point) list; mode 2 replays those two launches
+ * from a CUDA graph captured once per buffer parity.  Modes 1 and 2 apply when
+ * every case has FP32 or BF16 storage (the same for all), fixed points and the
+ * same dimension; otherwise mode 0 is used.  mode = -1 (default) selects 2 for
+ * n_cases > 1 and 0 otherwise.  The results are the same in every mode. */
+int bgk_set_batching(bgk_ctx* ctx, int32_t mode);
+
+/* Time the batched transport for CTA sizes of 4 and 8 warps and persistent grids
+ * of {1, 2, 3, 4, 6} x the SM count (or one CTA per tile) on the current state and
+ * keep the fastest (see bgk_stats).  The state is not changed.  Synchronous. */
+int bgk_autotune(bgk_ctx* ctx, void* stream);
+
 /* Per-kernel timing with CUDA events on the launching stream: enable = 1
  * brackets every launch of the transport kernel with an event pair.
  * bgk_get_timing synchronises and returns the summed device time (ms) and
  * launch count of kernel `which` (0 = transport+relaxation, 1 = wall, 2 =
- * neighbour build, 3 = stencils, 4 = motion, 5 = adjoint step) since timing was enabled. */
+ * neighbour build, 3 = stencils, 4 = motion, 5 = adjoint step, 6 = one batched step of all cases) since
+ * timing was enabled. */
 int bgk_set_timing(bgk_ctx* ctx, int32_t enable);
 int bgk_get_timing(bgk_ctx* ctx, int32_t which, double* total_ms, int64_t* launches);
 

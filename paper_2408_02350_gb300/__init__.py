@@ -22,7 +22,7 @@ BGK_OK, BGK_E_INVAL, BGK_E_NOMEM, BGK_E_CUDA, BGK_E_SINGULAR = 0, 1, 2, 3, 4
 BGK_E_NBR_OVERFLOW, BGK_E_NONFINITE, BGK_E_TIMEOUT, BGK_E_STATE = 5, 6, 7, 8
 BGK_F64, BGK_F32, BGK_BF16 = 0, 1, 2
 STORAGE = {"f64": BGK_F64, "f32": BGK_F32, "bf16": BGK_BF16}
-K_TRANSPORT, K_WALLS, K_NBR, K_STENCIL, K_MOVE, K_ADJOINT = 0, 1, 2, 3, 4, 5
+K_TRANSPORT, K_WALLS, K_NBR, K_STENCIL, K_MOVE, K_ADJOINT, K_BATCH = 0, 1, 2, 3, 4, 5, 6
 
 _STATUS_NAMES = {1: "BGK_E_INVAL", 2: "BGK_E_NOMEM", 3: "BGK_E_CUDA", 4: "BGK_E_SINGULAR",
                  5: "BGK_E_NBR_OVERFLOW", 6: "BGK_E_NONFINITE", 7: "BGK_E_TIMEOUT", 8: "BGK_E_STATE"}
@@ -46,7 +46,8 @@ class bgk_params(C.Structure):
 
 class bgk_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("launches", C.c_int64), ("clamps", C.c_int64), ("nnz", C.c_int64),
-                ("nv_pad", C.c_int32), ("n_cases", C.c_int32)]
+                ("nv_pad", C.c_int32), ("n_cases", C.c_int32), ("batch_mode", C.c_int32), ("batch_warps", C.c_int32),
+                ("batch_grid", C.c_int32), ("pad_", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -75,6 +76,8 @@ _SIGS = {
     "bgk_last_error": (C.c_char_p, [_P]),
     "bgk_free": (None, [_P]),
     "bgk_set_params": (C.c_int, [_P, C.c_int32, C.POINTER(bgk_params)]),
+    "bgk_set_batching": (C.c_int, [_P, C.c_int32]),
+    "bgk_autotune": (C.c_int, [_P, _P]),
     "bgk_objective": (C.c_int, [_P, C.c_int32, _P, _P, C.c_double, _P]),
     "bgk_adjoint_step": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "bgk_neighbours_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
@@ -243,6 +246,14 @@ def bgk_free(ctx) -> None:
 def bgk_set_params(ctx, case: int, params) -> None:
     q = params if isinstance(params, bgk_params) else params_from(params)
     _check(lib().bgk_set_params(ctx, case, C.byref(q)), ctx)
+
+
+def bgk_set_batching(ctx, mode: int) -> None:
+    _check(lib().bgk_set_batching(ctx, mode), ctx)
+
+
+def bgk_autotune(ctx, stream=None) -> None:
+    _check(lib().bgk_autotune(ctx, _stream_ptr(stream)), ctx)
 
 
 def bgk_objective(ctx, case: int, J=None, lam=None, scale: float = 1.0, stream=None) -> None:

@@ -55,6 +55,16 @@ struct CaseHost {
 
 struct bgk_ctx {
   std::vector<CaseHost> cases;
+  // batched stepping of many cases (FP32/BF16, fixed points, one dimension)
+  int batch_mode = -1;             // -1 default (graph when eligible and n_cases > 1), 0 per case, 1 batched, 2 batched + graph
+  bool batch_ready = false;        // d_cases / items uploaded for the current parameters
+  CaseView* d_cases[2] = {nullptr, nullptr};
+  int2* d_items = nullptr;
+  int2* d_witems = nullptr;
+  int n_items = 0, n_witems = 0, capmax = 0, batch_dim = 0, batch_storage = 0;
+  int batch_warps = 8, batch_grid = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;
   std::vector<void*> allocs;
   DevStatus* status = nullptr;
   std::string err;
@@ -62,8 +72,8 @@ struct bgk_ctx {
   bool timing = false;
   std::vector<EvPair> ev;
   size_t ev_used = 0;
-  double t_ms[K_COUNT] = {0, 0, 0, 0, 0, 0};
-  int64_t t_n[K_COUNT] = {0, 0, 0, 0, 0, 0};
+  double t_ms[K_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t t_n[K_COUNT] = {0, 0, 0, 0, 0, 0, 0};
   void* staging = nullptr;
   size_t staging_bytes = 0;
 };
@@ -200,6 +210,110 @@ int build_lists(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
   if ((st = timed_end(ctx, e, s))) return st;
   c.stencils_valid = true;
   c.tslot_valid = false;
+  return BGK_OK;
+}
+
+// ---- batched stepping ----
+
+bool batch_eligible(const bgk_ctx* ctx) {
+  if (ctx->cases.empty()) return false;
+  const CaseHost& c0 = ctx->cases[0];
+  for (const CaseHost& c : ctx->cases) {
+    if (c.cv.ale || c.p.storage == 0 || c.p.storage != c0.p.storage || c.cv.dim != c0.cv.dim || c.cur != c0.cur)
+      return false;
+  }
+  return true;
+}
+
+int effective_mode(const bgk_ctx* ctx) {
+  if (!batch_eligible(ctx)) return 0;
+  if (ctx->batch_mode >= 0) return ctx->batch_mode;
+  return ctx->cases.size() > 1 ? 2 : 0;
+}
+
+void drop_graphs(bgk_ctx* ctx) {
+  for (int q = 0; q < 2; ++q)
+    if (ctx->graph[q]) {
+      cudaGraphExecDestroy(ctx->graph[q]);
+      ctx->graph[q] = nullptr;
+    }
+}
+
+void invalidate_batch(bgk_ctx* ctx) {
+  ctx->batch_ready = false;
+  drop_graphs(ctx);
+}
+
+// Upload the per-parity case descriptors and the (case, slot) work lists.
+int prepare_batch(bgk_ctx* ctx, cudaStream_t s) {
+  if (ctx->batch_ready) return BGK_OK;
+  int st;
+  for (auto& c : ctx->cases) {
+    refresh_view(c);
+    if (!c.stencils_valid && (st = build_lists(ctx, c, s))) return st;
+  }
+  const int nc = (int)ctx->cases.size();
+  if (!ctx->d_cases[0]) {
+    for (int q = 0; q < 2; ++q)
+      if ((st = dalloc(ctx, &ctx->d_cases[q], nc))) return st;
+    std::vector<int2> items, witems;
+    int capmax = 0;
+    for (int ci = 0; ci < nc; ++ci) {
+      const CaseView& v = ctx->cases[ci].cv;
+      for (int k = 0; k < v.n_int; ++k) items.push_back(make_int2(ci, k));
+      for (int k = 0; k < v.n_wall; ++k) witems.push_back(make_int2(ci, k));
+      capmax = std::max(capmax, v.cap);
+    }
+    if ((st = dalloc(ctx, &ctx->d_items, std::max<size_t>(items.size(), 1)))) return st;
+    if ((st = dalloc(ctx, &ctx->d_witems, std::max<size_t>(witems.size(), 1)))) return st;
+    CK(ctx, cudaMemcpy(ctx->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->d_witems, witems.data(), sizeof(int2) * witems.size(), cudaMemcpyHostToDevice));
+    ctx->n_items = (int)items.size();
+    ctx->n_witems = (int)witems.size();
+    ctx->capmax = capmax;
+    ctx->batch_dim = ctx->cases[0].cv.dim;
+    ctx->batch_storage = ctx->cases[0].p.storage;
+  }
+  std::vector<CaseView> views(nc);
+  for (int q = 0; q < 2; ++q) {
+    for (int ci = 0; ci < nc; ++ci) {
+      CaseHost& c = ctx->cases[ci];
+      views[ci] = c.cv;
+      views[ci].f_in = c.f[q];
+      views[ci].f_out = c.f[1 - q];
+    }
+    CK(ctx, cudaMemcpyAsync(ctx->d_cases[q], views.data(), sizeof(CaseView) * nc, cudaMemcpyHostToDevice, s));
+  }
+  CK(ctx, cudaStreamSynchronize(s));
+  ctx->batch_ready = true;
+  return BGK_OK;
+}
+
+int launch_batch_step(bgk_ctx* ctx, int parity, cudaStream_t s) {
+  ctx->launches += launch_transport_batch(ctx->d_cases[parity], ctx->d_items, ctx->n_items, ctx->batch_dim,
+                                          ctx->batch_storage, ctx->capmax, ctx->batch_warps, ctx->batch_grid, s);
+  ctx->launches += launch_walls_batch(ctx->d_cases[parity], ctx->d_witems, ctx->n_witems, ctx->batch_dim,
+                                      ctx->batch_storage, ctx->capmax, s);
+  CKL(ctx);
+  return BGK_OK;
+}
+
+int capture_graphs(bgk_ctx* ctx) {
+  if (ctx->graph[0] && ctx->graph[1]) return BGK_OK;
+  if (!ctx->cap_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  for (int q = 0; q < 2; ++q) {
+    cudaGraph_t g = nullptr;
+    CK(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = ctx->launches;
+    int st = launch_batch_step(ctx, q, ctx->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->launches = l0;  // counted when the graph is launched
+    if (st) return st;
+    if (e != cudaSuccess) return fail(ctx, BGK_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph[q], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, BGK_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
   return BGK_OK;
 }
 
@@ -405,6 +519,7 @@ int bgk_get_f(bgk_ctx* ctx, int32_t ci, void* f, int32_t dtype, int32_t on_devic
 int bgk_neighbours(bgk_ctx* ctx, void* stream) {
   if (!ctx) return BGK_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  invalidate_batch(ctx);
   for (auto& c : ctx->cases) {
     refresh_view(c);
     int st = build_lists(ctx, c, s);
@@ -466,6 +581,28 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   EvPair* e;
+  const int mode = effective_mode(ctx);
+  if (mode >= 1 && nsteps > 0) {
+    if ((st = prepare_batch(ctx, s))) return st;
+    if (mode == 2 && (st = capture_graphs(ctx))) return st;
+    for (int step = 0; step < nsteps; ++step) {
+      const int parity = ctx->cases[0].cur;
+      if ((st = timed_begin(ctx, K_BATCH, s, &e))) return st;
+      if (mode == 2) {
+        CK(ctx, cudaGraphLaunch(ctx->graph[parity], s));
+        ctx->launches += 2;
+      } else if ((st = launch_batch_step(ctx, parity, s))) {
+        return st;
+      }
+      if ((st = timed_end(ctx, e, s))) return st;
+      for (auto& c : ctx->cases) {
+        c.cur = 1 - c.cur;
+        refresh_view(c);
+      }
+      ctx->steps += 1;
+    }
+    return BGK_OK;
+  }
   for (int step = 0; step < nsteps; ++step) {
     for (auto& c : ctx->cases) {
       refresh_view(c);
@@ -589,13 +726,16 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
     CK(ctx, cudaMemcpy(c.cv.x, o, b, cudaMemcpyHostToDevice));
     o += b;
     b = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
-    CK(ctx, cudaMemcpy(c.f[c.cur], o, b, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(c.f[0], o, b, cudaMemcpyHostToDevice));
     o += b;
     b = sizeof(double) * c.cv.n * MOM_STRIDE;
     CK(ctx, cudaMemcpy(c.cv.mom, o, b, cudaMemcpyHostToDevice));
     o += b;
     c.stencils_valid = false;
+    c.cur = 0;
+    refresh_view(c);
   }
+  invalidate_batch(ctx);
   ctx->steps = (int64_t)hdr[3];
   return BGK_OK;
 }
@@ -625,6 +765,7 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   ctx->launches += launch_init_tables(v, 0);
   CKL(ctx);
   CK(ctx, cudaDeviceSynchronize());
+  invalidate_batch(ctx);
   return BGK_OK;
 }
 
@@ -676,6 +817,54 @@ int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out
   return BGK_OK;
 }
 
+int bgk_set_batching(bgk_ctx* ctx, int32_t mode) {
+  if (!ctx || mode < -1 || mode > 2) return ctx ? fail(ctx, BGK_E_INVAL, "bgk_set_batching: mode in -1..2") : BGK_E_INVAL;
+  ctx->batch_mode = mode;
+  drop_graphs(ctx);
+  return BGK_OK;
+}
+
+int bgk_autotune(bgk_ctx* ctx, void* stream) {
+  if (!ctx) return BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!batch_eligible(ctx)) return BGK_OK;  // nothing to tune: per-case launches
+  int st;
+  if ((st = prepare_batch(ctx, s))) return st;
+  int dev = 0, nsm = 0;
+  CK(ctx, cudaGetDevice(&dev));
+  CK(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int parity = ctx->cases[0].cur;
+  cudaEvent_t e0, e1;
+  CK(ctx, cudaEventCreate(&e0));
+  CK(ctx, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bw = ctx->batch_warps, bg = ctx->batch_grid;
+  const int warps_c[2] = {4, 8};
+  const int mult_c[6] = {0, 1, 2, 3, 4, 6};
+  for (int wi = 0; wi < 2; ++wi)
+    for (int mi = 0; mi < 6; ++mi) {
+      const int grid = mult_c[mi] * nsm;
+      // the transport launch reads f_in and writes f_out only, so repeating it leaves the state unchanged
+      for (int rep = 0; rep < 6; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        ctx->launches += launch_transport_batch(ctx->d_cases[parity], ctx->d_items, ctx->n_items, ctx->batch_dim,
+                                                ctx->batch_storage, ctx->capmax, warps_c[wi], grid, s);
+      }
+      cudaEventRecord(e1, s);
+      CKL(ctx);
+      CK(ctx, cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bw = warps_c[wi]; bg = grid; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->batch_warps = bw;
+  ctx->batch_grid = bg;
+  drop_graphs(ctx);
+  return BGK_OK;
+}
+
 int bgk_set_timing(bgk_ctx* ctx, int32_t enable) {
   if (!ctx) return BGK_E_INVAL;
   int st = collect_timing(ctx);
@@ -713,6 +902,9 @@ int bgk_get_stats(bgk_ctx* ctx, bgk_stats* out) {
   out->nnz = (int64_t)hs.nnz;
   out->nv_pad = ctx->cases.empty() ? 0 : ctx->cases[0].cv.NVp;
   out->n_cases = (int32_t)ctx->cases.size();
+  out->batch_mode = effective_mode(ctx);
+  out->batch_warps = ctx->batch_warps;
+  out->batch_grid = ctx->batch_grid;
   return BGK_OK;
 }
 
@@ -723,6 +915,8 @@ const char* bgk_last_error(const bgk_ctx* ctx) {
 void bgk_free(bgk_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
+  drop_graphs(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto& e : ctx->ev) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);

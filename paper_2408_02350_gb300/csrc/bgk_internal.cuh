@@ -73,6 +73,11 @@ int launch_transport(const CaseView& cv, cudaStream_t s);
 // FP32 warp-per-point transport + relaxation (used by the adjoint's forward recomputation)
 int launch_transport_fp32(const CaseView& cv, cudaStream_t s);
 int launch_walls(const CaseView& cv, cudaStream_t s);
+// Batched (many cases, one launch each): FP32/BF16 storage, all cases of one dimension.
+int launch_transport_batch(const CaseView* d_cases, const int2* items, int n_items, int dim, int storage, int capmax,
+                           int warps, int grid, cudaStream_t s);
+int launch_walls_batch(const CaseView* d_cases, const int2* witems, int n_witems, int dim, int storage, int capmax,
+                       cudaStream_t s);
 int launch_move(const CaseView& cv, cudaStream_t s);
 int launch_set_maxwellian(const CaseView& cv, double rho0, const double* u0, double T0, cudaStream_t s);
 int launch_moments(const CaseView& cv, const void* f, cudaStream_t s);
@@ -93,6 +98,6 @@ int launch_adjoint_fp32(const CaseView& cv, const void* lam1, void* lam0, double
 int launch_objective(const CaseView& cv, int nlid, double* J, void* lam, double scale, cudaStream_t s);
 
 // Kernel ids for timing.
-enum KernelId { K_TRANSPORT = 0, K_WALLS = 1, K_NBR = 2, K_STENCIL = 3, K_MOVE = 4, K_ADJOINT = 5, K_COUNT = 6 };
+enum KernelId { K_TRANSPORT = 0, K_WALLS = 1, K_NBR = 2, K_STENCIL = 3, K_MOVE = 4, K_ADJOINT = 5, K_BATCH = 6, K_COUNT = 7 };
 
 }  // namespace bgk

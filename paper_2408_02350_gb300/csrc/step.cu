@@ -351,31 +351,27 @@ __device__ __forceinline__ void chunk_velocities(int k0, int nv, int NV, float i
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 min0(float2 p) { return make_float2(fminf(p.x, 0.0f), fminf(p.y, 0.0f)); }
 
+// The per-point body, shared by the single-case kernel and the batched kernel:
+// one warp, point i of case cv; s_v, s_col, s_P are this warp's shared buffers
+// (nv, cap and cap * dim^2 entries).
 template <typename S, int DIM, bool ALE, bool ROW4>
-__global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
+__device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
+                                                   float* s_P) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   constexpr int DD = DIM * DIM;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int W = blockDim.x >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const float inv_nv = 1.0f / (float)nv;
-  float* s_v = reinterpret_cast<float*>(smem);
-  int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256) + warp * cap;
-  float* s_P = reinterpret_cast<float*>(smem + 256 + align16(sizeof(int32_t) * cap * W)) + (size_t)warp * cap * DD;
-
-  const int t = blockIdx.x * W + warp;
-  const bool active = t < cv.n_int;
-  const int i = active ? cv.int_idx[t] : 0;
-  const int m = active ? cv.cnt[i] : 0;
-  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = (float)cv.vnodes[q];
+  const bool active = true;
+  const int m = cv.cnt[i];
+  for (int q = lane; q < nv; q += 32) s_v[q] = (float)cv.vnodes[q];
   {
     const int32_t* col = cv.col + (int64_t)i * cap;
     const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
     for (int q = lane; q < m; q += 32) s_col[q] = col[q];
     for (int q = lane; q < m * DD; q += 32) s_P[q] = P[q];
   }
-  __syncthreads();
+  __syncwarp();
 
   float U[DIM];
 #pragma unroll
@@ -531,7 +527,6 @@ __global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
   const float Tn = (tot[DIM + 1] - R * u2) / (3.0f * R);
   const float wv = (float)(DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
   const float rho = R * wv;
-  if (!active) return;
   if (lane == 0) {
     double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
     mo[0] = rho;
@@ -577,10 +572,54 @@ __global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
   }
 }
 
+template <typename S, int DIM, bool ALE, bool ROW4>
+__global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
+  constexpr int DD = DIM * DIM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const int cap = cv.cap;
+  float* s_v = reinterpret_cast<float*>(smem) + warp * 64;
+  int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * cap;
+  float* s_P = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W)) + (size_t)warp * cap * DD;
+  const int t = blockIdx.x * W + warp;
+  if (t >= cv.n_int) return;
+  transport_point_wp<S, DIM, ALE, ROW4>(cv, cv.int_idx[t], s_v, s_col, s_P);
+}
+
+// Many cases in one persistent launch: items[k] = (case, interior slot), tiles of W
+// consecutive items per CTA, tiles taken in grid-stride order.  Every warp reads
+// its case's descriptor; the ROW4 / ALE variants are chosen per warp.
+template <typename S, int DIM>
+__global__ void __launch_bounds__(256, 3) k_transport_batch(const CaseView* __restrict__ cases, const int2* __restrict__ items,
+                                                             int n_items, int capmax) {
+  constexpr int DD = DIM * DIM;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  float* s_v = reinterpret_cast<float*>(smem) + warp * 64;
+  int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * capmax;
+  float* s_P = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * capmax * W)) + (size_t)warp * capmax * DD;
+  for (int tile = blockIdx.x; tile * W < n_items; tile += gridDim.x) {
+    const int it = tile * W + warp;
+    if (it >= n_items) continue;
+    const int2 e = items[it];
+    const CaseView& cv = cases[e.x];
+    const int i = cv.int_idx[e.y];
+    const bool row4 = cv.nv % 4 == 0;
+    if (cv.ale) {
+      if (row4) transport_point_wp<S, DIM, true, true>(cv, i, s_v, s_col, s_P);
+      else transport_point_wp<S, DIM, true, false>(cv, i, s_v, s_col, s_P);
+    } else {
+      if (row4) transport_point_wp<S, DIM, false, true>(cv, i, s_v, s_col, s_P);
+      else transport_point_wp<S, DIM, false, false>(cv, i, s_v, s_col, s_P);
+    }
+    __syncwarp();
+  }
+}
+
 template <typename S, int DIM>
 static void launch_transport_wp(const CaseView& cv, cudaStream_t s) {
   const int W = 8, threads = 32 * W;
-  const size_t smem = 256 + align16(sizeof(int32_t) * cv.cap * W) + sizeof(float) * cv.cap * DIM * DIM * W;
+  const size_t smem = 256 * W + align16(sizeof(int32_t) * cv.cap * W) + sizeof(float) * cv.cap * DIM * DIM * W;
   const int grid = (cv.n_int + W - 1) / W;
   const bool row4 = cv.nv % 4 == 0;
 #define BGK_LAUNCH_WP(ALE, ROW4)                                                          \
@@ -626,15 +665,14 @@ int launch_transport(const CaseView& cv, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // walls
 // ---------------------------------------------------------------------------
+// The per-wall-point body (one CTA), shared by the single-case and batched kernels.
 template <typename S, typename C, int DIM>
-__global__ void __launch_bounds__(256) k_walls(const CaseView cv) {
+__device__ __forceinline__ void walls_point(const CaseView& cv, const int w, unsigned char* smem) {
   constexpr int NC = DIM == 2 ? 2 : 1;
-  extern __shared__ __align__(16) unsigned char smem[];
   double* s_red = reinterpret_cast<double*>(smem);
   C* s_v = reinterpret_cast<C*>(smem + RED_BYTES);
   int32_t* s_j = reinterpret_cast<int32_t*>(smem + RED_BYTES + NODE_BYTES);
   C* s_r = reinterpret_cast<C*>(smem + RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)));
-  const int w = blockIdx.x;
   const int b = cv.wall_idx[w];
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   if (threadIdx.x == 0) {
@@ -721,6 +759,57 @@ __global__ void __launch_bounds__(256) k_walls(const CaseView cv) {
     mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
     if (!(rho_w >= 0.0) || !isfinite(rho_w)) set_status(cv.status, ST_NONFINITE);
   }
+}
+
+template <typename S, typename C, int DIM>
+__global__ void __launch_bounds__(256) k_walls(const CaseView cv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  walls_point<S, C, DIM>(cv, blockIdx.x, smem);
+}
+
+// witems[k] = (case, wall slot): one CTA per wall point of any case
+template <typename S, typename C, int DIM>
+__global__ void __launch_bounds__(256) k_walls_batch(const CaseView* __restrict__ cases, const int2* __restrict__ witems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int2 e = witems[blockIdx.x];
+  walls_point<S, C, DIM>(cases[e.x], e.y, smem);
+}
+
+int launch_transport_batch(const CaseView* d_cases, const int2* items, int n_items, int dim, int storage, int capmax,
+                           int warps, int grid, cudaStream_t s) {
+  if (n_items == 0) return 0;
+  const int threads = 32 * warps;
+  const int DD = dim * dim;
+  const size_t smem = 256 * warps + align16(sizeof(int32_t) * capmax * warps) + sizeof(float) * capmax * DD * warps;
+  const int ntiles = (n_items + warps - 1) / warps;
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+#define BGK_BATCH(S, D)                                                                    \
+  {                                                                                        \
+    auto k = k_transport_batch<S, D>;                                                      \
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+    k<<<grid, threads, smem, s>>>(d_cases, items, n_items, capmax);                        \
+  }
+  if (dim == 2) {
+    if (storage == 1) BGK_BATCH(float, 2) else BGK_BATCH(__nv_bfloat16, 2)
+  } else {
+    if (storage == 1) BGK_BATCH(float, 3) else BGK_BATCH(__nv_bfloat16, 3)
+  }
+#undef BGK_BATCH
+  return 1;
+}
+
+int launch_walls_batch(const CaseView* d_cases, const int2* witems, int n_witems, int dim, int storage, int capmax,
+                       cudaStream_t s) {
+  if (n_witems == 0) return 0;
+  const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (capmax + 1)) + sizeof(double) * capmax;
+  if (dim == 2) {
+    if (storage == 1) k_walls_batch<float, float, 2><<<n_witems, 256, smem, s>>>(d_cases, witems);
+    else k_walls_batch<__nv_bfloat16, float, 2><<<n_witems, 256, smem, s>>>(d_cases, witems);
+  } else {
+    if (storage == 1) k_walls_batch<float, float, 3><<<n_witems, 256, smem, s>>>(d_cases, witems);
+    else k_walls_batch<__nv_bfloat16, float, 3><<<n_witems, 256, smem, s>>>(d_cases, witems);
+  }
+  return 1;
 }
 
 int launch_walls(const CaseView& cv, cudaStream_t s) {
