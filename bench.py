@@ -57,6 +57,25 @@ def _dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_config(p: dict, rank: int, world: int) -> dict:
+    """The workload of one rank: every rank runs its own independent cavity of the same size
+    (weak scaling); with ALE the ranks take the Kn sweep 0.01 / 0.1 / 1 in turn."""
+    q = dict(p)
+    if world > 1 and q.get("ale"):
+        q["kn"] = bi.KN_SWEEP_ALE[rank % len(bi.KN_SWEEP_ALE)]
+    return q
+
+
+def reduce_max(value: float, dist, device) -> float:
+    """Maximum of a per-rank value over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -209,7 +228,7 @@ def run_reference(args, p: dict) -> None:
     if rank != 0:
         return
     import oracle
-    sample_n = 51
+    sample_n = 25
     q = bi.config(WORKLOAD, n=sample_n)
     cl = bi.cloud_for(q)
     sim = oracle.Simulation(q, cl)
@@ -247,9 +266,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-cavity batched measurement")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
-    p = bi.config(args.workload, **({"n": args.n} if args.n else {}))
-    if world > 1:
-        p["kn"] = bi.KN_SWEEP_ALE[rank % len(bi.KN_SWEEP_ALE)] if p.get("ale") else p["kn"]
+    p = rank_config(bi.config(args.workload, **({"n": args.n} if args.n else {})), rank, world)
     if args.storage:
         p["storage"] = args.storage
     if args.impl == "reference":
@@ -302,10 +319,7 @@ def main():
                   (("transport", g.K_TRANSPORT), ("walls", g.K_WALLS), ("neighbours", g.K_NBR),
                    ("stencils", g.K_STENCIL), ("move", g.K_MOVE))}
     g.bgk_set_timing(s.ctx, False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dist, "cuda")
     value = upd_per_step * args.steps * world / (ms * 1e-3)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -326,10 +340,7 @@ def main():
         g.bgk_moments(s.ctx, 0, *mom_host, stream)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(e2e_s, dist, "cuda")
     s.sync(stream)
     e2e_value = upd_per_step * args.e2e_steps * world / e2e_s
 

@@ -192,8 +192,8 @@ int bgk_adjoint_step(bgk_ctx* ctx, int32_t c, const void* lam_in, void* lam_out,
  * with one persistent transport launch over a (case, point) work list and one
  * wall launch over a (case, wall point) list; mode 2 replays those two launches
  * from a CUDA graph captured once per buffer parity.  Modes 1 and 2 apply when
- * every case has FP32 or BF16 storage (the same for all), fixed points and the
- * same dimension; otherwise mode 0 is used.  mode = -1 (default) selects 2 for
+ * every case is 2D with FP32 or BF16 storage (the same for all) and fixed points;
+ * otherwise mode 0 is used.  mode = -1 (default) selects 2 for
  * n_cases > 1 and 0 otherwise.  The results are the same in every mode. */
 int bgk_set_batching(bgk_ctx* ctx, int32_t mode);
 

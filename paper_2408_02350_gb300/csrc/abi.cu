@@ -218,6 +218,7 @@ int build_lists(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
 bool batch_eligible(const bgk_ctx* ctx) {
   if (ctx->cases.empty()) return false;
   const CaseHost& c0 = ctx->cases[0];
+  if (c0.cv.dim != 2) return false;  // the batched kernels are the 2D ones
   for (const CaseHost& c : ctx->cases) {
     if (c.cv.ale || c.p.storage == 0 || c.p.storage != c0.p.storage || c.cv.dim != c0.cv.dim || c.cur != c0.cur)
       return false;

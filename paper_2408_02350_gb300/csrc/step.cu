@@ -314,27 +314,27 @@ static void launch_transport_d(const CaseView& cv, cudaStream_t s) {
 // 1/(2n) away from an integer and the float error is below (k/n + 1) 2^-23, so truncation is exact.
 __device__ __forceinline__ int fdiv_small(int k, float inv_n) { return (int)(((float)k + 0.5f) * inv_n); }
 
-// Velocity components of the 4 velocities k0..k0+3.  With ROW4 (nv % 4 == 0, k0 % 4 == 0)
-// they share every component but the first.
-template <int DIM, bool ROW4>
+// Velocity components of the VPL velocities k0..k0+VPL-1.  With ROW (nv % VPL == 0,
+// k0 % VPL == 0) they share every component but the first.
+template <int DIM, int VPL, bool ROW>
 __device__ __forceinline__ void chunk_velocities(int k0, int nv, int NV, float inv_nv, const float* s_v,
-                                                 float (&vel)[4][DIM], bool (&kin)[4]) {
-  if (ROW4) {
+                                                 float (&vel)[VPL][DIM], bool (&kin)[VPL]) {
+  if (ROW) {
     int q = fdiv_small(k0, inv_nv);
     const int kx0 = k0 - q * nv;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) { vel[e][0] = s_v[kx0 + e]; kin[e] = k0 + e < NV; }
+    for (int e = 0; e < VPL; ++e) { vel[e][0] = s_v[kx0 + e]; kin[e] = k0 + e < NV; }
 #pragma unroll
     for (int a = 1; a < DIM; ++a) {
       const int q2 = fdiv_small(q, inv_nv);
       const float va = s_v[q - q2 * nv];
       q = q2;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) vel[e][a] = va;
+      for (int e = 0; e < VPL; ++e) vel[e][a] = va;
     }
   } else {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < VPL; ++e) {
       int kk = k0 + e;
       kin[e] = kk < NV;
       if (!kin[e]) kk = 0;
@@ -351,18 +351,30 @@ __device__ __forceinline__ void chunk_velocities(int k0, int nv, int NV, float i
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 min0(float2 p) { return make_float2(fminf(p.x, 0.0f), fminf(p.y, 0.0f)); }
 
+template <typename S, int VPL>
+__device__ __forceinline__ void ldv(const S* p, float (&v)[VPL]) {
+#pragma unroll
+  for (int q = 0; q < VPL / 4; ++q) ld4(p + 4 * q, v + 4 * q);
+}
+template <typename S, int VPL>
+__device__ __forceinline__ void stv(S* p, const float (&v)[VPL]) {
+#pragma unroll
+  for (int q = 0; q < VPL / 4; ++q) st4(p + 4 * q, v + 4 * q);
+}
+
 // The per-point body, shared by the single-case kernel and the batched kernel:
 // one warp, point i of case cv; s_v, s_col, s_P are this warp's shared buffers
-// (nv, cap and cap * dim^2 entries).
-template <typename S, int DIM, bool ALE, bool ROW4>
+// (nv, cap and cap * dim^2 entries).  Each lane owns VPL consecutive velocities of
+// every (32 VPL)-velocity slice.
+template <typename S, int DIM, bool ALE, bool ROW, int VPL>
 __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
                                                    float* s_P) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   constexpr int DD = DIM * DIM;
+  constexpr int NP = VPL / 2;  // velocity pairs per lane
   const int lane = threadIdx.x & 31;
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const float inv_nv = 1.0f / (float)nv;
-  const bool active = true;
   const int m = cv.cnt[i];
   for (int q = lane; q < nv; q += 32) s_v[q] = (float)cv.vnodes[q];
   {
@@ -375,9 +387,9 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
 
   float U[DIM];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) U[a] = (ALE && active) ? (float)cv.mom[(int64_t)i * MOM_STRIDE + 1 + a] : 0.0f;
+  for (int a = 0; a < DIM; ++a) U[a] = ALE ? (float)cv.mom[(int64_t)i * MOM_STRIDE + 1 + a] : 0.0f;
 
-  const int nchunk = NVp >> 2;
+  const int nchunk = NVp / VPL;
   const int nslice = (nchunk + 31) >> 5;
   const int64_t rowlen = (int64_t)NC * NVp;
   const S* fbase = reinterpret_cast<const S*>(cv.f_in);
@@ -391,128 +403,132 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
 
   for (int sl = 0; sl < nslice; ++sl) {
     const int chunk = sl * 32 + lane;
-    const bool valid = active && chunk < nchunk;
-    float vel[4][DIM];
-    bool kin[4];
-    chunk_velocities<DIM, ROW4>(4 * chunk, nv, NV, inv_nv, s_v, vel, kin);
-    float acc[NC][4], sk[4];
+    if (chunk >= nchunk) break;
+    const int k0 = VPL * chunk;
+    float vel[VPL][DIM];
+    bool kin[VPL];
+    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float acc[NC][VPL], sk[VPL];
+    const S* fj0 = fbase + k0;
+    if (ROW) {
+      // velocity pairs in packed FP32x2 arithmetic; the pairs share (v_y, v_z)
+      float2 cx[NP];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      sk[e] = 0.0f;
+      for (int q = 0; q < NP; ++q) cx[q] = f2(vel[2 * q][0] - U[0], vel[2 * q + 1][0] - U[0]);
+      float crest[DIM - 1];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c][e] = 0.0f;
-    }
-    if (valid) {
-      const S* fj0 = fbase + 4 * chunk;
-      if (ROW4) {
-        // velocity pairs (0,1), (2,3) in packed FP32x2 arithmetic
-        const float2 cx01 = f2(vel[0][0] - U[0], vel[1][0] - U[0]);
-        const float2 cx23 = f2(vel[2][0] - U[0], vel[3][0] - U[0]);
-        float crest[DIM - 1];
+      for (int a = 1; a < DIM; ++a) crest[a - 1] = vel[0][a] - U[a];
+      float2 skp[NP], ap[NC][NP];
 #pragma unroll
-        for (int a = 1; a < DIM; ++a) crest[a - 1] = vel[0][a] - U[a];
-        float2 sk01 = f2(0.0f, 0.0f), sk23 = f2(0.0f, 0.0f);
-        float2 a01[NC], a23[NC];
+      for (int q = 0; q < NP; ++q) {
+        skp[q] = f2(0.0f, 0.0f);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) { a01[c] = f2(0.0f, 0.0f); a23[c] = f2(0.0f, 0.0f); }
+        for (int c = 0; c < NC; ++c) ap[c][q] = f2(0.0f, 0.0f);
+      }
 #pragma unroll 2
-        for (int s = 0; s < m; ++s) {
-          const int j = s_col[s];
-          float P[DD];
+      for (int s = 0; s < m; ++s) {
+        const int j = s_col[s];
+        float P[DD];
 #pragma unroll
-          for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
-          const S* fj = fj0 + (int64_t)j * rowlen;
-          float fv[NC][4];
+        for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
+        const S* fj = fj0 + (int64_t)j * rowlen;
+        float fv[NC][VPL];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) ld4(fj + (int64_t)c * NVp, fv[c]);
-          float2 mk01, mk23;
+        for (int c = 0; c < NC; ++c) ldv<S, VPL>(fj + (int64_t)c * NVp, fv[c]);
+        float2 mk[NP];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          float b = crest[0] * P[d * DIM + 1];
+#pragma unroll
+          for (int a = 2; a < DIM; ++a) b = fmaf(crest[a - 1], P[d * DIM + a], b);
+          const float2 px = f2(P[d * DIM], P[d * DIM]), bb = f2(b, b);
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const float2 mq = min0(__ffma2_rn(cx[q], px, bb));
+            mk[q] = d == 0 ? mq : __fadd2_rn(mk[q], mq);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          skp[q] = __fadd2_rn(skp[q], mk[q]);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ap[c][q] = __ffma2_rn(mk[q], f2(fv[c][2 * q], fv[c][2 * q + 1]), ap[c][q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        sk[2 * q] = skp[q].x; sk[2 * q + 1] = skp[q].y;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { acc[c][2 * q] = ap[c][q].x; acc[c][2 * q + 1] = ap[c][q].y; }
+      }
+    } else {
+      float cvel[VPL][DIM];
+#pragma unroll
+      for (int e = 0; e < VPL; ++e) {
+        sk[e] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c][e] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) cvel[e][a] = vel[e][a] - U[a];
+      }
+#pragma unroll 2
+      for (int s = 0; s < m; ++s) {
+        const int j = s_col[s];
+        float P[DD];
+#pragma unroll
+        for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
+        const S* fj = fj0 + (int64_t)j * rowlen;
+        float fv[NC][VPL];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ldv<S, VPL>(fj + (int64_t)c * NVp, fv[c]);
+#pragma unroll
+        for (int e = 0; e < VPL; ++e) {
+          float mk = 0.0f;
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
-            float b = crest[0] * P[d * DIM + 1];
+            float p = cvel[e][0] * P[d * DIM];
 #pragma unroll
-            for (int a = 2; a < DIM; ++a) b = fmaf(crest[a - 1], P[d * DIM + a], b);
-            const float2 px = f2(P[d * DIM], P[d * DIM]), bb = f2(b, b);
-            const float2 m01 = min0(__ffma2_rn(cx01, px, bb));
-            const float2 m23 = min0(__ffma2_rn(cx23, px, bb));
-            if (d == 0) { mk01 = m01; mk23 = m23; }
-            else { mk01 = __fadd2_rn(mk01, m01); mk23 = __fadd2_rn(mk23, m23); }
+            for (int a = 1; a < DIM; ++a) p = fmaf(cvel[e][a], P[d * DIM + a], p);
+            mk = d == 0 ? fminf(p, 0.0f) : mk + fminf(p, 0.0f);
           }
-          sk01 = __fadd2_rn(sk01, mk01);
-          sk23 = __fadd2_rn(sk23, mk23);
+          sk[e] += mk;
 #pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            a01[c] = __ffma2_rn(mk01, f2(fv[c][0], fv[c][1]), a01[c]);
-            a23[c] = __ffma2_rn(mk23, f2(fv[c][2], fv[c][3]), a23[c]);
-          }
-        }
-        sk[0] = sk01.x; sk[1] = sk01.y; sk[2] = sk23.x; sk[3] = sk23.y;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) { acc[c][0] = a01[c].x; acc[c][1] = a01[c].y; acc[c][2] = a23[c].x; acc[c][3] = a23[c].y; }
-      } else {
-        float cvel[4][DIM];
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) cvel[e][a] = vel[e][a] - U[a];
-#pragma unroll 2
-        for (int s = 0; s < m; ++s) {
-          const int j = s_col[s];
-          float P[DD];
-#pragma unroll
-          for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
-          const S* fj = fj0 + (int64_t)j * rowlen;
-          float fv[NC][4];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) ld4(fj + (int64_t)c * NVp, fv[c]);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float mk = 0.0f;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-              float p = cvel[e][0] * P[d * DIM];
-#pragma unroll
-              for (int a = 1; a < DIM; ++a) p = fmaf(cvel[e][a], P[d * DIM + a], p);
-              mk = d == 0 ? fminf(p, 0.0f) : mk + fminf(p, 0.0f);
-            }
-            sk[e] += mk;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c][e] = fmaf(mk, fv[c][e], acc[c][e]);
-          }
+          for (int c = 0; c < NC; ++c) acc[c][e] = fmaf(mk, fv[c][e], acc[c][e]);
         }
       }
-      // f~ = f_i - 2 dt (acc - sk f_i); slice moment sums, Kahan-added to the running sums
-      float fiv[NC][4], ft[NC][4];
+    }
+    // f~ = f_i - 2 dt (acc - sk f_i); slice moment sums, Kahan-added to the running sums
+    float fiv[NC][VPL], ft[NC][VPL];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) ld4(fi + (int64_t)c * NVp + 4 * chunk, fiv[c]);
-      float ps[DIM + 2];
+    for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, fiv[c]);
+    float ps[DIM + 2];
 #pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+    for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < VPL; ++e) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? fiv[c][e] - two_dt * (acc[c][e] - sk[e] * fiv[c][e]) : 0.0f;
-        const float g = ft[0][e];
-        float v2 = 0.0f;
-        ps[0] += g;
+      for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? fiv[c][e] - two_dt * (acc[c][e] - sk[e] * fiv[c][e]) : 0.0f;
+      const float g = ft[0][e];
+      float v2 = 0.0f;
+      ps[0] += g;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
-        ps[DIM + 1] = fmaf(v2, g, ps[DIM + 1]);
-        if (NC == 2) ps[DIM + 1] += ft[NC - 1][e];
-      }
+      for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
+      ps[DIM + 1] = fmaf(v2, g, ps[DIM + 1]);
+      if (NC == 2) ps[DIM + 1] += ft[NC - 1][e];
+    }
 #pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) {
-        const float y = ps[q] - mcmp[q];
-        const float tt = msum[q] + y;
-        mcmp[q] = (tt - msum[q]) - y;
-        msum[q] = tt;
-      }
+    for (int q = 0; q < DIM + 2; ++q) {
+      const float y = ps[q] - mcmp[q];
+      const float tt = msum[q] + y;
+      mcmp[q] = (tt - msum[q]) - y;
+      msum[q] = tt;
+    }
 #pragma unroll
-      for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, ft[c]);
-      if (cv.ft_out) {
+    for (int c = 0; c < NC; ++c) stv<S, VPL>(fo + (int64_t)c * NVp + k0, ft[c]);
+    if (cv.ft_out) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) st4(cv.ft_out + (int64_t)i * rowlen + (int64_t)c * NVp + 4 * chunk, ft[c]);
-        st4(cv.sk_out + (int64_t)i * NVp + 4 * chunk, sk);
-      }
+      for (int c = 0; c < NC; ++c) stv<float, VPL>(cv.ft_out + (int64_t)i * rowlen + (int64_t)c * NVp + k0, ft[c]);
+      stv<float, VPL>(cv.sk_out + (int64_t)i * NVp + k0, sk);
     }
   }
 
@@ -545,18 +561,18 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
     pref = cb * (DIM == 2 ? rho / twopiT : rho / (twopiT * sqrtf(twopiT)));
     nl2 = -0.5f / Tn;
   }
-  const float cbT = Tn;
   for (int sl = 0; sl < nslice; ++sl) {
     const int chunk = sl * 32 + lane;
     if (chunk >= nchunk) break;
-    float vel[4][DIM];
-    bool kin[4];
-    chunk_velocities<DIM, ROW4>(4 * chunk, nv, NV, inv_nv, s_v, vel, kin);
-    float ft[NC][4], out[NC][4];
+    const int k0 = VPL * chunk;
+    float vel[VPL][DIM];
+    bool kin[VPL];
+    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float ft[NC][VPL], out[NC][VPL];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) ld4(fo + (int64_t)c * NVp + 4 * chunk, ft[c]);
+    for (int c = 0; c < NC; ++c) ldv<S, VPL>(fo + (int64_t)c * NVp + k0, ft[c]);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < VPL; ++e) {
       float c2 = 0.0f;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
@@ -565,15 +581,15 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
       }
       const float bM = kin[e] ? pref * __expf(nl2 * c2) : 0.0f;  // dt/(tau+dt) * M(v)
       out[0][e] = kin[e] ? fmaf(ca, ft[0][e], bM) : 0.0f;
-      if (NC == 2) out[NC - 1][e] = kin[e] ? fmaf(ca, ft[NC - 1][e], cbT * bM) : 0.0f;
+      if (NC == 2) out[NC - 1][e] = kin[e] ? fmaf(ca, ft[NC - 1][e], Tn * bM) : 0.0f;
     }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, out[c]);
+    for (int c = 0; c < NC; ++c) stv<S, VPL>(fo + (int64_t)c * NVp + k0, out[c]);
   }
 }
 
-template <typename S, int DIM, bool ALE, bool ROW4>
-__global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
+template <typename S, int DIM, bool ALE, bool ROW, int VPL>
+__global__ void __launch_bounds__(256, VPL == 4 ? 3 : 2) k_transport_wp(const CaseView cv) {
   constexpr int DD = DIM * DIM;
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -583,7 +599,7 @@ __global__ void __launch_bounds__(256, 3) k_transport_wp(const CaseView cv) {
   float* s_P = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W)) + (size_t)warp * cap * DD;
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
-  transport_point_wp<S, DIM, ALE, ROW4>(cv, cv.int_idx[t], s_v, s_col, s_P);
+  transport_point_wp<S, DIM, ALE, ROW, VPL>(cv, cv.int_idx[t], s_v, s_col, s_P);
 }
 
 // Many cases in one persistent launch: items[k] = (case, interior slot), tiles of W
@@ -606,32 +622,45 @@ __global__ void __launch_bounds__(256, 3) k_transport_batch(const CaseView* __re
     const int i = cv.int_idx[e.y];
     const bool row4 = cv.nv % 4 == 0;
     if (cv.ale) {
-      if (row4) transport_point_wp<S, DIM, true, true>(cv, i, s_v, s_col, s_P);
-      else transport_point_wp<S, DIM, true, false>(cv, i, s_v, s_col, s_P);
+      if (row4) transport_point_wp<S, DIM, true, true, 4>(cv, i, s_v, s_col, s_P);
+      else transport_point_wp<S, DIM, true, false, 4>(cv, i, s_v, s_col, s_P);
     } else {
-      if (row4) transport_point_wp<S, DIM, false, true>(cv, i, s_v, s_col, s_P);
-      else transport_point_wp<S, DIM, false, false>(cv, i, s_v, s_col, s_P);
+      if (row4) transport_point_wp<S, DIM, false, true, 4>(cv, i, s_v, s_col, s_P);
+      else transport_point_wp<S, DIM, false, false, 4>(cv, i, s_v, s_col, s_P);
     }
     __syncwarp();
   }
 }
+
+// Velocities per lane: 8 in 3D when the velocity rows split into groups of 8 (fewer
+// per-neighbour instructions and more loads in flight pay off there: 7.1 vs 8.6 ms
+// on the 41^3 x 16^3 cavity), 4 in 2D (where the lower occupancy of the wider
+// variant costs more than it saves: 0.53 vs 0.48 ms on the 201^2 x 32^2 cavity).
+int transport_vpl = 0;  // 0 = automatic; 4 or 8 forces a width
 
 template <typename S, int DIM>
 static void launch_transport_wp(const CaseView& cv, cudaStream_t s) {
   const int W = 8, threads = 32 * W;
   const size_t smem = 256 * W + align16(sizeof(int32_t) * cv.cap * W) + sizeof(float) * cv.cap * DIM * DIM * W;
   const int grid = (cv.n_int + W - 1) / W;
-  const bool row4 = cv.nv % 4 == 0;
-#define BGK_LAUNCH_WP(ALE, ROW4)                                                          \
+  const bool row4 = cv.nv % 4 == 0, row8 = cv.nv % 8 == 0 && cv.NVp % 8 == 0;
+  const bool v8 = transport_vpl == 8 ? (cv.NVp % 8 == 0) : (transport_vpl == 4 ? false : (DIM == 3 && row8));
+#define BGK_LAUNCH_WP(ALE, ROW, VPL)                                                      \
   {                                                                                       \
-    auto k = k_transport_wp<S, DIM, ALE, ROW4>;                                           \
+    auto k = k_transport_wp<S, DIM, ALE, ROW, VPL>;                                       \
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
     k<<<grid, threads, smem, s>>>(cv);                                                    \
   }
-  if (cv.ale) {
-    if (row4) BGK_LAUNCH_WP(true, true) else BGK_LAUNCH_WP(true, false)
+  if (v8) {
+    if (cv.ale) {
+      if (row8) BGK_LAUNCH_WP(true, true, 8) else BGK_LAUNCH_WP(true, false, 8)
+    } else {
+      if (row8) BGK_LAUNCH_WP(false, true, 8) else BGK_LAUNCH_WP(false, false, 8)
+    }
+  } else if (cv.ale) {
+    if (row4) BGK_LAUNCH_WP(true, true, 4) else BGK_LAUNCH_WP(true, false, 4)
   } else {
-    if (row4) BGK_LAUNCH_WP(false, true) else BGK_LAUNCH_WP(false, false)
+    if (row4) BGK_LAUNCH_WP(false, true, 4) else BGK_LAUNCH_WP(false, false, 4)
   }
 #undef BGK_LAUNCH_WP
 }

@@ -1,0 +1,51 @@
+"""Multi-rank logic of bench.py on CPU (gloo, two ranks) and the reference arm's output line."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    import bgk_inputs as bi
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p = bench.rank_config(bi.config(bench.WORKLOAD), rank, world)
+    m = bench.reduce_max(float(10 + rank), dist, "cpu")
+    dist.barrier()
+    out[rank] = (p["kn"], m, p["n"])
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_independent_cavities_and_the_max_time():
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    assert out[0][1] == out[1][1] == 11.0          # max over ranks
+    assert out[0][0] != out[1][0]                  # Kn sweep by rank (weak scaling)
+    assert out[0][2] == out[1][2] == 201           # same cavity size on every rank
+
+
+def test_reference_arm_prints_its_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["unit"] == "updates/s" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
