@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -386,12 +387,26 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     c.s_bytes = q.storage == 0 ? 8 : (q.storage == 1 ? 4 : 2);
     c.c_bytes = q.storage == 0 ? 8 : 4;
 
-    // interior / wall partition of the input (ascending index)
+    // interior / wall partition of the input.  Interior points are listed in Morton
+    // (Z) order of their initial positions, so that consecutive points (the points of
+    // one CTA) are spatially compact and share most of their neighbours; wall points
+    // are listed in index order.  The order changes which CTA handles a point, not
+    // its arithmetic.
     std::vector<int32_t> inner, wall;
+    std::vector<std::pair<uint64_t, int32_t>> keyed;
     for (int64_t i = 0; i < n; ++i) {
-      if (kind[off + i] == 0) inner.push_back((int32_t)i);
-      else wall.push_back((int32_t)i);
+      if (kind[off + i] != 0) { wall.push_back((int32_t)i); continue; }
+      uint64_t key = 0;
+      for (int a = 0; a < dim; ++a) {
+        double xa = x[(off + i) * dim + a];
+        xa = xa < 0.0 ? 0.0 : (xa > 1.0 ? 1.0 : xa);
+        const uint64_t qa = (uint64_t)(xa * 1048575.0);  // 20 bits per axis
+        for (int bit = 0; bit < 20; ++bit) key |= ((qa >> bit) & 1ull) << (bit * dim + a);
+      }
+      keyed.emplace_back(key, (int32_t)i);
     }
+    std::sort(keyed.begin(), keyed.end());
+    for (auto& kv : keyed) inner.push_back(kv.second);
     if (q.periodic && !wall.empty()) return bail(fail(ctx, BGK_E_INVAL, "case %d: periodic box with wall points", ci));
     v.n_int = (int32_t)inner.size();
     v.n_wall = (int32_t)wall.size();

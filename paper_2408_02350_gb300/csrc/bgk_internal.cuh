@@ -36,7 +36,7 @@ struct CaseView {
   double* x;               // [n][dim]
   const int32_t* kind;     // [n]
   const double* normal;    // [n][dim]
-  const int32_t* int_idx;  // [n_int] interior point indices, ascending
+  const int32_t* int_idx;  // [n_int] interior point indices, Morton order of the initial positions
   const int32_t* wall_idx; // [n_wall] wall point indices, ascending
 
   float* xf;            // [n][dim] FP32 rounding of x (neighbour-search prefilter, high part)

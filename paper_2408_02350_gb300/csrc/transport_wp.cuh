@@ -1,0 +1,353 @@
+// Warp-per-point transport + moments + relaxation in FP32 arithmetic (FP32 or BF16
+// storage), Sec. 3.2 and 3.4: the per-point body and its pieces, shared by the
+// single-case and batched transport kernels.
+#pragma once
+
+#include "bgk_internal.cuh"
+#include "device_common.cuh"
+
+namespace bgk {
+
+// ---------------------------------------------------------------------------
+// transport + moments + relaxation, FP32 arithmetic (FP32 or BF16 storage):
+// one warp per interior point.  Each lane owns 4 consecutive velocities of
+// every 128-velocity slice; the warps of a CTA handle consecutive points, whose
+// shared neighbour rows are often served from L1.  f~ of
+// a slice is written to the output row and re-read after the moments, which are
+// warp-shuffle sums of per-lane Kahan-compensated slice sums (no CTA barrier).
+// With ROW4 (nv % 4 == 0) a lane's 4 velocities share (v_y, v_z), so the
+// projection c.P_d costs one FMA per velocity: c.P_d = c_x P_dx + (c_y P_dy + c_z P_dz).
+// ---------------------------------------------------------------------------
+// Quotient k / n for 0 <= k < 2^13, 1 <= n <= 64 by a float reciprocal: (k + 1/2)/n lies at least
+// 1/(2n) away from an integer and the float error is below (k/n + 1) 2^-23, so truncation is exact.
+__device__ __forceinline__ int fdiv_small(int k, float inv_n) { return (int)(((float)k + 0.5f) * inv_n); }
+
+// Velocity components of the VPL velocities k0..k0+VPL-1.  With ROW (nv % VPL == 0,
+// k0 % VPL == 0) they share every component but the first.
+template <int DIM, int VPL, bool ROW>
+__device__ __forceinline__ void chunk_velocities(int k0, int nv, int NV, float inv_nv, const float* s_v,
+                                                 float (&vel)[VPL][DIM], bool (&kin)[VPL]) {
+  if (ROW) {
+    int q = fdiv_small(k0, inv_nv);
+    const int kx0 = k0 - q * nv;
+#pragma unroll
+    for (int e = 0; e < VPL; ++e) { vel[e][0] = s_v[kx0 + e]; kin[e] = k0 + e < NV; }
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) {
+      const int q2 = fdiv_small(q, inv_nv);
+      const float va = s_v[q - q2 * nv];
+      q = q2;
+#pragma unroll
+      for (int e = 0; e < VPL; ++e) vel[e][a] = va;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < VPL; ++e) {
+      int kk = k0 + e;
+      kin[e] = kk < NV;
+      if (!kin[e]) kk = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const int q = fdiv_small(kk, inv_nv);
+        vel[e][a] = s_v[kk - q * nv];
+        kk = q;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 min0(float2 p) { return make_float2(fminf(p.x, 0.0f), fminf(p.y, 0.0f)); }
+
+template <typename S, int VPL>
+__device__ __forceinline__ void ldv(const S* p, float (&v)[VPL]) {
+#pragma unroll
+  for (int q = 0; q < VPL / 4; ++q) ld4(p + 4 * q, v + 4 * q);
+}
+// Neighbour rows of f^n through the read-only data path (f^n is not written while
+// the transport runs: the output goes to the other buffer).
+__device__ __forceinline__ void ld4_ro(const float* p, float v[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4_ro(const __nv_bfloat16* p, float v[4]) {
+  uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+  const float2 l = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&a.x));
+  const float2 h = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&a.y));
+  v[0] = l.x; v[1] = l.y; v[2] = h.x; v[3] = h.y;
+}
+template <typename S, int VPL>
+__device__ __forceinline__ void ldv_ro(const S* p, float (&v)[VPL]) {
+#pragma unroll
+  for (int q = 0; q < VPL / 4; ++q) ld4_ro(p + 4 * q, v + 4 * q);
+}
+template <typename S, int VPL>
+__device__ __forceinline__ void stv(S* p, const float (&v)[VPL]) {
+#pragma unroll
+  for (int q = 0; q < VPL / 4; ++q) st4(p + 4 * q, v + 4 * q);
+}
+
+// Upwind sums of one neighbour row for the VPL = 2 NP velocities of a lane that lie
+// in one row of the velocity grid (they share every component but the first):
+//   m = sum_d min(c.P_d, 0),  sk += m,  acc_c += m f_j,c
+// in packed FP32x2 arithmetic, with c.P_d = c_x P_dx + (c_y P_dy + c_z P_dz).
+template <int DIM, int NC, int NP>
+__device__ __forceinline__ void row_upwind(const float2 (&cx)[NP], const float (&crest)[DIM - 1],
+                                           const float (&P)[DIM * DIM], const float (&fv)[NC][2 * NP],
+                                           float2 (&skp)[NP], float2 (&ap)[NC][NP]) {
+  float2 mk[NP];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    float b = crest[0] * P[d * DIM + 1];
+#pragma unroll
+    for (int a = 2; a < DIM; ++a) b = fmaf(crest[a - 1], P[d * DIM + a], b);
+    const float2 px = f2(P[d * DIM], P[d * DIM]), bb = f2(b, b);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float2 mq = min0(__ffma2_rn(cx[q], px, bb));
+      mk[q] = d == 0 ? mq : __fadd2_rn(mk[q], mq);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    skp[q] = __fadd2_rn(skp[q], mk[q]);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ap[c][q] = __ffma2_rn(mk[q], f2(fv[c][2 * q], fv[c][2 * q + 1]), ap[c][q]);
+  }
+}
+
+// End of a velocity slice: f~ = f_i - 2 dt (acc - sk f_i) for the lane's VPL
+// velocities, written to the output row (and to the adjoint's tape when one is
+// attached); the slice's moment sums are Kahan-added to the lane's running sums.
+template <typename S, int DIM, int NC, int VPL>
+__device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const int k0, const float (&vel)[VPL][DIM],
+                                          const bool (&kin)[VPL], const float (&acc)[NC][VPL],
+                                          const float (&sk)[VPL], const float two_dt, float (&msum)[DIM + 2],
+                                          float (&mcmp)[DIM + 2]) {
+  const int NVp = cv.NVp;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  const S* fi = reinterpret_cast<const S*>(cv.f_in) + (int64_t)i * rowlen;
+  S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * rowlen;
+  float fiv[NC][VPL], ft[NC][VPL];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, fiv[c]);
+  float ps[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+#pragma unroll
+  for (int e = 0; e < VPL; ++e) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? fiv[c][e] - two_dt * (acc[c][e] - sk[e] * fiv[c][e]) : 0.0f;
+    const float g = ft[0][e];
+    float v2 = 0.0f;
+    ps[0] += g;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
+    ps[DIM + 1] = fmaf(v2, g, ps[DIM + 1]);
+    if (NC == 2) ps[DIM + 1] += ft[NC - 1][e];
+  }
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) {
+    const float y = ps[q] - mcmp[q];
+    const float tt = msum[q] + y;
+    mcmp[q] = (tt - msum[q]) - y;
+    msum[q] = tt;
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) stv<S, VPL>(fo + (int64_t)c * NVp + k0, ft[c]);
+  if (cv.ft_out) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) stv<float, VPL>(cv.ft_out + (int64_t)i * rowlen + (int64_t)c * NVp + k0, ft[c]);
+    stv<float, VPL>(cv.sk_out + (int64_t)i * NVp + k0, sk);
+  }
+}
+
+// Moments of f~_i (warp totals of the lanes' compensated sums; every lane gets them),
+// tau and the Maxwellian, then the relaxation pass over the output row:
+// f^{n+1} = (tau f~ + dt M)/(tau + dt).  All 32 lanes of the warp take part.
+template <typename S, int DIM, bool ROW, int VPL>
+__device__ __forceinline__ void finish_point(const CaseView& cv, const int i, const float* s_v,
+                                             const float (&msum)[DIM + 2], const float (&mcmp)[DIM + 2]) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  const int lane = threadIdx.x & 31;
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const float inv_nv = 1.0f / (float)nv;
+  const int nchunk = NVp / VPL;
+  const int nslice = (nchunk + 31) >> 5;
+  S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * NC * NVp;
+  float tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
+  const float R = tot[0];
+  float Un[DIM], u2 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { Un[a] = tot[1 + a] / R; u2 = fmaf(Un[a], Un[a], u2); }
+  const float Tn = (tot[DIM + 1] - R * u2) / (3.0f * R);
+  const float wv = (float)(DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
+  const float rho = R * wv;
+  if (lane == 0) {
+    double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
+    mo[0] = rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mo[1 + a] = a < DIM ? (double)Un[a < DIM ? a : 0] : 0.0;
+    mo[4] = Tn;
+    if (!(rho > 0.0f) || !(Tn > 0.0f) || !isfinite(rho) || !isfinite(Tn)) set_status(cv.status, ST_NONFINITE);
+  }
+  float ca = 1.0f, cb = 0.0f, pref = 0.0f, nl2 = 0.0f;
+  if (cv.tau_mode != 2 && rho > 0.0f && Tn > 0.0f) {
+    const float kn = (float)cv.kn, dtf = (float)cv.dt;
+    const float tau = cv.tau_mode == 1 ? 0.7978845608f * kn : 0.7978845608f * kn / (rho * sqrtf(Tn));
+    ca = tau / (tau + dtf);
+    cb = dtf / (tau + dtf);
+    const float twopiT = 6.283185307f * Tn;
+    pref = cb * (DIM == 2 ? rho / twopiT : rho / (twopiT * sqrtf(twopiT)));
+    nl2 = -0.5f / Tn;
+  }
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    if (chunk >= nchunk) break;
+    const int k0 = VPL * chunk;
+    float vel[VPL][DIM];
+    bool kin[VPL];
+    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float ft[NC][VPL], out[NC][VPL];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ldv<S, VPL>(fo + (int64_t)c * NVp + k0, ft[c]);
+#pragma unroll
+    for (int e = 0; e < VPL; ++e) {
+      float c2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float d = vel[e][a] - Un[a];
+        c2 = fmaf(d, d, c2);
+      }
+      const float bM = kin[e] ? pref * __expf(nl2 * c2) : 0.0f;  // dt/(tau+dt) * M(v)
+      out[0][e] = kin[e] ? fmaf(ca, ft[0][e], bM) : 0.0f;
+      if (NC == 2) out[NC - 1][e] = kin[e] ? fmaf(ca, ft[NC - 1][e], Tn * bM) : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) stv<S, VPL>(fo + (int64_t)c * NVp + k0, out[c]);
+  }
+}
+
+// The per-point body, shared by the single-case kernel and the batched kernel:
+// one warp, point i of case cv; s_v, s_col, s_P are this warp's shared buffers
+// (nv, cap and cap * dim^2 entries).  Each lane owns VPL consecutive velocities of
+// every (32 VPL)-velocity slice.
+template <typename S, int DIM, bool ALE, bool ROW, int VPL>
+__device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
+                                                   float* s_P) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int DD = DIM * DIM;
+  constexpr int NP = VPL / 2;  // velocity pairs per lane
+  const int lane = threadIdx.x & 31;
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const float inv_nv = 1.0f / (float)nv;
+  const int m = cv.cnt[i];
+  for (int q = lane; q < nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  {
+    const int32_t* col = cv.col + (int64_t)i * cap;
+    const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
+    for (int q = lane; q < m; q += 32) s_col[q] = col[q];
+    for (int q = lane; q < m * DD; q += 32) s_P[q] = P[q];
+  }
+  __syncwarp();
+
+  float U[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) U[a] = ALE ? (float)cv.mom[(int64_t)i * MOM_STRIDE + 1 + a] : 0.0f;
+
+  const int nchunk = NVp / VPL;
+  const int nslice = (nchunk + 31) >> 5;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  const S* fbase = reinterpret_cast<const S*>(cv.f_in);
+  const float two_dt = (float)(2.0 * cv.dt);
+
+  float msum[DIM + 2], mcmp[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) { msum[q] = 0.0f; mcmp[q] = 0.0f; }
+
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    if (chunk >= nchunk) break;
+    const int k0 = VPL * chunk;
+    float vel[VPL][DIM];
+    bool kin[VPL];
+    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float acc[NC][VPL], sk[VPL];
+    const S* fj0 = fbase + k0;
+    if (ROW) {
+      // velocity pairs in packed FP32x2 arithmetic; the pairs share (v_y, v_z)
+      float2 cx[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) cx[q] = f2(vel[2 * q][0] - U[0], vel[2 * q + 1][0] - U[0]);
+      float crest[DIM - 1];
+#pragma unroll
+      for (int a = 1; a < DIM; ++a) crest[a - 1] = vel[0][a] - U[a];
+      float2 skp[NP], ap[NC][NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        skp[q] = f2(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ap[c][q] = f2(0.0f, 0.0f);
+      }
+#pragma unroll 2
+      for (int s = 0; s < m; ++s) {
+        const int j = s_col[s];
+        float P[DD];
+#pragma unroll
+        for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
+        const S* fj = fj0 + (int64_t)j * rowlen;
+        float fv[NC][VPL];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ldv_ro<S, VPL>(fj + (int64_t)c * NVp, fv[c]);
+        row_upwind<DIM, NC, NP>(cx, crest, P, fv, skp, ap);
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        sk[2 * q] = skp[q].x; sk[2 * q + 1] = skp[q].y;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { acc[c][2 * q] = ap[c][q].x; acc[c][2 * q + 1] = ap[c][q].y; }
+      }
+    } else {
+      float cvel[VPL][DIM];
+#pragma unroll
+      for (int e = 0; e < VPL; ++e) {
+        sk[e] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c][e] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) cvel[e][a] = vel[e][a] - U[a];
+      }
+#pragma unroll 2
+      for (int s = 0; s < m; ++s) {
+        const int j = s_col[s];
+        float P[DD];
+#pragma unroll
+        for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
+        const S* fj = fj0 + (int64_t)j * rowlen;
+        float fv[NC][VPL];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ldv_ro<S, VPL>(fj + (int64_t)c * NVp, fv[c]);
+#pragma unroll
+        for (int e = 0; e < VPL; ++e) {
+          float mk = 0.0f;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            float p = cvel[e][0] * P[d * DIM];
+#pragma unroll
+            for (int a = 1; a < DIM; ++a) p = fmaf(cvel[e][a], P[d * DIM + a], p);
+            mk = d == 0 ? fminf(p, 0.0f) : mk + fminf(p, 0.0f);
+          }
+          sk[e] += mk;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c][e] = fmaf(mk, fv[c][e], acc[c][e]);
+        }
+      }
+    }
+    slice_out<S, DIM, NC, VPL>(cv, i, k0, vel, kin, acc, sk, two_dt, msum, mcmp);
+  }
+  finish_point<S, DIM, ROW, VPL>(cv, i, s_v, msum, mcmp);
+}
+
+}  // namespace bgk
