@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 1
+#define BGK_ABI_VERSION 2
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -76,13 +76,19 @@ typedef struct bgk_params {
   double wall_T;     /* wall temperature */
   double guard;      /* ALE: interior coordinates are clamped to [guard, 1 - guard] */
   double lid_u[3];   /* lid velocity */
+  double skin;       /* ALE neighbour-list skin, a fraction of h in [0, 1]: candidate
+                        lists of radius h (1 + skin) are built with the cell search and
+                        re-filtered with the exact test every step, and rebuilt once a
+                        point has moved more than h skin / 2 since the last build.  The
+                        lists equal those of a full search every step; 0 turns it off.
+                        Fixed at bgk_init. */
 } bgk_params;
 
 typedef struct bgk_stats {
   int64_t steps;          /* time steps taken */
   int64_t launches;       /* kernels launched by this context since creation */
   int64_t clamps;         /* ALE wall-guard clamps (valid after bgk_sync) */
-  int64_t nnz;            /* neighbour pairs of the last build (valid after bgk_sync) */
+  int64_t nnz;            /* neighbour pairs in the current lists, all cases */
   int32_t nv_pad;         /* padded velocity stride of the internal f layout */
   int32_t n_cases;
   int32_t batch_mode;     /* stepping mode in effect: 0 per case, 1 batched kernels, 2 batched kernels in a graph */

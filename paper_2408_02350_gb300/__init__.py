@@ -40,7 +40,7 @@ class bgk_params(C.Structure):
         ("tau_mode", C.c_int32), ("ale", C.c_int32), ("periodic", C.c_int32), ("lid_wall", C.c_int32),
         ("max_nbrs", C.c_int32), ("storage", C.c_int32),
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
-        ("guard", C.c_double), ("lid_u", C.c_double * 3),
+        ("guard", C.c_double), ("lid_u", C.c_double * 3), ("skin", C.c_double),
     ]
 
 
@@ -293,6 +293,7 @@ def params_from(p: dict) -> bgk_params:
     lu = list(p.get("lid_u", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
     for a in range(3):
         q.lid_u[a] = float(lu[a])
+    q.skin = float(p.get("skin", 0.2 if q.ale else 0.0))
     return q
 
 

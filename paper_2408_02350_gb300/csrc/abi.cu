@@ -50,6 +50,21 @@ struct CaseHost {
   int32_t* wall_of = nullptr;
   bool tslot_valid = false;
   int32_t nlid = 0;
+  // ALE: the lists of the next step (second set of cnt, col, P, recon) are built on
+  // the side stream right after the motion, while the wall kernel runs; they are
+  // swapped in at the next step.  ev_fork orders the side work after the transport,
+  // ev_join orders later work after it.
+  int32_t* nx_cnt = nullptr;
+  int32_t* nx_col = nullptr;
+  void* nx_P = nullptr;
+  void* nx_recon = nullptr;
+  bool next_ready = false;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // wall reconstruction weights of the second set follow on the side stream while
+  // the next transport runs; chain k records ev_recon[k & 1], which the wall kernel
+  // of the step that uses that set waits for
+  cudaEvent_t ev_recon[2] = {nullptr, nullptr};
+  int64_t chain = 0;
 };
 
 }  // namespace
@@ -66,6 +81,7 @@ struct bgk_ctx {
   int batch_warps = 8, batch_grid = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side = nullptr;  // ALE motion and next-step lists, concurrent with the wall kernel
   std::vector<void*> allocs;
   DevStatus* status = nullptr;
   std::string err;
@@ -154,6 +170,7 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
   if (p.max_nbrs < 1 || p.max_nbrs > 512) { *why = "max_nbrs must be in [1, 512]"; return 0; }
   if (n < 1 || n > (int64_t)1 << 30) { *why = "point count must be in [1, 2^30]"; return 0; }
   if (p.guard < 0 || p.guard >= 0.5) { *why = "guard must be in [0, 0.5)"; return 0; }
+  if (!(p.skin >= 0 && p.skin <= 1)) { *why = "skin must be in [0, 1]"; return 0; }
   return 1;
 }
 
@@ -197,21 +214,101 @@ int collect_timing(bgk_ctx* ctx) {
   return BGK_OK;
 }
 
-int build_lists(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+// Forces a candidate rebuild at the next list build of an ALE case with skin lists.
+int reset_skin(bgk_ctx* ctx, CaseHost& c) {
+  if (!c.cv.sk) return BGK_OK;
+  const SkinState s0 = {0u, 1, 0u, 0};
+  CK(ctx, cudaMemcpy(c.cv.sk, &s0, sizeof(s0), cudaMemcpyHostToDevice));
+  return BGK_OK;
+}
+
+// Neighbour lists and stencils of the current positions into the list arrays of v
+// (part: as launch_stencils).
+int build_lists_into(bgk_ctx* ctx, const CaseView& v, cudaStream_t s, int part = 0) {
   EvPair* e;
   int st;
-  CK(ctx, cudaMemsetAsync(&ctx->status->nnz, 0, sizeof(unsigned long long), s));
   if ((st = timed_begin(ctx, K_NBR, s, &e))) return st;
-  ctx->launches += launch_neighbours(c.cv, s);
+  ctx->launches += v.ale && v.sk ? launch_neighbours_skin(v, s) : launch_neighbours(v, s);
   CKL(ctx);
   if ((st = timed_end(ctx, e, s))) return st;
   if ((st = timed_begin(ctx, K_STENCIL, s, &e))) return st;
-  ctx->launches += launch_stencils(c.cv, s);
+  ctx->launches += launch_stencils(v, s, part);
   CKL(ctx);
   if ((st = timed_end(ctx, e, s))) return st;
+  return BGK_OK;
+}
+
+// Orders stream s after the side-stream work of case c (motion, next lists, wall weights).
+int join_side(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+  if (c.ev_join) CK(ctx, cudaStreamWaitEvent(s, c.ev_join, 0));
+  if (c.chain > 0) CK(ctx, cudaStreamWaitEvent(s, c.ev_recon[(c.chain - 1) & 1], 0));
+  return BGK_OK;
+}
+
+int build_lists(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+  int st;
+  if ((st = join_side(ctx, c, s))) return st;
+  if ((st = build_lists_into(ctx, c.cv, s))) return st;
+  c.next_ready = false;
   c.stencils_valid = true;
   c.tslot_valid = false;
   return BGK_OK;
+}
+
+// After the transport of an ALE case on stream s: on the side stream, move the
+// points and build the lists of the new positions into the second list set.  The
+// next transport waits for the interior stencils (ev_join); the wall weights that
+// follow overlap it (no kernel writes x or that set meanwhile) and the next wall
+// kernel waits for them.
+int move_and_prebuild(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+  int st;
+  EvPair* e;
+  if (!ctx->side) CK(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  if (!c.ev_fork) {
+    CK(ctx, cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&c.ev_recon[0], cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&c.ev_recon[1], cudaEventDisableTiming));
+  }
+  if (!c.nx_cnt) {
+    const size_t n = c.cv.n, cap = c.cv.cap, dim = c.cv.dim;
+    if ((st = dalloc(ctx, &c.nx_cnt, n))) return st;
+    if ((st = dalloc(ctx, &c.nx_col, n * cap))) return st;
+    if ((st = dalloc_bytes(ctx, &c.nx_P, n * cap * dim * dim * c.c_bytes))) return st;
+    if ((st = dalloc_bytes(ctx, &c.nx_recon, n * cap * c.c_bytes))) return st;
+  }
+  cudaStream_t q = ctx->side;
+  CK(ctx, cudaEventRecord(c.ev_fork, s));
+  CK(ctx, cudaStreamWaitEvent(q, c.ev_fork, 0));
+  if ((st = timed_begin(ctx, K_MOVE, q, &e))) return st;
+  ctx->launches += launch_move(c.cv, q);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, q))) return st;
+  CaseView nx = c.cv;
+  nx.cnt = c.nx_cnt;
+  nx.col = c.nx_col;
+  nx.P = c.nx_P;
+  nx.recon = c.nx_recon;
+  if ((st = build_lists_into(ctx, nx, q, 1))) return st;
+  CK(ctx, cudaEventRecord(c.ev_join, q));
+  if ((st = timed_begin(ctx, K_STENCIL, q, &e))) return st;
+  ctx->launches += launch_stencils(nx, q, 2);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, q))) return st;
+  CK(ctx, cudaEventRecord(c.ev_recon[c.chain & 1], q));
+  c.chain += 1;
+  c.next_ready = true;
+  return BGK_OK;
+}
+
+// At the start of a step: the lists built after the last motion become current.
+void swap_in_next(CaseHost& c) {
+  std::swap(c.cv.cnt, c.nx_cnt);
+  std::swap(c.cv.col, c.nx_col);
+  std::swap(c.cv.P, c.nx_P);
+  std::swap(c.cv.recon, c.nx_recon);
+  c.next_ready = false;
+  c.tslot_valid = false;
 }
 
 // ---- batched stepping ----
@@ -377,7 +474,9 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.guard = q.guard;
     v.dv = 2.0 * q.vmax / (double)(q.nv - 1);
     for (int a = 0; a < 3; ++a) v.lid_u[a] = q.lid_u[a];
-    v.nc = (int)std::floor(1.0 / (q.h * (1.0 + 1e-9)));
+    v.skin = q.skin;
+    // cells of side >= the search radius (h, or h (1 + skin) for the candidate lists)
+    v.nc = (int)std::floor(1.0 / (q.h * (1.0 + q.skin) * (1.0 + 1e-9)));
     if (v.nc < 1) v.nc = 1;
     if (v.nc > 4096) v.nc = 4096;
     int64_t ncell = 1;
@@ -457,6 +556,19 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     for (int b = 0; b < 2; ++b) {
       if ((st = dalloc_bytes(ctx, &c.f[b], fbytes))) return bail(st);
       if (cudaMemset(c.f[b], 0, fbytes) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset f"));
+    }
+    if (q.skin > 0) {
+      // candidate capacity: max_nbrs scaled by the volume ratio of the two radii, plus 10 %
+      const double r = std::pow(1.0 + q.skin, dim) * 1.1;
+      v.ccap = (int32_t)std::min<double>(std::ceil(v.cap * r), 4096.0);
+      if ((st = dalloc(ctx, &v.xb, n * dim))) return bail(st);
+      if ((st = dalloc(ctx, &v.ccnt, n))) return bail(st);
+      if ((st = dalloc(ctx, &v.ccol, (size_t)n * v.ccap))) return bail(st);
+      if ((st = dalloc(ctx, &v.sk, 1))) return bail(st);
+      const SkinState s0 = {0u, 1, 0u, 0};
+      if (cudaMemcpy(v.sk, &s0, sizeof(s0), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemset(v.cell_cnt, 0, sizeof(int32_t) * ncell) != cudaSuccess)
+        return bail(fail(ctx, BGK_E_CUDA, "case %d: skin state upload failed", ci));
     }
     if ((st = dalloc(ctx, &v.mom, (size_t)n * MOM_STRIDE))) return bail(st);
     if (cudaMemset(v.mom, 0, sizeof(double) * n * MOM_STRIDE) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset mom"));
@@ -622,27 +734,33 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
   for (int step = 0; step < nsteps; ++step) {
     for (auto& c : ctx->cases) {
       refresh_view(c);
-      if (c.cv.ale || !c.stencils_valid)
+      int64_t recon_chain = -1;  // side chain whose wall weights the wall kernel needs
+      if (c.next_ready && c.stencils_valid && c.cv.ale) {
+        swap_in_next(c);
+        CK(ctx, cudaStreamWaitEvent(s, c.ev_join, 0));
+        recon_chain = c.chain - 1;
+      } else if (c.cv.ale || !c.stencils_valid) {
         if ((st = build_lists(ctx, c, s))) return st;
+      }
       if ((st = timed_begin(ctx, K_TRANSPORT, s, &e))) return st;
       ctx->launches += launch_transport(c.cv, s);
       CKL(ctx);
       if ((st = timed_end(ctx, e, s))) return st;
+      // ALE: motion and the next step's lists on the side stream (they read U^{n+1}
+      // and write x and the second list set, which the wall kernel does not touch)
+      if (c.cv.ale && (st = move_and_prebuild(ctx, c, s))) return st;
+      if (recon_chain >= 0) CK(ctx, cudaStreamWaitEvent(s, c.ev_recon[recon_chain & 1], 0));
       if ((st = timed_begin(ctx, K_WALLS, s, &e))) return st;
       ctx->launches += launch_walls(c.cv, s);
       CKL(ctx);
       if ((st = timed_end(ctx, e, s))) return st;
-      if (c.cv.ale) {
-        if ((st = timed_begin(ctx, K_MOVE, s, &e))) return st;
-        ctx->launches += launch_move(c.cv, s);
-        CKL(ctx);
-        if ((st = timed_end(ctx, e, s))) return st;
-      }
       c.cur = 1 - c.cur;
       refresh_view(c);
     }
     ctx->steps += 1;
   }
+  for (auto& c : ctx->cases)
+    if (c.next_ready && (st = join_side(ctx, c, s))) return st;
   return BGK_OK;
 }
 
@@ -748,6 +866,7 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
     CK(ctx, cudaMemcpy(c.cv.mom, o, b, cudaMemcpyHostToDevice));
     o += b;
     c.stencils_valid = false;
+    if (int st = reset_skin(ctx, c)) return st;  // positions changed: rebuild the candidates
     c.cur = 0;
     refresh_view(c);
   }
@@ -764,7 +883,7 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   const char* why = nullptr;
   if (!check_params(*p, c.cv.n, &why)) return fail(ctx, BGK_E_INVAL, "bgk_set_params: %s", why);
   if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
-      p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic)
+      p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin)
     return fail(ctx, BGK_E_INVAL, "bgk_set_params: only kn, tau_mode, dt, wall_T, lid_u, lid_wall, ale, guard may change");
   CK(ctx, cudaDeviceSynchronize());
   c.p = *p;
@@ -774,6 +893,12 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   v.dt = p->dt;
   v.wall_T = p->wall_T;
   v.lid_wall = p->lid_wall;
+  if (v.ale != p->ale) {
+    // the points may have moved since the lists were built: rebuild them at the next step
+    int st = reset_skin(ctx, c);
+    if (st) return st;
+    c.stencils_valid = false;
+  }
   v.ale = p->ale;
   v.guard = p->guard;
   for (int a = 0; a < 3; ++a) v.lid_u[a] = p->lid_u[a];
@@ -915,7 +1040,12 @@ int bgk_get_stats(bgk_ctx* ctx, bgk_stats* out) {
   out->steps = ctx->steps;
   out->launches = ctx->launches;
   out->clamps = (int64_t)hs.clamps;
-  out->nnz = (int64_t)hs.nnz;
+  out->nnz = 0;
+  for (auto& c : ctx->cases) {
+    std::vector<int32_t> cnt(c.cv.n);
+    cudaMemcpy(cnt.data(), c.cv.cnt, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost);
+    for (int32_t v : cnt) out->nnz += v;
+  }
   out->nv_pad = ctx->cases.empty() ? 0 : ctx->cases[0].cv.NVp;
   out->n_cases = (int32_t)ctx->cases.size();
   out->batch_mode = effective_mode(ctx);
@@ -933,6 +1063,13 @@ void bgk_free(bgk_ctx* ctx) {
   cudaDeviceSynchronize();
   drop_graphs(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  for (auto& c : ctx->cases) {
+    if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+    if (c.ev_join) cudaEventDestroy(c.ev_join);
+    for (int k = 0; k < 2; ++k)
+      if (c.ev_recon[k]) cudaEventDestroy(c.ev_recon[k]);
+  }
   for (auto& e : ctx->ev) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);

@@ -12,11 +12,22 @@ namespace bgk {
 // Device status bits (reported by bgk_sync).
 enum : int32_t { ST_OVERFLOW = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
 
+// Verlet-list state of an ALE case: the largest squared displacement of an interior
+// point since the candidate build (FP32 bits, rounded up), the rebuild decision for
+// the next list build (taken by the last CTA of the motion kernel; set by the host
+// whenever positions or lists are reset), and that kernel's CTA counter.
+struct SkinState {
+  uint32_t disp2;
+  int32_t rebuild;
+  uint32_t blocks;
+  int32_t pad;
+};
+
 struct DevStatus {
   int32_t flags;
   int32_t pad;
   unsigned long long clamps;
-  unsigned long long nnz;
+
 };
 
 // Moments are stored per point as MOM_STRIDE doubles: rho, U[3], T.
@@ -63,12 +74,24 @@ struct CaseView {
   float* sk_out; // optional [n][NVp] sum_j min-terms of the upwind coefficients (diagonal of the transport)
   double* mom;   // [n][MOM_STRIDE]
   DevStatus* status;
+
+  // ALE neighbour-list skin (null / 0 when not used): candidate lists of radius h (1 + skin)
+  double skin;          // fraction of h
+  int32_t ccap;         // candidate-list capacity
+  double* xb;           // [n][dim] positions at the last candidate build
+  int32_t* ccnt;        // [n]
+  int32_t* ccol;        // [n][ccap] candidates, ascending
+  SkinState* sk;
 };
 
 // Launchers (stream-ordered; each returns the number of kernels launched).
 int launch_init_tables(const CaseView& cv, cudaStream_t s);
 int launch_neighbours(const CaseView& cv, cudaStream_t s);
-int launch_stencils(const CaseView& cv, cudaStream_t s);
+// ALE with a skin: rebuild the candidate lists if a point moved too far, then filter them.
+int launch_neighbours_skin(const CaseView& cv, cudaStream_t s);
+// part 0: all points; 1: interior stencils (all points for FP64 storage); 2: wall
+// reconstruction weights (nothing for FP64 storage).
+int launch_stencils(const CaseView& cv, cudaStream_t s, int part = 0);
 int launch_transport(const CaseView& cv, cudaStream_t s);
 // FP32 warp-per-point transport + relaxation (used by the adjoint's forward recomputation)
 int launch_transport_fp32(const CaseView& cv, cudaStream_t s);

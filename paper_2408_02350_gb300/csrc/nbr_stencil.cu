@@ -27,7 +27,9 @@ namespace bgk {
 
 static inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 
-__global__ void k_cell_assign(CaseView cv) {
+// With sk (ALE skin lists) the cell kernels run only in steps that rebuild the candidates.
+__global__ void k_cell_assign(CaseView cv, const SkinState* sk) {
+  if (sk && !sk->rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cv.n) return;
   int c = 0, stride = 1;
@@ -50,7 +52,8 @@ __global__ void k_cell_assign(CaseView cv) {
 // Exclusive scan of the cell counts into cell_start (one block of 1024 threads:
 // per-thread serial sums, warp-shuffle scans, one scan of the warp totals), then
 // clear the counts for k_cell_fill.
-__global__ void k_cell_scan(CaseView cv) {
+__global__ void k_cell_scan(CaseView cv, const SkinState* sk) {
+  if (sk && !sk->rebuild) return;
   __shared__ int32_t s_w[32];
   const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5;
   const int ncell = cv.ncell;
@@ -85,7 +88,8 @@ __global__ void k_cell_scan(CaseView cv) {
   if (t == 0) cv.cell_start[ncell] = s_w[31];
 }
 
-__global__ void k_cell_fill(CaseView cv) {
+__global__ void k_cell_fill(CaseView cv, const SkinState* sk) {
+  if (sk && !sk->rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cv.n) return;
   int c = cv.cell_of[i];
@@ -103,13 +107,18 @@ __global__ void k_cell_fill(CaseView cv) {
 // parallel, matches are compacted with a ballot into a per-warp shared buffer,
 // and the row is written in ascending order by a rank sort (every index in a
 // row is distinct, so the rank of an entry is the number of smaller entries).
-template <int DIM>
+//
+// CAND: candidate lists of the skin (radius h (1 + skin) in hi, superset test
+// d2_f <= hi, rows into ccol / ccnt, positions saved in xb), only in steps that
+// rebuild them; the cell counts are left at zero for the next rebuild.
+template <int DIM, bool CAND>
 __global__ void __launch_bounds__(256) k_neighbours_warp(CaseView cv, float lo, float hi) {
   extern __shared__ int32_t s_buf[];  // [W][cap]
+  if (CAND && !cv.sk->rebuild) return;
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * W + warp;
   if (i >= cv.n) return;  // whole warp leaves together
-  const int cap = cv.cap, nc = cv.nc;
+  const int cap = CAND ? cv.ccap : cv.cap, nc = cv.nc;
   int32_t* buf = s_buf + warp * cap;
   float xif[DIM];
 #pragma unroll
@@ -170,7 +179,9 @@ __global__ void __launch_bounds__(256) k_neighbours_warp(CaseView cv, float lo, 
                 if (cv.periodic) d = d > 0.5f ? d - 1.0f : (d < -0.5f ? d + 1.0f : d);
                 d2f = fmaf(d, d, d2f);
               }
-              if (d2f <= hi) {
+              if (CAND) {
+                inside = d2f <= hi;
+              } else if (d2f <= hi) {
                 inside = d2f <= lo;
                 if (!inside) {
                   double xi[DIM], xj[DIM];
@@ -191,36 +202,121 @@ __global__ void __launch_bounds__(256) k_neighbours_warp(CaseView cv, float lo, 
       }
   __syncwarp();
   const int mm = m < cap ? m : cap;
-  int32_t* row = cv.col + (int64_t)i * cap;
+  int32_t* row = (CAND ? cv.ccol : cv.col) + (int64_t)i * cap;
   for (int e = lane; e < mm; e += 32) {
     const int v = buf[e];
     int rank = 0;
     for (int k = 0; k < mm; ++k) rank += buf[k] < v ? 1 : 0;
     row[rank] = v;
   }
+  if (CAND) {
+    if (lane < DIM) cv.xb[(int64_t)i * DIM + lane] = cv.x[(int64_t)i * DIM + lane];
+    // cell counts back to zero for the next rebuild (only k_cell_fill read them)
+    for (int c = i * 32 + lane; c < cv.ncell; c += cv.n * 32) cv.cell_cnt[c] = 0;
+  }
   if (lane == 0) {
-    cv.cnt[i] = mm;
+    (CAND ? cv.ccnt : cv.cnt)[i] = mm;
     if (m > cap) set_status(cv.status, ST_OVERFLOW);
-    atomicAdd(&cv.status->nnz, (unsigned long long)m);
   }
 }
 
+// The exact test of k_neighbours_warp applied to the candidate list of each point
+// (ascending, so the kept entries are ascending too; one warp per point).  The
+// candidates contain every point within h: a pair within h now was within
+// h + 2 max|x - x_b| < h (1 + skin) at the build.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_filter(CaseView cv, float lo, float hi) {
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * W + warp;
+  if (i >= cv.n) return;
+  const int cap = cv.cap, nc = cv.ccnt[i];
+  const int32_t* cand = cv.ccol + (int64_t)i * cv.ccap;
+  int32_t* row = cv.col + (int64_t)i * cap;
+  float xif[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) xif[a] = cv.xf[(int64_t)i * DIM + a];
+  const double h2 = __dmul_rn(cv.h, cv.h);
+  int m = 0;
+  for (int qb = 0; qb < nc; qb += 32) {
+    const int q = qb + lane;
+    bool inside = false;
+    int j = -1;
+    if (q < nc) {
+      j = cand[q];
+      float d2f = 0.0f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        float d = cv.xf[(int64_t)j * DIM + a] - xif[a];
+        if (cv.periodic) d = d > 0.5f ? d - 1.0f : (d < -0.5f ? d + 1.0f : d);
+        d2f = fmaf(d, d, d2f);
+      }
+      if (d2f <= hi) {
+        inside = d2f <= lo;
+        if (!inside) {
+          double xi[DIM], xj[DIM];
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) { xi[a] = cv.x[(int64_t)i * DIM + a]; xj[a] = cv.x[(int64_t)j * DIM + a]; }
+          inside = dist2_d<DIM>(xi, xj, cv.periodic) <= h2;
+        }
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, inside);
+    if (inside) {
+      const int pos = m + __popc(bal & ((1u << lane) - 1u));
+      if (pos < cap) row[pos] = j;
+    }
+    m += __popc(bal);
+  }
+  if (lane == 0) {
+    cv.cnt[i] = m < cap ? m : cap;
+    if (m > cap) set_status(cv.status, ST_OVERFLOW);
+  }
+}
+
+// FP32 prefilter bounds for radius r: squared distances below lo are inside, above
+// hi outside, in between the FP64 test decides.
+static void prefilter_bounds(int dim, double r, float* lo, float* hi) {
+  const double r2 = r * r;
+  const double band = 8.0 * dim * std::ldexp(1.0, -22) / r + std::ldexp(1.0, -16);
+  *lo = band < 1.0 ? (float)(r2 * (1.0 - band)) : -1.0f;
+  *hi = (float)(r2 * (1.0 + band));
+}
+
 int launch_neighbours(const CaseView& cv, cudaStream_t s) {
-  const int B = 128;
   cudaMemsetAsync(cv.cell_cnt, 0, sizeof(int32_t) * cv.ncell, s);
-  k_cell_assign<<<grid_for(cv.n, 256), 256, 0, s>>>(cv);
-  k_cell_scan<<<1, 1024, 0, s>>>(cv);
-  k_cell_fill<<<grid_for(cv.n, 256), 256, 0, s>>>(cv);
+  k_cell_assign<<<grid_for(cv.n, 256), 256, 0, s>>>(cv, nullptr);
+  k_cell_scan<<<1, 1024, 0, s>>>(cv, nullptr);
+  k_cell_fill<<<grid_for(cv.n, 256), 256, 0, s>>>(cv, nullptr);
   const int W = 8;
-  size_t smem = sizeof(int32_t) * (size_t)cv.cap * W;
-  const double h2 = cv.h * cv.h;
-  const double band = 8.0 * cv.dim * std::ldexp(1.0, -22) / cv.h + std::ldexp(1.0, -16);
-  const float lo = band < 1.0 ? (float)(h2 * (1.0 - band)) : -1.0f;
-  const float hi = (float)(h2 * (1.0 + band));
-  (void)B;
-  if (cv.dim == 2) k_neighbours_warp<2><<<grid_for(cv.n, W), 32 * W, smem, s>>>(cv, lo, hi);
-  else k_neighbours_warp<3><<<grid_for(cv.n, W), 32 * W, smem, s>>>(cv, lo, hi);
+  const size_t smem = sizeof(int32_t) * (size_t)cv.cap * W;
+  float lo, hi;
+  prefilter_bounds(cv.dim, cv.h, &lo, &hi);
+  if (cv.dim == 2) k_neighbours_warp<2, false><<<grid_for(cv.n, W), 32 * W, smem, s>>>(cv, lo, hi);
+  else k_neighbours_warp<3, false><<<grid_for(cv.n, W), 32 * W, smem, s>>>(cv, lo, hi);
   return 4;
+}
+
+int launch_neighbours_skin(const CaseView& cv, cudaStream_t s) {
+  k_cell_assign<<<grid_for(cv.n, 256), 256, 0, s>>>(cv, cv.sk);
+  k_cell_scan<<<1, 1024, 0, s>>>(cv, cv.sk);
+  k_cell_fill<<<grid_for(cv.n, 256), 256, 0, s>>>(cv, cv.sk);
+  const int W = 8;
+  const size_t smem = sizeof(int32_t) * (size_t)cv.ccap * W;
+  float clo, chi, lo, hi;
+  prefilter_bounds(cv.dim, cv.h * (1.0 + cv.skin), &clo, &chi);
+  prefilter_bounds(cv.dim, cv.h, &lo, &hi);
+  if (cv.dim == 2) {
+    auto kc = k_neighbours_warp<2, true>;
+    cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kc<<<grid_for(cv.n, W), 32 * W, smem, s>>>(cv, clo, chi);
+    k_filter<2><<<grid_for(cv.n, W), 32 * W, 0, s>>>(cv, lo, hi);
+  } else {
+    auto kc = k_neighbours_warp<3, true>;
+    cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kc<<<grid_for(cv.n, W), 32 * W, smem, s>>>(cv, clo, chi);
+    k_filter<3><<<grid_for(cv.n, W), 32 * W, 0, s>>>(cv, lo, hi);
+  }
+  return 6;
 }
 
 // ---- stencils ----
@@ -640,23 +736,24 @@ __global__ void __launch_bounds__(256) k_recon_grp(CaseView cv) {
   }
 }
 
-int launch_stencils(const CaseView& cv, cudaStream_t s) {
+int launch_stencils(const CaseView& cv, cudaStream_t s, int part) {
   const int B = 128;
   const bool f64 = cv.storage == 0;
   if (f64) {
+    if (part == 2) return 0;
     if (cv.dim == 2) k_stencils<double, 2><<<grid_for(cv.n, B), B, 0, s>>>(cv);
     else k_stencils<double, 3><<<grid_for(cv.n, B), B, 0, s>>>(cv);
     return 1;
   }
   constexpr int LPP = 4;
   int n = 0;
-  if (cv.n_int > 0) {
+  if (cv.n_int > 0 && part != 2) {
     const int grid = grid_for((int64_t)cv.n_int * LPP, 256);
     if (cv.dim == 2) k_stencils_grp<2, LPP><<<grid, 256, 0, s>>>(cv);
     else k_stencils_grp<3, LPP><<<grid, 256, 0, s>>>(cv);
     ++n;
   }
-  if (cv.n_wall > 0) {
+  if (cv.n_wall > 0 && part != 1) {
     const int grid = grid_for((int64_t)cv.n_wall * LPP, 128);
     if (cv.dim == 2) k_recon_grp<2, LPP><<<grid, 128, 0, s>>>(cv);
     else k_recon_grp<3, LPP><<<grid, 128, 0, s>>>(cv);

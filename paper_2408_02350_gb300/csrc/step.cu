@@ -676,11 +676,13 @@ int launch_init_tables(const CaseView& cv, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // point motion (Eqs. originalALE1, ALE1)
 // ---------------------------------------------------------------------------
-__global__ void k_move(CaseView cv) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cv.n_int) return;
-  const int i = cv.int_idx[t];
+// x_i += dt U_i^{n+1} for one interior point (FP64 without fused multiply-add,
+// clamped to [guard, 1 - guard] or wrapped in a periodic box); with skin lists also
+// the FP32 split of x_i, and the squared displacement since the candidate build is
+// returned.
+__device__ __forceinline__ double move_point(const CaseView& cv, const int i) {
   unsigned long long nclamp = 0;
+  double d2 = 0.0;
   for (int a = 0; a < cv.dim; ++a) {
     double* xa = cv.x + (int64_t)i * cv.dim + a;
     double y = __dadd_rn(*xa, __dmul_rn(cv.dt, cv.mom[(int64_t)i * MOM_STRIDE + 1 + a]));
@@ -690,13 +692,58 @@ __global__ void k_move(CaseView cv) {
     } else if (y < cv.guard) { y = cv.guard; ++nclamp; }
     else if (y > 1.0 - cv.guard) { y = 1.0 - cv.guard; ++nclamp; }
     *xa = y;
+    if (cv.sk) {
+      // FP32 split for the prefilters (k_cell_assign sets it only when the cells are rebuilt)
+      const float hi = (float)y;
+      cv.xf[(int64_t)i * cv.dim + a] = hi;
+      cv.xlo[(int64_t)i * cv.dim + a] = (float)(y - (double)hi);
+      const double d = __dadd_rn(y, -cv.xb[(int64_t)i * cv.dim + a]);
+      d2 = __dadd_rn(d2, __dmul_rn(d, d));
+    }
   }
   if (nclamp) atomicAdd(&cv.status->clamps, nclamp);
+  return d2;
+}
+
+// After every CTA has merged its maximum squared displacement (bits b) into disp2,
+// the last one decides whether the next list build rebuilds the candidates.
+__device__ __forceinline__ void skin_merge(const CaseView& cv, uint32_t b, double thr2) {
+  atomicMax(&cv.sk->disp2, b);
+  __threadfence();
+  if (atomicAdd(&cv.sk->blocks, 1u) == gridDim.x - 1) {
+    __threadfence();
+    const uint32_t d = atomicOr(&cv.sk->disp2, 0u);
+    const int rb = (double)__uint_as_float(d) > thr2;
+    cv.sk->rebuild = rb;
+    if (rb) cv.sk->disp2 = 0u;
+    cv.sk->blocks = 0u;
+  }
+}
+
+// With skin lists the kernel also tracks max |x - x_b|^2; its last CTA decides
+// whether the next list build rebuilds the candidates (max |x - x_b| > h skin / 2,
+// thr2 = (h skin / 2)^2 (1 - 1e-6)).
+__global__ void __launch_bounds__(256) k_move(CaseView cv, double thr2) {
+  __shared__ uint32_t s_max[8];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const double d2 = t < cv.n_int ? move_point(cv, cv.int_idx[t]) : 0.0;
+  if (cv.sk) {
+    // CTA maximum of the displacement bits (non-negative floats order as integers)
+    const uint32_t w = __reduce_max_sync(0xffffffffu, __float_as_uint(__double2float_ru(d2)));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t b = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b = max(b, s_max[k]);
+      skin_merge(cv, b, thr2);
+    }
+  }
 }
 
 int launch_move(const CaseView& cv, cudaStream_t s) {
   if (cv.n_int == 0) return 0;
-  k_move<<<grid_for(cv.n_int, 256), 256, 0, s>>>(cv);
+  const double half = 0.5 * cv.h * cv.skin;
+  k_move<<<grid_for(cv.n_int, 256), 256, 0, s>>>(cv, half * half * (1.0 - 1e-6));
   return 1;
 }
 

@@ -36,14 +36,27 @@ def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in _declared() if not hasattr(h, n)]
     assert not missing, missing
     assert set(_declared()) <= set(lib.exported_symbols()) | {"bgk_version"}
-    assert lib.bgk_version() == 1
+    assert lib.bgk_version() == 2
 
 
-def test_params_struct_layout_matches_header(lib):
-    # bgk_params: 10 int32 + 3 doubles ... checked by size and field offsets against the C layout rules
-    q = lib.bgk_params
-    assert q.dt.offset % 8 == 0 and q.lid_u.offset % 8 == 0
-    assert C.sizeof(q) == q.lid_u.offset + 24
+@pytest.mark.parametrize("struct", ["bgk_params", "bgk_stats"])
+def test_struct_layout_matches_header(lib, struct, tmp_path):
+    # sizes and field offsets of the ctypes mirrors against a C compiler's view of include/bgk.h
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    q = getattr(lib, struct)
+    names = [f[0] for f in q._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {n}));\n' for n in names)
+    src.write_text(f'#include <stddef.h>\n#include <stdio.h>\n#include "bgk.h"\nint main(void) {{\n'
+                   f'  printf("%zu\\n", sizeof({struct}));\n{body}  return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == C.sizeof(q)
+    assert out[1:] == [getattr(q, n).offset for n in names]
 
 
 @pytest.mark.parametrize("field,value", [("dim", 4), ("nv", 1), ("nv", 65), ("storage", 3), ("max_nbrs", 0),
