@@ -38,10 +38,13 @@ WORKLOAD = "cavity2d_ale_n201_v32_f32"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 N_SM = 152
 FP32_LANES_PER_SM = 128
-# FP32 lane-instructions per (point, neighbour, velocity) of the upwind transport:
-# 2D: two projections c.P_d (2 each), two min(., 0), one add, sk +=, acc_g, acc_h  -> 10
-# 3D: three projections (3 each), three min, two adds, sk +=, acc                  -> 16
-OPS_PER_PAIR = {2: 10, 3: 16}
+# Algorithmic FP32 lane-instructions per (point, neighbour, velocity) of the upwind
+# transport, the smallest count the scheme admits: d projections abar_d (c.e_d), one FMA
+# each from a base shared along a row of the velocity grid; c.coef, one FMA; d FMAs
+# with |.| operand modifiers for the dissipation sum_d |abar_d c.e_d|; then per component
+# (2D: g and h) one difference f_j - f_i and one accumulation.  2D: 2+1+2+2+2 = 9,
+# 3D: 3+1+3+1+1 = 9.
+OPS_PER_PAIR = {2: 9, 3: 9}
 
 
 def _peaks():
@@ -127,6 +130,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def transport_source_sha() -> str:
+    """Hash of the sources that define the transport kernel (step.cu and its headers)."""
+    d = os.path.join(ROOT, "paper_2408_02350_gb300", "csrc")
+    hs = hashlib.sha256()
+    for f in ("step.cu", "transport_wp.cuh", "device_common.cuh", "bgk_internal.cuh"):
+        hs.update(open(os.path.join(d, f), "rb").read())
+    return hs.hexdigest()[:16]
+
+
 def _traffic_record(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -136,8 +148,7 @@ def _traffic_record(kernel: str, workload: str):
         rec = json.load(open(path))
     except ValueError:
         return None
-    src = os.path.join(ROOT, "paper_2408_02350_gb300", "csrc", "step.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = transport_source_sha()
     r = rec.get(kernel + ":" + workload)
     if not r or r.get("source_sha") != h:
         return None

@@ -127,7 +127,8 @@ int bgk_get_f(bgk_ctx* ctx, int32_t c, void* f, int32_t dtype, int32_t on_device
  * bgk_step does this itself: every step when ale = 1, once otherwise. */
 int bgk_neighbours(bgk_ctx* ctx, void* stream);
 
-/* Host copy of case c's neighbour lists as CSR: rowptr[n+1], col[cap].
+/* Host copy of case c's neighbour lists as CSR: rowptr[n+1], col[cap]: the
+ * lists the last step used (after bgk_neighbours: the lists it built).
  * *nnz receives the pair count; BGK_E_INVAL if cap < nnz.  Synchronous. */
 int bgk_get_neighbours(bgk_ctx* ctx, int32_t c, int64_t* rowptr, int32_t* col, int64_t cap, int64_t* nnz);
 
@@ -142,7 +143,10 @@ int bgk_get_stencils(bgk_ctx* ctx, int32_t c, double* P, double* recon, int64_t 
  * Sec. 3.2: positive upwind transport f~ = f - dt (v - U^n).grad f (Sec. 3.4.2),
  * moments of f~ (Eqs. fullmoment1a, moment1a, moment1b), implicit BGK
  * relaxation f^{n+1} = (tau f~ + dt M^{n+1}) / (tau + dt), diffuse-reflection
- * walls, and with ale = 1 the motion x^{n+1} = x^n + dt U^{n+1}.  Asynchronous. */
+ * walls, and with ale = 1 the motion x^{n+1} = x^n + dt U^{n+1}.  Asynchronous:
+ * with ale = 1 the motion and the next step's lists run on an internal stream
+ * concurrently with the wall kernel, and every such piece of work is ordered
+ * before later work on `stream` when the call returns. */
 int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream);
 
 /* Case c's stored moments: rho[n], u[n][dim], T[n] (interior points: moments
