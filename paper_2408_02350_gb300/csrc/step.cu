@@ -301,18 +301,28 @@ static void launch_transport_d(const CaseView& cv, cudaStream_t s) {
   }
 }
 
+// Shared memory of the warp-per-point kernels with W warps: velocity nodes, lists,
+// stencils, compensated moment sums.
+template <int DIM>
+__host__ __device__ inline size_t wp_smem_bytes(int W, int cap) {
+  return 256 * W + align16(sizeof(int32_t) * cap * W) + sizeof(float) * cap * DIM * DIM * W +
+         sizeof(float) * kahan_floats<DIM>() * W;
+}
+
 template <typename S, int DIM, bool ALE, bool ROW, int VPL>
-__global__ void __launch_bounds__(256, VPL == 4 ? 3 : 2) k_transport_wp(const CaseView cv) {
+__global__ void __launch_bounds__(256, VPL == 4 ? 4 : 2) k_transport_wp(const CaseView cv) {
   constexpr int DD = DIM * DIM;
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const int cap = cv.cap;
   float* s_v = reinterpret_cast<float*>(smem) + warp * 64;
   int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * cap;
-  float* s_P = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W)) + (size_t)warp * cap * DD;
+  float* s_P0 = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W));
+  float* s_P = s_P0 + (size_t)warp * cap * DD;
+  float* s_k = s_P0 + (size_t)W * cap * DD + warp * kahan_floats<DIM>();
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
-  transport_point_wp<S, DIM, ALE, ROW, VPL>(cv, cv.int_idx[t], s_v, s_col, s_P);
+  transport_point_wp<S, DIM, ALE, ROW, VPL, VPL == 4>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
 }
 
 // Many cases in one persistent launch: items[k] = (case, interior slot), tiles of W
@@ -326,7 +336,9 @@ __global__ void __launch_bounds__(256, 3) k_transport_batch(const CaseView* __re
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
   float* s_v = reinterpret_cast<float*>(smem) + warp * 64;
   int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * capmax;
-  float* s_P = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * capmax * W)) + (size_t)warp * capmax * DD;
+  float* s_P0 = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * capmax * W));
+  float* s_P = s_P0 + (size_t)warp * capmax * DD;
+  float* s_k = s_P0 + (size_t)W * capmax * DD + warp * kahan_floats<DIM>();
   for (int tile = blockIdx.x; tile * W < n_items; tile += gridDim.x) {
     const int it = tile * W + warp;
     if (it >= n_items) continue;
@@ -335,11 +347,11 @@ __global__ void __launch_bounds__(256, 3) k_transport_batch(const CaseView* __re
     const int i = cv.int_idx[e.y];
     const bool row4 = cv.nv % 4 == 0;
     if (cv.ale) {
-      if (row4) transport_point_wp<S, DIM, true, true, 4>(cv, i, s_v, s_col, s_P);
-      else transport_point_wp<S, DIM, true, false, 4>(cv, i, s_v, s_col, s_P);
+      if (row4) transport_point_wp<S, DIM, true, true, 4, false>(cv, i, s_v, s_col, s_P, s_k);
+      else transport_point_wp<S, DIM, true, false, 4, false>(cv, i, s_v, s_col, s_P, s_k);
     } else {
-      if (row4) transport_point_wp<S, DIM, false, true, 4>(cv, i, s_v, s_col, s_P);
-      else transport_point_wp<S, DIM, false, false, 4>(cv, i, s_v, s_col, s_P);
+      if (row4) transport_point_wp<S, DIM, false, true, 4, false>(cv, i, s_v, s_col, s_P, s_k);
+      else transport_point_wp<S, DIM, false, false, 4, false>(cv, i, s_v, s_col, s_P, s_k);
     }
     __syncwarp();
   }
@@ -354,7 +366,7 @@ int transport_vpl = 0;  // 0 = automatic; 4 or 8 forces a width
 template <typename S, int DIM>
 static void launch_transport_wp(const CaseView& cv, cudaStream_t s) {
   const int W = 8, threads = 32 * W;
-  const size_t smem = 256 * W + align16(sizeof(int32_t) * cv.cap * W) + sizeof(float) * cv.cap * DIM * DIM * W;
+  const size_t smem = wp_smem_bytes<DIM>(W, cv.cap);
   const int grid = (cv.n_int + W - 1) / W;
   const bool row4 = cv.nv % 4 == 0, row8 = cv.nv % 8 == 0 && cv.NVp % 8 == 0;
   const bool v8 = transport_vpl == 8 ? (cv.NVp % 8 == 0) : (transport_vpl == 4 ? false : (DIM == 3 && row8));
@@ -521,8 +533,7 @@ int launch_transport_batch(const CaseView* d_cases, const int2* items, int n_ite
                            int warps, int grid, cudaStream_t s) {
   if (n_items == 0) return 0;
   const int threads = 32 * warps;
-  const int DD = dim * dim;
-  const size_t smem = 256 * warps + align16(sizeof(int32_t) * capmax * warps) + sizeof(float) * capmax * DD * warps;
+  const size_t smem = dim == 2 ? wp_smem_bytes<2>(warps, capmax) : wp_smem_bytes<3>(warps, capmax);
   const int ntiles = (n_items + warps - 1) / warps;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
 #define BGK_BATCH(S, D)                                                                    \

@@ -231,12 +231,20 @@ __device__ __forceinline__ void finish_point(const CaseView& cv, const int i, co
 }
 
 // The per-point body, shared by the single-case kernel and the batched kernel:
-// one warp, point i of case cv; s_v, s_col, s_P are this warp's shared buffers
-// (nv, cap and cap * dim^2 entries).  Each lane owns VPL consecutive velocities of
-// every (32 VPL)-velocity slice.
-template <typename S, int DIM, bool ALE, bool ROW, int VPL>
+// one warp, point i of case cv; s_v, s_col, s_P, s_k are this warp's shared buffers
+// (nv, cap, cap * dim^2 and kahan_floats(DIM) entries).  Each lane owns VPL
+// consecutive velocities of every (32 VPL)-velocity slice.  With KS the lanes'
+// compensated moment sums live in s_k between slices and the velocities are
+// recomputed after the neighbour loop, which keeps the 4-velocity body within 64
+// registers (4 CTAs of 8 warps per SM: 0.432 against 0.465 ms at 3 CTAs on the
+// 201^2 x 32^2 ALE cavity); without KS they stay in registers (the 8-velocity 3D
+// body and the batched kernel, which lose with KS).
+template <int DIM>
+__host__ __device__ constexpr int kahan_floats() { return 2 * (DIM + 2) * 32; }
+
+template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool KS>
 __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
-                                                   float* s_P) {
+                                                   float* s_P, float* s_k) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   constexpr int DD = DIM * DIM;
   constexpr int NP = VPL / 2;  // velocity pairs per lane
@@ -263,18 +271,25 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
   const S* fbase = reinterpret_cast<const S*>(cv.f_in);
   const float two_dt = (float)(2.0 * cv.dt);
 
-  float msum[DIM + 2], mcmp[DIM + 2];
+  // KS: s_k[q * 32 + lane] holds running sum q (q < DIM + 2) and its compensation
+  // (q >= DIM + 2); otherwise rsum / rcmp do
+  float rsum[DIM + 2], rcmp[DIM + 2];
 #pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) { msum[q] = 0.0f; mcmp[q] = 0.0f; }
+  for (int q = 0; q < DIM + 2; ++q) { rsum[q] = 0.0f; rcmp[q] = 0.0f; }
+  if (KS) {
+#pragma unroll
+    for (int q = 0; q < 2 * (DIM + 2); ++q) s_k[q * 32 + lane] = 0.0f;
+  }
 
   for (int sl = 0; sl < nslice; ++sl) {
     const int chunk = sl * 32 + lane;
     if (chunk >= nchunk) break;
     const int k0 = VPL * chunk;
+    float acc[NC][VPL], sk[VPL];
     float vel[VPL][DIM];
     bool kin[VPL];
     chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
-    float acc[NC][VPL], sk[VPL];
+    {
     const S* fj0 = fbase + k0;
     if (ROW) {
       // velocity pairs in packed FP32x2 arithmetic; the pairs share (v_y, v_z)
@@ -345,9 +360,24 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
         }
       }
     }
-    slice_out<S, DIM, NC, VPL>(cv, i, k0, vel, kin, acc, sk, two_dt, msum, mcmp);
+    }
+    if (KS) {
+      // the velocities again (not held in registers across the neighbour loop)
+      chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+    }
+    slice_out<S, DIM, NC, VPL>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
+    if (KS) {
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
+    }
   }
-  finish_point<S, DIM, ROW, VPL>(cv, i, s_v, msum, mcmp);
+  if (KS) {
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+  }
+  finish_point<S, DIM, ROW, VPL>(cv, i, s_v, rsum, rcmp);
 }
 
 }  // namespace bgk
