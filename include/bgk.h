@@ -117,7 +117,9 @@ int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, v
 /* Copy case c's distribution in or out, layout [n][ncomp][NV] with element
  * type dtype (bgk_storage), from/to host memory (on_device = 0) or device
  * memory (on_device = 1).  bgk_set_f also recomputes the stored moments.
- * Host copies are staged and synchronous; device copies are stream-ordered. */
+ * Host copies are synchronous (direct between host memory and the distribution
+ * buffer when dtype is the storage type and NV needs no padding, else staged
+ * and converted on the device); device copies are stream-ordered. */
 int bgk_set_f(bgk_ctx* ctx, int32_t c, const void* f, int32_t dtype, int32_t on_device, void* stream);
 int bgk_get_f(bgk_ctx* ctx, int32_t c, void* f, int32_t dtype, int32_t on_device, void* stream);
 

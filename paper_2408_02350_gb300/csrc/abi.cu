@@ -609,13 +609,18 @@ int bgk_set_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype, int32_t on
   const size_t esz = dtype == 0 ? 8 : (dtype == 1 ? 4 : 2);
   const size_t bytes = (size_t)c.cv.n * c.cv.ncomp * c.cv.NV * esz;
   const void* src = f;
-  if (!on_device) {
-    int st = ensure_staging(ctx, bytes);
-    if (st) return st;
-    CK(ctx, cudaMemcpyAsync(ctx->staging, f, bytes, cudaMemcpyHostToDevice, s));
-    src = ctx->staging;
+  const bool direct = dtype == c.cv.storage && c.cv.NV == c.cv.NVp;  // same element type, no padding
+  if (!on_device && direct) {
+    CK(ctx, cudaMemcpyAsync(c.f[c.cur], f, bytes, cudaMemcpyHostToDevice, s));
+  } else {
+    if (!on_device) {
+      int st = ensure_staging(ctx, bytes);
+      if (st) return st;
+      CK(ctx, cudaMemcpyAsync(ctx->staging, f, bytes, cudaMemcpyHostToDevice, s));
+      src = ctx->staging;
+    }
+    ctx->launches += launch_pack_f(c.cv, src, dtype, c.f[c.cur], s);
   }
-  ctx->launches += launch_pack_f(c.cv, src, dtype, c.f[c.cur], s);
   ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
   CKL(ctx);
   if (!on_device) CK(ctx, cudaStreamSynchronize(s));
@@ -633,6 +638,11 @@ int bgk_get_f(bgk_ctx* ctx, int32_t ci, void* f, int32_t dtype, int32_t on_devic
   if (on_device) {
     ctx->launches += launch_unpack_f(c.cv, c.f[c.cur], f, dtype, s);
     CKL(ctx);
+    return BGK_OK;
+  }
+  if (dtype == c.cv.storage && c.cv.NV == c.cv.NVp) {  // same element type, no padding: direct copy
+    CK(ctx, cudaMemcpyAsync(f, c.f[c.cur], bytes, cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
     return BGK_OK;
   }
   int st = ensure_staging(ctx, bytes);
