@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 2
+#define BGK_ABI_VERSION 3
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -82,6 +82,9 @@ typedef struct bgk_params {
                         point has moved more than h skin / 2 since the last build.  The
                         lists equal those of a full search every step; 0 turns it off.
                         Fixed at bgk_init. */
+  int32_t spare_points; /* room for points that bgk_manage may add beyond the initial
+                           count (every per-point array holds n + spare_points) */
+  int32_t pad2_;
 } bgk_params;
 
 typedef struct bgk_stats {
@@ -175,6 +178,24 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size);
  * velocity grid, the storage and the neighbour settings must stay the same
  * (BGK_E_INVAL otherwise).  Synchronous. */
 int bgk_set_params(bgk_ctx* ctx, int32_t c, const bgk_params* p);
+
+/* Point management of case c between steps (Sec. 3.5.2, adding and removing
+ * points), one pass on the current positions:
+ *  - interior points that are each other's nearest interior neighbour and closer
+ *    than rmin (absolute distance) are replaced by one point at their midpoint;
+ *  - an interior point in no such pair with fewer than min_nbrs neighbours gets a
+ *    new interior point at x_i - (h/2) c/|c|, c the sum of its neighbour
+ *    separations, when that position lies in [guard, 1 - guard]^dim (wrapped in a
+ *    periodic box) and no point of N(i) + {i} is within rmin of it;
+ *  - f at a new position is the linear WLS reconstruction there from N(i) + {i};
+ *    the stored moments of every point are recomputed from f.
+ * Surviving points keep their order (a merged pair keeps the smaller index);
+ * added points follow in the order of the points that made them, up to the
+ * capacity n + spare_points (later additions are dropped).  Point indices change:
+ * host arrays of per-point data must be re-read.  counts (host, int64[3])
+ * receives the new point count, the points removed by merging and the points
+ * added.  Synchronous. */
+int bgk_manage(bgk_ctx* ctx, int32_t c, double rmin, int32_t min_nbrs, int64_t* counts, void* stream);
 
 /* Objective of the current state of case c, not in the paper: the x-momentum flux
  * through the lid plane averaged over the lid points,

@@ -106,6 +106,8 @@ def lib():
                 "or_run": (C.c_int, [_PP, C.c_int64, _PD, _PI, _PD, _PD, _PD, _PD, _PD, C.c_int32, _PL]),
                 "or_adjoint_step": (C.c_int, [_PP, C.c_int64, _PI, _PD, _PI, _PI, _PD, _PD, _PD, _PD, _PD, _PD, _PD]),
                 "or_objective": (C.c_double, [_PP, C.c_int64, _PI, _PD, _PD, C.c_double]),
+                "or_manage": (C.c_int64, [_PP, C.c_int64, _PD, _PI, _PD, _PD, _PI, _PI, C.c_double, C.c_int32,
+                                          C.c_int64, _PD, _PI, _PD, _PD, _PL, _PL]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(h, name)
@@ -287,6 +289,30 @@ def boundary(p: dict, kind, normal, cnt, col, st: dict, f, rho, U, T) -> int:
 def move(p: dict, kind, U, x) -> int:
     q = params(p)
     return lib().or_move(C.byref(q), x.shape[0], _i(_i32(kind)), _d(_f64(U)), _d(x))
+
+
+def manage(p: dict, x, kind, normal, f, cnt, col, rmin: float, min_nbrs: int, cap_out: int | None = None):
+    """One pass of point management (Sec. 3.5.2): merge mutually nearest interior pairs
+    closer than rmin at their midpoint, add points into holes next to interior points
+    with fewer than min_nbrs neighbours; f at new positions by linear WLS
+    reconstruction.  Returns dict(x, kind, normal, f, origin, merges, adds)."""
+    q = params(p)
+    x, f = _f64(x), _f64(f)
+    n, dim = x.shape
+    cap_out = int(cap_out if cap_out is not None else 2 * n)
+    xo = np.zeros((cap_out, dim))
+    ko = np.zeros(cap_out, dtype=np.int32)
+    no = np.zeros((cap_out, dim))
+    fo = np.zeros((cap_out,) + f.shape[1:])
+    org = np.zeros(cap_out, dtype=np.int64)
+    counts = np.zeros(2, dtype=np.int64)
+    m = lib().or_manage(C.byref(q), n, _d(x), _i(_i32(kind)), _d(_f64(normal)), _d(f), _i(_i32(cnt)), _i(_i32(col)),
+                        float(rmin), int(min_nbrs), cap_out, _d(xo), _i(ko), _d(no), _d(fo),
+                        org.ctypes.data_as(_PL), counts.ctypes.data_as(_PL))
+    if m < 0:
+        raise MemoryError("or_manage")
+    return {"x": xo[:m].copy(), "kind": ko[:m].copy(), "normal": no[:m].copy(), "f": fo[:m].copy(),
+            "origin": org[:m].copy(), "merges": int(counts[0]), "adds": int(counts[1])}
 
 
 def adjoint_step(p: dict, kind, normal, cnt, col, st: dict, f, lam1):

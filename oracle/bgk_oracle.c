@@ -449,6 +449,185 @@ int or_stencils(const or_params* p, int64_t n, const double* x, const int32_t* k
   return status;
 }
 
+/* ---- point management (Sec. 3.5.2: removing and adding points) ---- */
+
+/* Linear WLS reconstruction at the position y from the points k in src[0..m): p_k =
+ * (1, x_k - y), w_k = exp(-alpha |x_k - y|^2 / h^2) (no cutoff), r_k = e_0^T (sum w p p^T)^-1
+ * w_k p_k, so that f(y) = sum_k r_k f_k reproduces linear fields; the constant fit
+ * w_k / sum w where m < dim + 1 or the system is singular. */
+static void recon_at(const or_params* p, const double* y, const double* x, const int32_t* src, int m, double* r) {
+  const int dim = p->dim, mm = dim + 1;
+  double B[16] = {0}, Binv[16];
+  for (int s = 0; s < m; ++s) {
+    const double* xk = x + (int64_t)src[s] * dim;
+    double pk[4];
+    pk[0] = 1.0;
+    for (int a = 0; a < dim; ++a) pk[1 + a] = sep(y[a], xk[a], p->periodic);
+    double w = exp(-p->alpha * dist2(dim, y, xk, p->periodic) / (p->h * p->h));
+    for (int u = 0; u < mm; ++u)
+      for (int v = 0; v < mm; ++v) B[u * mm + v] += w * pk[u] * pk[v];
+  }
+  if (m < mm || gj_inverse(mm, B, Binv) != OR_OK) {
+    double wsum = 0.0;
+    for (int s = 0; s < m; ++s) {
+      const double* xk = x + (int64_t)src[s] * dim;
+      r[s] = exp(-p->alpha * dist2(dim, y, xk, p->periodic) / (p->h * p->h));
+      wsum += r[s];
+    }
+    for (int s = 0; s < m; ++s) r[s] /= wsum;
+    return;
+  }
+  for (int s = 0; s < m; ++s) {
+    const double* xk = x + (int64_t)src[s] * dim;
+    double pk[4];
+    pk[0] = 1.0;
+    for (int a = 0; a < dim; ++a) pk[1 + a] = sep(y[a], xk[a], p->periodic);
+    double w = exp(-p->alpha * dist2(dim, y, xk, p->periodic) / (p->h * p->h));
+    double acc = 0.0;
+    for (int b = 0; b < mm; ++b) acc += Binv[b] * pk[b];
+    r[s] = w * acc;
+  }
+}
+
+/*
+ * One pass of point management on the neighbour lists cnt/col of x (radius h).
+ * Readings (the paper names the operations, not their thresholds):
+ *  - remove: interior points i and j that are each other's nearest interior
+ *    neighbour (ties to the smaller index) and closer than rmin are replaced by
+ *    one point at their midpoint (the survivor keeps i's slot, i < j);
+ *  - add: an interior point i that takes part in no merge and has fewer than
+ *    min_nbrs neighbours gets a new interior point at x_i - (h/2) c/|c|, c the
+ *    sum of the separations to its neighbours (away from them, into the hole),
+ *    if that position lies in [guard, 1 - guard]^dim (wrapped in a periodic box)
+ *    and no point of N(i) + {i} is closer than rmin to it;
+ *  - f at a new position y is the linear WLS reconstruction at y from
+ *    N(i) + {i} (all point kinds), the least-squares update of the paper.
+ * Output: the surviving points in index order (survivor slots take the
+ * midpoint), then the added points in the order of the points that made them;
+ * at most cap_out points (later additions are dropped).  origin[k] is the old
+ * index of output point k, -1 for an added point.  counts[0] = merged pairs,
+ * counts[1] = added points.  Returns the new point count.
+ */
+int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t* kind, const double* normal,
+                  const double* f, const int32_t* cnt, const int32_t* col, double rmin, int32_t min_nbrs,
+                  int64_t cap_out, double* x_out, int32_t* kind_out, double* normal_out, double* f_out,
+                  int64_t* origin, int64_t* counts) {
+  const int dim = p->dim, cap = p->max_nbrs;
+  const int64_t NV = nvel_of(dim, p->nv), row = (int64_t)ncomp_of(dim) * NV;
+  const double rmin2 = rmin * rmin;
+  int64_t* nn = (int64_t*)malloc(sizeof(int64_t) * n);
+  int32_t* role = (int32_t*)calloc(n, sizeof(int32_t)); /* 0 keep, 1 merge survivor, 2 merged away, 3 adds */
+  double* ynew = (double*)malloc(sizeof(double) * n * dim);
+  int32_t* src = (int32_t*)malloc(sizeof(int32_t) * (cap + 1));
+  double* r = (double*)malloc(sizeof(double) * (cap + 1));
+  if (!nn || !role || !ynew || !src || !r) { free(nn); free(role); free(ynew); free(src); free(r); return -1; }
+  /* nearest interior neighbour */
+  for (int64_t i = 0; i < n; ++i) {
+    nn[i] = -1;
+    if (kind[i] != 0) continue;
+    double best = 0.0;
+    for (int s = 0; s < cnt[i]; ++s) {
+      int32_t j = col[i * cap + s];
+      if (kind[j] != 0) continue;
+      double d2 = dist2(dim, x + i * dim, x + (int64_t)j * dim, p->periodic);
+      if (nn[i] < 0 || d2 < best) { nn[i] = j; best = d2; }
+    }
+    if (nn[i] >= 0 && !(best < rmin2)) nn[i] = -1;
+  }
+  /* mutual nearest pairs closer than rmin */
+  int64_t merges = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t j = nn[i];
+    if (j > i && nn[j] == i) { role[i] = 1; role[j] = 2; ++merges; }
+  }
+  /* additions into holes */
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != 0 || role[i] != 0 || cnt[i] >= min_nbrs || cnt[i] == 0) continue;
+    const double* xi = x + i * dim;
+    double c[3] = {0.0, 0.0, 0.0}, c2 = 0.0;
+    for (int s = 0; s < cnt[i]; ++s) {
+      const double* xj = x + (int64_t)col[i * cap + s] * dim;
+      for (int a = 0; a < dim; ++a) c[a] = c[a] + sep(xi[a], xj[a], p->periodic);
+    }
+    for (int a = 0; a < dim; ++a) c2 = c2 + c[a] * c[a];
+    if (!(c2 > 0.0)) continue;
+    const double cl = sqrt(c2), step = 0.5 * p->h;
+    double* y = ynew + i * dim;
+    int ok = 1;
+    for (int a = 0; a < dim; ++a) {
+      double ya = xi[a] - step * (c[a] / cl);
+      if (p->periodic) {
+        if (ya >= 1.0) ya -= 1.0;
+        else if (ya < 0.0) ya += 1.0;
+      } else if (ya < p->guard || ya > 1.0 - p->guard) {
+        ok = 0;
+      }
+      y[a] = ya;
+    }
+    if (!ok) continue;
+    if (dist2(dim, y, xi, p->periodic) < rmin2) continue;
+    for (int s = 0; s < cnt[i] && ok; ++s)
+      if (dist2(dim, y, x + (int64_t)col[i * cap + s] * dim, p->periodic) < rmin2) ok = 0;
+    if (ok) role[i] = 3;
+  }
+  /* output: survivors, then additions */
+  int64_t k = 0;
+  for (int64_t i = 0; i < n && k < cap_out; ++i) {
+    if (role[i] == 2) continue;
+    for (int a = 0; a < dim; ++a) normal_out[k * dim + a] = normal[i * dim + a];
+    kind_out[k] = kind[i];
+    origin[k] = i;
+    if (role[i] == 1) {
+      const int64_t j = nn[i];
+      double* y = x_out + k * dim;
+      for (int a = 0; a < dim; ++a) {
+        double ya = x[i * dim + a] + 0.5 * sep(x[i * dim + a], x[j * dim + a], p->periodic);
+        if (p->periodic) {
+          if (ya >= 1.0) ya -= 1.0;
+          else if (ya < 0.0) ya += 1.0;
+        }
+        y[a] = ya;
+      }
+      int m = 0;
+      src[m++] = (int32_t)i;
+      for (int s = 0; s < cnt[i]; ++s) src[m++] = col[i * cap + s];
+      recon_at(p, y, x, src, m, r);
+      for (int64_t q = 0; q < row; ++q) {
+        double acc = 0.0;
+        for (int s = 0; s < m; ++s) acc += r[s] * f[(int64_t)src[s] * row + q];
+        f_out[k * row + q] = acc;
+      }
+    } else {
+      for (int a = 0; a < dim; ++a) x_out[k * dim + a] = x[i * dim + a];
+      memcpy(f_out + k * row, f + i * row, sizeof(double) * row);
+    }
+    ++k;
+  }
+  int64_t adds = 0;
+  for (int64_t i = 0; i < n && k < cap_out; ++i) {
+    if (role[i] != 3) continue;
+    const double* y = ynew + i * dim;
+    for (int a = 0; a < dim; ++a) { x_out[k * dim + a] = y[a]; normal_out[k * dim + a] = 0.0; }
+    kind_out[k] = 0;
+    origin[k] = -1;
+    int m = 0;
+    src[m++] = (int32_t)i;
+    for (int s = 0; s < cnt[i]; ++s) src[m++] = col[i * cap + s];
+    recon_at(p, y, x, src, m, r);
+    for (int64_t q = 0; q < row; ++q) {
+      double acc = 0.0;
+      for (int s = 0; s < m; ++s) acc += r[s] * f[(int64_t)src[s] * row + q];
+      f_out[k * row + q] = acc;
+    }
+    ++k;
+    ++adds;
+  }
+  counts[0] = merges;
+  counts[1] = adds;
+  free(nn); free(role); free(ynew); free(src); free(r);
+  return k;
+}
+
 /* ---- explicit transport with the positive upwind flux (Eq. explicit, Sec. 3.4.2) ---- */
 
 static double sgn(double a) { return a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0); }

@@ -41,6 +41,7 @@ class bgk_params(C.Structure):
         ("max_nbrs", C.c_int32), ("storage", C.c_int32),
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
         ("guard", C.c_double), ("lid_u", C.c_double * 3), ("skin", C.c_double),
+        ("spare_points", C.c_int32), ("pad2_", C.c_int32),
     ]
 
 
@@ -76,6 +77,7 @@ _SIGS = {
     "bgk_last_error": (C.c_char_p, [_P]),
     "bgk_free": (None, [_P]),
     "bgk_set_params": (C.c_int, [_P, C.c_int32, C.POINTER(bgk_params)]),
+    "bgk_manage": (C.c_int, [_P, C.c_int32, C.c_double, C.c_int32, _PL, _P]),
     "bgk_set_batching": (C.c_int, [_P, C.c_int32]),
     "bgk_autotune": (C.c_int, [_P, _P]),
     "bgk_objective": (C.c_int, [_P, C.c_int32, _P, _P, C.c_double, _P]),
@@ -248,6 +250,13 @@ def bgk_set_params(ctx, case: int, params) -> None:
     _check(lib().bgk_set_params(ctx, case, C.byref(q)), ctx)
 
 
+def bgk_manage(ctx, case: int, rmin: float, min_nbrs: int, stream=None):
+    """One point-management pass; returns (new point count, removed by merging, added)."""
+    counts = (C.c_int64 * 3)()
+    _check(lib().bgk_manage(ctx, case, float(rmin), int(min_nbrs), counts, _stream_ptr(stream)), ctx)
+    return int(counts[0]), int(counts[1]), int(counts[2])
+
+
 def bgk_set_batching(ctx, mode: int) -> None:
     _check(lib().bgk_set_batching(ctx, mode), ctx)
 
@@ -294,6 +303,7 @@ def params_from(p: dict) -> bgk_params:
     for a in range(3):
         q.lid_u[a] = float(lu[a])
     q.skin = float(p.get("skin", 0.2 if q.ale else 0.0))
+    q.spare_points = int(p.get("spare_points", 0))
     return q
 
 
@@ -354,6 +364,12 @@ class Solver:
 
     def step(self, nsteps: int = 1, stream=None):
         bgk_step(self.ctx, nsteps, stream)
+
+    def manage(self, rmin: float, min_nbrs: int, case: int = 0, stream=None):
+        """Point management pass; updates the point count; returns (n, removed, added)."""
+        n, removed, added = bgk_manage(self.ctx, case, rmin, min_nbrs, stream)
+        self.n[case] = n
+        return n, removed, added
 
     def sync(self, stream=None):
         bgk_sync(self.ctx, stream)

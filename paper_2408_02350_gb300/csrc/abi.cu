@@ -65,6 +65,11 @@ struct CaseHost {
   // of the step that uses that set waits for
   cudaEvent_t ev_recon[2] = {nullptr, nullptr};
   int64_t chain = 0;
+  int64_t cap_n = 0;  // capacity of the per-point arrays (initial points + spare_points)
+  // point management scratch (allocated on first use, cap_n entries)
+  int32_t *pm_nn = nullptr, *pm_role = nullptr, *pm_newidx = nullptr, *pm_addidx = nullptr, *pm_totals = nullptr;
+  int32_t *pm_kind2 = nullptr, *pm_int2 = nullptr;
+  double *pm_ynew = nullptr, *pm_x2 = nullptr, *pm_norm2 = nullptr;
 };
 
 }  // namespace
@@ -171,6 +176,7 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
   if (n < 1 || n > (int64_t)1 << 30) { *why = "point count must be in [1, 2^30]"; return 0; }
   if (p.guard < 0 || p.guard >= 0.5) { *why = "guard must be in [0, 0.5)"; return 0; }
   if (!(p.skin >= 0 && p.skin <= 1)) { *why = "skin must be in [0, 1]"; return 0; }
+  if (p.spare_points < 0 || n + p.spare_points > (int64_t)1 << 30) { *why = "spare_points out of range"; return 0; }
   return 1;
 }
 
@@ -271,7 +277,7 @@ int move_and_prebuild(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
     CK(ctx, cudaEventCreateWithFlags(&c.ev_recon[1], cudaEventDisableTiming));
   }
   if (!c.nx_cnt) {
-    const size_t n = c.cv.n, cap = c.cv.cap, dim = c.cv.dim;
+    const size_t n = c.cap_n, cap = c.cv.cap, dim = c.cv.dim;
     if ((st = dalloc(ctx, &c.nx_cnt, n))) return st;
     if ((st = dalloc(ctx, &c.nx_col, n * cap))) return st;
     if ((st = dalloc_bytes(ctx, &c.nx_P, n * cap * dim * dim * c.c_bytes))) return st;
@@ -511,19 +517,22 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.n_wall = (int32_t)wall.size();
     c.nlid = 0;
     for (int64_t i = 0; i < n; ++i) c.nlid += kind[off + i] == q.lid_wall && q.lid_wall != 0;
+    // per-point arrays hold cap_n = n + spare_points points (room for added points)
+    const int64_t ncap = n + q.spare_points;
+    c.cap_n = ncap;
     std::vector<int32_t> wall_of(n, -1);
     for (size_t w = 0; w < wall.size(); ++w) wall_of[wall[w]] = (int32_t)w;
-    if ((st = dalloc(ctx, &c.wall_of, n))) return bail(st);
+    if ((st = dalloc(ctx, &c.wall_of, ncap))) return bail(st);
     if (cudaMemcpy(c.wall_of, wall_of.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(ctx, BGK_E_CUDA, "case %d: wall map upload failed", ci));
 
     double* dx = nullptr;
     int32_t *dkind = nullptr, *dint = nullptr, *dwall = nullptr;
     double* dnorm = nullptr;
-    if ((st = dalloc(ctx, &dx, n * dim))) return bail(st);
-    if ((st = dalloc(ctx, &dkind, n))) return bail(st);
-    if ((st = dalloc(ctx, &dnorm, n * dim))) return bail(st);
-    if ((st = dalloc(ctx, &dint, inner.size()))) return bail(st);
+    if ((st = dalloc(ctx, &dx, ncap * dim))) return bail(st);
+    if ((st = dalloc(ctx, &dkind, ncap))) return bail(st);
+    if ((st = dalloc(ctx, &dnorm, ncap * dim))) return bail(st);
+    if ((st = dalloc(ctx, &dint, inner.size() + q.spare_points))) return bail(st);
     if ((st = dalloc(ctx, &dwall, wall.size()))) return bail(st);
     if (cudaMemcpy(dx, x + off * dim, sizeof(double) * n * dim, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dkind, kind + off, sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -538,21 +547,21 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.wall_idx = dwall;
 
     if ((st = dalloc(ctx, &v.vnodes, q.nv))) return bail(st);
-    if ((st = dalloc(ctx, &v.xf, n * dim))) return bail(st);
-    if ((st = dalloc(ctx, &v.xlo, n * dim))) return bail(st);
-    if ((st = dalloc(ctx, &v.cell_of, n))) return bail(st);
+    if ((st = dalloc(ctx, &v.xf, ncap * dim))) return bail(st);
+    if ((st = dalloc(ctx, &v.xlo, ncap * dim))) return bail(st);
+    if ((st = dalloc(ctx, &v.cell_of, ncap))) return bail(st);
     if ((st = dalloc(ctx, &v.cell_start, ncell + 1))) return bail(st);
     if ((st = dalloc(ctx, &v.cell_cnt, ncell))) return bail(st);
-    if ((st = dalloc(ctx, &v.cell_pts, n))) return bail(st);
-    if ((st = dalloc(ctx, &v.cnt, n))) return bail(st);
-    if ((st = dalloc(ctx, &v.col, n * v.cap))) return bail(st);
-    if ((st = dalloc_bytes(ctx, &v.P, (size_t)n * v.cap * dim * dim * c.c_bytes))) return bail(st);
-    if ((st = dalloc_bytes(ctx, &v.recon, (size_t)n * v.cap * c.c_bytes))) return bail(st);
+    if ((st = dalloc(ctx, &v.cell_pts, ncap))) return bail(st);
+    if ((st = dalloc(ctx, &v.cnt, ncap))) return bail(st);
+    if ((st = dalloc(ctx, &v.col, ncap * v.cap))) return bail(st);
+    if ((st = dalloc_bytes(ctx, &v.P, (size_t)ncap * v.cap * dim * dim * c.c_bytes))) return bail(st);
+    if ((st = dalloc_bytes(ctx, &v.recon, (size_t)ncap * v.cap * c.c_bytes))) return bail(st);
     if ((st = dalloc(ctx, &v.wcls, (size_t)v.n_wall * v.NVp))) return bail(st);
     if ((st = dalloc_bytes(ctx, &v.wvn, (size_t)v.n_wall * v.NVp * c.c_bytes))) return bail(st);
     if ((st = dalloc(ctx, &v.winv, v.n_wall))) return bail(st);
     if ((st = dalloc_bytes(ctx, &v.mw, (size_t)2 * v.NVp * c.c_bytes))) return bail(st);
-    const size_t fbytes = (size_t)n * v.ncomp * v.NVp * c.s_bytes;
+    const size_t fbytes = (size_t)ncap * v.ncomp * v.NVp * c.s_bytes;
     for (int b = 0; b < 2; ++b) {
       if ((st = dalloc_bytes(ctx, &c.f[b], fbytes))) return bail(st);
       if (cudaMemset(c.f[b], 0, fbytes) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset f"));
@@ -561,17 +570,17 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
       // candidate capacity: max_nbrs scaled by the volume ratio of the two radii, plus 10 %
       const double r = std::pow(1.0 + q.skin, dim) * 1.1;
       v.ccap = (int32_t)std::min<double>(std::ceil(v.cap * r), 4096.0);
-      if ((st = dalloc(ctx, &v.xb, n * dim))) return bail(st);
-      if ((st = dalloc(ctx, &v.ccnt, n))) return bail(st);
-      if ((st = dalloc(ctx, &v.ccol, (size_t)n * v.ccap))) return bail(st);
+      if ((st = dalloc(ctx, &v.xb, ncap * dim))) return bail(st);
+      if ((st = dalloc(ctx, &v.ccnt, ncap))) return bail(st);
+      if ((st = dalloc(ctx, &v.ccol, (size_t)ncap * v.ccap))) return bail(st);
       if ((st = dalloc(ctx, &v.sk, 1))) return bail(st);
       const SkinState s0 = {0u, 1, 0u, 0};
       if (cudaMemcpy(v.sk, &s0, sizeof(s0), cudaMemcpyHostToDevice) != cudaSuccess ||
           cudaMemset(v.cell_cnt, 0, sizeof(int32_t) * ncell) != cudaSuccess)
         return bail(fail(ctx, BGK_E_CUDA, "case %d: skin state upload failed", ci));
     }
-    if ((st = dalloc(ctx, &v.mom, (size_t)n * MOM_STRIDE))) return bail(st);
-    if (cudaMemset(v.mom, 0, sizeof(double) * n * MOM_STRIDE) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset mom"));
+    if ((st = dalloc(ctx, &v.mom, (size_t)ncap * MOM_STRIDE))) return bail(st);
+    if (cudaMemset(v.mom, 0, sizeof(double) * ncap * MOM_STRIDE) != cudaSuccess) return bail(fail(ctx, BGK_E_CUDA, "cudaMemset mom"));
     v.status = ctx->status;
     refresh_view(c);
     ctx->launches += launch_init_tables(v, 0);
@@ -893,7 +902,8 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   const char* why = nullptr;
   if (!check_params(*p, c.cv.n, &why)) return fail(ctx, BGK_E_INVAL, "bgk_set_params: %s", why);
   if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
-      p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin)
+      p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin ||
+      p->spare_points != o.spare_points)
     return fail(ctx, BGK_E_INVAL, "bgk_set_params: only kn, tau_mode, dt, wall_T, lid_u, lid_wall, ale, guard may change");
   CK(ctx, cudaDeviceSynchronize());
   c.p = *p;
@@ -920,6 +930,77 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   return BGK_OK;
 }
 
+int bgk_manage(bgk_ctx* ctx, int32_t ci, double rmin, int32_t min_nbrs, int64_t* counts, void* stream) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !counts || !(rmin >= 0) || min_nbrs < 0)
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_manage: bad argument") : BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CaseHost& c = ctx->cases[ci];
+  int st;
+  if ((st = join_side(ctx, c, s))) return st;
+  refresh_view(c);
+  const int dim = c.cv.dim;
+  const size_t cn = c.cap_n;
+  if (!c.pm_nn) {
+    if ((st = dalloc(ctx, &c.pm_nn, cn))) return st;
+    if ((st = dalloc(ctx, &c.pm_role, cn))) return st;
+    if ((st = dalloc(ctx, &c.pm_newidx, cn))) return st;
+    if ((st = dalloc(ctx, &c.pm_addidx, cn))) return st;
+    if ((st = dalloc(ctx, &c.pm_totals, 2))) return st;
+    if ((st = dalloc(ctx, &c.pm_kind2, cn))) return st;
+    if ((st = dalloc(ctx, &c.pm_int2, cn))) return st;
+    if ((st = dalloc(ctx, &c.pm_ynew, cn * dim))) return st;
+    if ((st = dalloc(ctx, &c.pm_x2, cn * dim))) return st;
+    if ((st = dalloc(ctx, &c.pm_norm2, cn * dim))) return st;
+  }
+  // exact lists of the current positions
+  CaseView v = c.cv;
+  ctx->launches += launch_neighbours(v, s);
+  // the skin path expects zero cell counts at the start of a rebuild
+  if (v.sk) CK(ctx, cudaMemsetAsync(v.cell_cnt, 0, sizeof(int32_t) * v.ncell, s));
+  ctx->launches += launch_manage_plan(v, rmin, min_nbrs, c.pm_nn, c.pm_role, c.pm_ynew, c.pm_newidx, c.pm_addidx,
+                                      c.pm_totals, s);
+  CKL(ctx);
+  int32_t tot[2];
+  CK(ctx, cudaMemcpyAsync(tot, c.pm_totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  const int64_t n_old = v.n, survivors = tot[0];
+  const int64_t adds = std::min<int64_t>(tot[1], c.cap_n - survivors);
+  const int64_t n_new = survivors + adds;
+  ctx->launches += launch_manage_apply(v, c.cap_n, c.pm_nn, c.pm_role, c.pm_ynew, c.pm_newidx, c.pm_addidx,
+                                       c.pm_totals, c.pm_x2, c.pm_kind2, c.pm_norm2, c.f[c.cur], c.f[1 - c.cur],
+                                       c.pm_int2, const_cast<int32_t*>(c.cv.wall_idx), c.wall_of, n_new, s);
+  CKL(ctx);
+  // the new arrays become current
+  {
+    double* t = c.cv.x; c.cv.x = c.pm_x2; c.pm_x2 = t;
+  }
+  {
+    int32_t* t = const_cast<int32_t*>(c.cv.kind); c.cv.kind = c.pm_kind2; c.pm_kind2 = t;
+  }
+  {
+    double* t = const_cast<double*>(c.cv.normal); c.cv.normal = c.pm_norm2; c.pm_norm2 = t;
+  }
+  {
+    int32_t* t = const_cast<int32_t*>(c.cv.int_idx); c.cv.int_idx = c.pm_int2; c.pm_int2 = t;
+  }
+  c.cur = 1 - c.cur;
+  c.cv.n_int = (int32_t)(c.cv.n_int - (n_old - survivors) + adds);
+  c.cv.n = (int32_t)n_new;
+  refresh_view(c);
+  ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
+  CKL(ctx);
+  CK(ctx, cudaStreamSynchronize(s));
+  c.stencils_valid = false;
+  c.next_ready = false;
+  c.tslot_valid = false;
+  if ((st = reset_skin(ctx, c))) return st;
+  invalidate_batch(ctx);
+  counts[0] = n_new;
+  counts[1] = n_old - survivors;
+  counts[2] = adds;
+  return BGK_OK;
+}
+
 int bgk_objective(bgk_ctx* ctx, int32_t ci, double* J, void* lam, double scale, void* stream) {
   if (!ctx || ci < 0 || ci >= (int)ctx->cases.size())
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_objective: bad argument") : BGK_E_INVAL;
@@ -939,15 +1020,15 @@ int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out
   int st;
   refresh_view(c);
   if (!c.stencils_valid && (st = build_lists(ctx, c, s))) return st;
-  const size_t fl = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.c_bytes;
+  const size_t fl = (size_t)c.cap_n * c.cv.ncomp * c.cv.NVp * c.c_bytes;
   if (!c.adj_ft) {
     if ((st = dalloc_bytes(ctx, &c.adj_ft, fl))) return st;
     if ((st = dalloc_bytes(ctx, &c.adj_y, fl))) return st;
     if ((st = dalloc_bytes(ctx, &c.adj_lft, fl))) return st;
     if ((st = dalloc(ctx, &c.adj_wmu, std::max<int64_t>(c.cv.n_wall, 1)))) return st;
-    if ((st = dalloc(ctx, &c.adj_mom, (size_t)c.cv.n * MOM_STRIDE))) return st;
-    if ((st = dalloc(ctx, &c.adj_sk, (size_t)c.cv.n * c.cv.NVp))) return st;
-    if ((st = dalloc(ctx, &c.tslot, (size_t)c.cv.n * c.cv.cap))) return st;
+    if ((st = dalloc(ctx, &c.adj_mom, (size_t)c.cap_n * MOM_STRIDE))) return st;
+    if ((st = dalloc(ctx, &c.adj_sk, (size_t)c.cap_n * c.cv.NVp))) return st;
+    if ((st = dalloc(ctx, &c.tslot, (size_t)c.cap_n * c.cv.cap))) return st;
     CK(ctx, cudaMemset(c.adj_lft, 0, fl));
   }
   if (!c.tslot_valid) {

@@ -87,6 +87,15 @@ struct CaseView {
 // Launchers (stream-ordered; each returns the number of kernels launched).
 int launch_init_tables(const CaseView& cv, cudaStream_t s);
 int launch_neighbours(const CaseView& cv, cudaStream_t s);
+// Point management (between steps): plan (nearest pairs, roles, new indices; totals[0] =
+// survivors, totals[1] = additions requested) and apply (new positions, rows of f,
+// index lists) for n_new = survivors + min(additions, cap_n - survivors) points.
+int launch_manage_plan(const CaseView& cv, double rmin, int min_nbrs, int32_t* nn, int32_t* role, double* ynew,
+                       int32_t* newidx, int32_t* addidx, int32_t* totals, cudaStream_t s);
+int launch_manage_apply(const CaseView& cv, int64_t cap_n, const int32_t* nn, const int32_t* role,
+                        const double* ynew, const int32_t* newidx, const int32_t* addidx, const int32_t* totals,
+                        double* x2, int32_t* kind2, double* norm2, const void* f, void* f2, int32_t* int2,
+                        int32_t* wall_idx, int32_t* wall_of, int64_t n_new, cudaStream_t s);
 // ALE with a skin: rebuild the candidate lists if a point moved too far, then filter them.
 int launch_neighbours_skin(const CaseView& cv, cudaStream_t s);
 // part 0: all points; 1: interior stencils (all points for FP64 storage); 2: wall
