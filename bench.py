@@ -205,6 +205,36 @@ def adjoint_cost(g, torch, stream) -> dict:
             "ms_adjoint_step": adj, "ratio": adj / fwd}
 
 
+def manage_cost(g, torch, stream, p: dict, name: str, steps: int = 200) -> dict:
+    """One point-management pass (merge pairs closer than 0.25 dx, fill holes next to
+    points with fewer than 14 neighbours) on the bench workload after `steps` ALE steps,
+    wall-clock (the call is synchronous), against the mean step time."""
+    cl = bi.cloud_for(p)
+    n = len(cl["kind"])
+    q = dict(p, spare_points=n // 16)
+    s = g.Solver([q], [cl])
+    s.set_maxwellian(stream=stream)
+    s.step(steps, stream=stream)
+    s.sync(stream)
+    dx = 1.0 / (p["n"] - 1)
+    s.manage(0.25 * dx, 14, stream=stream)  # allocates the scratch, removes what accumulated
+    s.step(10, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    npts, removed, added = s.manage(0.25 * dx, 14, stream=stream)
+    ms = (time.perf_counter() - t0) * 1e3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(20, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 20
+    s.sync(stream)
+    s.close()
+    return {"workload": name, "after_steps": steps + 10, "ms_per_pass": ms,
+            "ms_per_step": step_ms, "points": npts, "removed": removed, "added": added}
+
+
 def batched_cost(g, torch, stream, steps: int = 20) -> dict:
     """64 independent 2D cavities (sides 41..121, 16..32 velocity nodes, FP32): batched + graph vs per case."""
     ps = bi.batched_cases(64)
@@ -275,6 +305,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override points per axis (profiling runs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-step cost measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-cavity batched measurement")
+    ap.add_argument("--no-manage", action="store_true", help="skip the point-management measurement")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
     p = rank_config(bi.config(args.workload, **({"n": args.n} if args.n else {})), rank, world)
@@ -310,8 +341,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-resident timed region ----
-    g.bgk_set_timing(s.ctx, True)
+    # ---- device-resident timed region (event pairs around the transport launches only) ----
+    g.bgk_set_timing(s.ctx, 1 << g.K_TRANSPORT)
     launches0 = s.stats()["launches"]
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -326,11 +357,16 @@ def main():
     s.sync(stream)
     launches = s.stats()["launches"] - launches0
     kt_ms, kt_n = g.bgk_get_timing(s.ctx, g.K_TRANSPORT)
+    g.bgk_set_timing(s.ctx, False)
+    ms = reduce_max(ms, dist, "cuda")
+    # per-kernel breakdown from a short separate run with every group timed
+    g.bgk_set_timing(s.ctx, True)
+    s.step(min(args.steps, 50), stream=stream)
+    s.sync(stream)
     per_kernel = {name: g.bgk_get_timing(s.ctx, k) for name, k in
                   (("transport", g.K_TRANSPORT), ("walls", g.K_WALLS), ("neighbours", g.K_NBR),
                    ("stencils", g.K_STENCIL), ("move", g.K_MOVE))}
     g.bgk_set_timing(s.ctx, False)
-    ms = reduce_max(ms, dist, "cuda")
     value = upd_per_step * args.steps * world / (ms * 1e-3)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -376,6 +412,9 @@ def main():
 
     # ---- discrete adjoint cost on the adjoint workload (101^2 x 24^2, FP32, fixed points) ----
     adj = None
+    manage = None
+    if not args.no_manage and world == 1 and p.get("ale"):
+        manage = manage_cost(g, torch, stream, p, args.workload)
     if not args.no_adjoint and world == 1:
         adj = adjoint_cost(g, torch, stream)
 
@@ -416,7 +455,8 @@ def main():
                 "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": args.e2e_steps},
-                "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj, "batched": batched}
+                "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj, "batched": batched,
+                "manage": manage}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, 1)
         print(json.dumps(line), flush=True)

@@ -235,12 +235,13 @@ int bgk_set_batching(bgk_ctx* ctx, int32_t mode);
  * keep the fastest (see bgk_stats).  The state is not changed.  Synchronous. */
 int bgk_autotune(bgk_ctx* ctx, void* stream);
 
-/* Per-kernel timing with CUDA events on the launching stream: enable = 1
- * brackets every launch of the transport kernel with an event pair.
- * bgk_get_timing synchronises and returns the summed device time (ms) and
- * launch count of kernel `which` (0 = transport+relaxation, 1 = wall, 2 =
- * neighbour build, 3 = stencils, 4 = motion, 5 = adjoint step, 6 = one batched step of all cases) since
- * timing was enabled. */
+/* Per-kernel timing with CUDA events on the launching stream: bit k of enable
+ * brackets every launch of kernel group k with an event pair (0 = transport+
+ * relaxation, 1 = wall, 2 = neighbour build, 3 = stencils, 4 = motion, 5 = adjoint
+ * step, 6 = one batched step of all cases; 0x7f times all, 0 none).  Each pair
+ * costs the stream a little, so time only what is needed.  bgk_get_timing
+ * synchronises and returns the summed device time (ms) and launch count of
+ * group `which` since timing was enabled. */
 int bgk_set_timing(bgk_ctx* ctx, int32_t enable);
 int bgk_get_timing(bgk_ctx* ctx, int32_t which, double* total_ms, int64_t* launches);
 

@@ -220,8 +220,10 @@ def bgk_set_state(ctx, blob: bytes) -> None:
     _check(lib().bgk_set_state(ctx, C.cast(buf, _P), len(blob)), ctx)
 
 
-def bgk_set_timing(ctx, enable: bool) -> None:
-    _check(lib().bgk_set_timing(ctx, int(enable)), ctx)
+def bgk_set_timing(ctx, enable) -> None:
+    """enable: True times every kernel group, False none, an int is the bit mask of group ids."""
+    mask = (0x7F if enable else 0) if isinstance(enable, bool) else int(enable)
+    _check(lib().bgk_set_timing(ctx, mask), ctx)
 
 
 def bgk_get_timing(ctx, which: int):

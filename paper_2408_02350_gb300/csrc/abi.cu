@@ -92,6 +92,7 @@ struct bgk_ctx {
   std::string err;
   int64_t steps = 0, launches = 0;
   bool timing = false;
+  int32_t timing_mask = 0;  // bit k: time kernel id k
   std::vector<EvPair> ev;
   size_t ev_used = 0;
   double t_ms[K_COUNT] = {0, 0, 0, 0, 0, 0, 0};
@@ -187,7 +188,7 @@ void refresh_view(CaseHost& c) {
 
 int timed_begin(bgk_ctx* ctx, int kid, cudaStream_t s, EvPair** out) {
   *out = nullptr;
-  if (!ctx->timing) return BGK_OK;
+  if (!((ctx->timing_mask >> kid) & 1)) return BGK_OK;
   if (ctx->ev_used == ctx->ev.size()) {
     EvPair e;
     CK(ctx, cudaEventCreate(&e.a));
@@ -1101,6 +1102,7 @@ int bgk_set_timing(bgk_ctx* ctx, int32_t enable) {
   if (!ctx) return BGK_E_INVAL;
   int st = collect_timing(ctx);
   if (st) return st;
+  ctx->timing_mask = enable;
   ctx->timing = enable != 0;
   // pre-create event pairs so that timed regions do not pay for cudaEventCreate
   while (ctx->timing && ctx->ev.size() < 8192) {
