@@ -185,68 +185,82 @@ __global__ void __launch_bounds__(256) k_adj_prep(CaseView cv, C* FT, C* Y) {
   }
 }
 
-// per wall point: wmu[w] = (dJ/drho_w) / N, and the lid-velocity derivative (lid points)
+// per wall point: wmu[w] = (dJ/drho_w) / N, and the lid-velocity derivative (lid points).
+// The interior neighbours and their weights are staged in shared memory; per-thread
+// partial sums are in the compute type C (FP32 on the FP32 path: FP64 runs at 1/64 of
+// the FP32 rate on this GPU), the block reduction in FP64.
 template <typename C, int DIM>
 __global__ void __launch_bounds__(256) k_adj_walls(CaseView cv, const C* Y, const C* lam1, double* wmu, double* dtheta) {
   constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int NA = 2 + 2 * DIM;
   __shared__ double s_red[RED];
-  __shared__ double s_nodes[64];
-  __shared__ double s_F;
+  __shared__ C s_nodes[64];
+  __shared__ int32_t s_j[512];
+  __shared__ C s_r[512];
+  __shared__ int s_mi;
   const int w = blockIdx.x;
   const int b = cv.wall_idx[w];
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const int64_t rowlen = (int64_t)NC * NVp;
-  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = cv.vnodes[t];
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = (C)cv.vnodes[t];
+  const C* R = reinterpret_cast<const C*>(cv.recon) + (int64_t)b * cap;
+  const int32_t* row = cv.col + (int64_t)b * cap;
+  if (threadIdx.x == 0) {
+    int mi = 0;
+    for (int s = 0; s < cv.cnt[b]; ++s)
+      if (cv.kind[row[s]] == 0) { s_j[mi] = row[s]; s_r[mi] = R[s]; ++mi; }
+    s_mi = mi;
+  }
   __syncthreads();
+  const int mi = s_mi;
   const int8_t* cls = cv.wcls + (int64_t)w * NVp;
   const C* vn = reinterpret_cast<const C*>(cv.wvn) + (int64_t)w * NVp;
   const bool lid = cv.kind[b] == cv.lid_wall;
   const C* Mw = reinterpret_cast<const C*>(cv.mw) + (lid ? NVp : 0);
-  const C* R = reinterpret_cast<const C*>(cv.recon) + (int64_t)b * cap;
-  const int32_t* row = cv.col + (int64_t)b * cap;
-  const int m = cv.cnt[b];
-  const double invN = cv.winv[w], Tw = cv.wall_T;
-  double uw[3] = {0, 0, 0};
+  const double invN = cv.winv[w];
+  const C Tw = (C)cv.wall_T, invTw = (C)(1.0 / cv.wall_T);
+  C uw[3] = {(C)0, (C)0, (C)0};
   if (lid)
-    for (int a = 0; a < DIM; ++a) uw[a] = cv.lid_u[a];
+    for (int a = 0; a < DIM; ++a) uw[a] = (C)cv.lid_u[a];
+  C acc[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) acc[q] = (C)0;
   // F = sum over arriving velocities of |v.n| g_b, g_b = sum_j r_bj y_j
-  double acc[1 + 2 * DIM + 1];
-  for (int q = 0; q < 2 + 2 * DIM; ++q) acc[q] = 0.0;
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
     if (cls[k] != 0) continue;
-    double g = 0.0;
-    for (int s = 0; s < m; ++s) {
-      const int j = row[s];
-      if (cv.kind[j] != 0) continue;
-      g += (double)R[s] * (double)Y[(int64_t)j * rowlen + k];
-    }
-    acc[0] += (double)vn[k] * g;
+    C g = (C)0;
+    for (int s = 0; s < mi; ++s) g += s_r[s] * Y[(int64_t)s_j[s] * rowlen + k];
+    acc[0] += vn[k] * g;
   }
   // mu = sum_{leaving} sum_c lam_c Mw_c ; du_a and dN_a for the lid
   const C* lb = lam1 + (int64_t)b * rowlen;
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
     if (cls[k] == 0) continue;
-    double vd[DIM];
-    vel_of<DIM>(k, nv, s_nodes, vd);
-    const double m0 = (double)Mw[k];
-    double lm = (double)lb[k] * m0;
-    if (NC == 2) lm += (double)lb[NVp + k] * Tw * m0;
+    C vd[DIM];
+    int kk = k;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { vd[a] = s_nodes[kk % nv]; kk /= nv; }
+    const C m0 = Mw[k];
+    C lm = lb[k] * m0;
+    if (NC == 2) lm += lb[NVp + k] * Tw * m0;
     acc[1] += lm;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      const double ca = (vd[a] - uw[a]) / Tw;
-      acc[2 + a] += lm * ca;                         // sum lam_c Mw_c (v_a - u_a)/T
-      acc[2 + DIM + a] += (double)vn[k] * m0 * ca;   // dN/du_a
+      const C ca = (vd[a] - uw[a]) * invTw;
+      acc[2 + a] += lm * ca;               // sum lam_c Mw_c (v_a - u_a)/T
+      acc[2 + DIM + a] += vn[k] * m0 * ca;  // dN/du_a
     }
   }
-  block_reduce<2 + 2 * DIM>(acc, s_red);
+  double accd[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) accd[q] = (double)acc[q];
+  block_reduce<NA>(accd, s_red);
   if (threadIdx.x == 0) {
-    const double F = acc[0], mu = acc[1], rho_w = F * invN;
+    const double F = accd[0], mu = accd[1], rho_w = F * invN;
     wmu[w] = mu * invN;
     if (lid)
-      for (int a = 0; a < DIM; ++a) atomicAdd(&dtheta[a], rho_w * acc[2 + a] - mu * rho_w * invN * acc[2 + DIM + a]);
+      for (int a = 0; a < DIM; ++a) atomicAdd(&dtheta[a], rho_w * accd[2 + a] - mu * rho_w * invN * accd[2 + DIM + a]);
   }
-  (void)s_F;
 }
 
 // per interior point: lam_f~ = VJP of the relaxation applied to lam_y
