@@ -205,11 +205,23 @@ __global__ void __launch_bounds__(256) k_adj_walls(CaseView cv, const C* Y, cons
   for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = (C)cv.vnodes[t];
   const C* R = reinterpret_cast<const C*>(cv.recon) + (int64_t)b * cap;
   const int32_t* row = cv.col + (int64_t)b * cap;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0 stages the interior neighbours in list order (ballot compaction)
+    const int lane = threadIdx.x, m = cv.cnt[b];
     int mi = 0;
-    for (int s = 0; s < cv.cnt[b]; ++s)
-      if (cv.kind[row[s]] == 0) { s_j[mi] = row[s]; s_r[mi] = R[s]; ++mi; }
-    s_mi = mi;
+    for (int s0 = 0; s0 < m; s0 += 32) {
+      const int s = s0 + lane;
+      const int j = s < m ? row[s] : 0;
+      const bool in = s < m && cv.kind[j] == 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int pos = mi + __popc(bal & ((1u << lane) - 1u));
+        s_j[pos] = j;
+        s_r[pos] = R[s];
+      }
+      mi += __popc(bal);
+    }
+    if (lane == 0) s_mi = mi;
   }
   __syncthreads();
   const int mi = s_mi;

@@ -429,14 +429,25 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   C* s_r = reinterpret_cast<C*>(smem + RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)));
   const int b = cv.wall_idx[w];
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
-  if (threadIdx.x == 0) {
-    const int m = cv.cnt[b];
+  if (threadIdx.x < 32) {
+    // warp 0 stages the interior neighbours in list order (ballot compaction)
+    const int lane = threadIdx.x, m = cv.cnt[b];
     const int32_t* col = cv.col + (int64_t)b * cv.cap;
     const C* R = reinterpret_cast<const C*>(cv.recon) + (int64_t)b * cv.cap;
     int mi = 0;
-    for (int s = 0; s < m; ++s)
-      if (cv.kind[col[s]] == 0) { s_j[1 + mi] = col[s]; s_r[mi] = R[s]; ++mi; }
-    s_j[0] = mi;
+    for (int s0 = 0; s0 < m; s0 += 32) {
+      const int s = s0 + lane;
+      const int j = s < m ? col[s] : 0;
+      const bool in = s < m && cv.kind[j] == 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int pos = mi + __popc(bal & ((1u << lane) - 1u));
+        s_j[1 + pos] = j;
+        s_r[pos] = R[s];
+      }
+      mi += __popc(bal);
+    }
+    if (lane == 0) s_j[0] = mi;
   }
   for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (C)cv.vnodes[t];
   __syncthreads();
