@@ -235,6 +235,36 @@ def manage_cost(g, torch, stream, p: dict, name: str, steps: int = 200) -> dict:
             "ms_per_step": step_ms, "points": npts, "removed": removed, "added": added}
 
 
+def _rate(g, torch, stream, p: dict, steps: int) -> dict:
+    """Device-resident updates/s of `steps` steps of workload p (after 3 warm-up steps)."""
+    cl = bi.cloud_for(p)
+    s = g.Solver([p], [cl])
+    s.set_maxwellian(stream=stream)
+    s.step(3, stream=stream)
+    s.sync(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.sync(stream)
+    s.close()
+    upd = len(cl["kind"]) * p["nv"] ** p["dim"]
+    return {"value": upd / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps}
+
+
+def extra_configs(g, torch, stream, workload: str) -> dict:
+    """The ALE workload over its Kn sweep, and the plain FP64 41^2 x 16^2 cavity."""
+    out = {}
+    p = bi.config(workload)
+    if p.get("ale"):
+        out["kn_sweep"] = {str(kn): _rate(g, torch, stream, bi.config(workload, kn=kn), 200)
+                           for kn in bi.KN_SWEEP_ALE}
+    out["cavity2d_n41_v16_f64"] = _rate(g, torch, stream, bi.config("cavity2d_n41_v16_f64"), 100)
+    return out
+
+
 def batched_cost(g, torch, stream, steps: int = 20) -> dict:
     """64 independent 2D cavities (sides 41..121, 16..32 velocity nodes, FP32): batched + graph vs per case."""
     ps = bi.batched_cases(64)
@@ -306,6 +336,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-step cost measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-cavity batched measurement")
     ap.add_argument("--no-manage", action="store_true", help="skip the point-management measurement")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Kn sweep and the FP64 41^2 cavity")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
     p = rank_config(bi.config(args.workload, **({"n": args.n} if args.n else {})), rank, world)
@@ -421,6 +452,9 @@ def main():
     batched = None
     if not args.no_batched and world == 1:
         batched = batched_cost(g, torch, stream)
+    extra = None
+    if not args.no_extra and world == 1:
+        extra = extra_configs(g, torch, stream, args.workload)
 
     # ---- roofline of the dominant kernel (transport + moments + relaxation) ----
     peaks = _peaks()
@@ -456,7 +490,7 @@ def main():
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": args.e2e_steps},
                 "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj, "batched": batched,
-                "manage": manage}
+                "manage": manage, "extra": extra}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, 1)
         print(json.dumps(line), flush=True)
