@@ -23,6 +23,8 @@ Wall kinds (the cavity walls of Sec. 5.1 and 5.2):
   5, 6       faces z = 0 and z = 1 (3D only)
   2*dim + 1  edge or corner point: a wall at rest whose inward normal is the
              normalised sum of the adjacent face normals
+  2*dim + 2  boundary point of a rigid body (a disc in 2D, a ball in 3D) that
+             moves through the gas with a constant velocity (Sec. 3.4.1)
 The lid is face y = 1 in 2D (kind 4) and face z = 1 in 3D (kind 6).  Only
 points strictly inside the lid face move with the lid velocity.
 """
@@ -106,6 +108,39 @@ def periodic_box(dim: int, n: int, seed: int | None = None, jitter: float = 0.0)
             "normal": np.zeros((npts, dim)), "dx": dx, "n": n, "lid_wall": 0, "dim": dim}
 
 
+def with_body(cl: dict, centre, radius: float, wall: int) -> dict:
+    """The cloud ``cl`` with a rigid body of the given centre and radius.
+
+    Interior points closer than radius + dx/2 to the centre are removed.  The body's
+    boundary points (kind ``wall``) follow the cloud's points, spaced about dx on the
+    circle (2D: equal angles) or sphere (3D: a Fibonacci spiral, equal areas); their
+    inward normal (into the gas) points away from the centre.
+    """
+    dim, dx = cl["dim"], cl["dx"]
+    c = np.asarray(centre, dtype=np.float64)[:dim]
+    x = cl["x"]
+    r = np.sqrt(((x - c) ** 2).sum(axis=1))
+    keep = ~((cl["kind"] == 0) & (r < radius + 0.5 * dx))
+    if dim == 2:
+        m = max(8, int(round(2.0 * math.pi * radius / dx)))
+        th = 2.0 * math.pi * np.arange(m) / m
+        nb = np.stack([np.cos(th), np.sin(th)], axis=1)
+    else:
+        m = max(12, int(round(4.0 * math.pi * radius * radius / (dx * dx))))
+        k = np.arange(m, dtype=np.float64)
+        z = 1.0 - (2.0 * k + 1.0) / m
+        rho = np.sqrt(1.0 - z * z)
+        phi = k * (math.pi * (3.0 - math.sqrt(5.0)))
+        nb = np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+    xb = c[None, :] + radius * nb
+    out = dict(cl)
+    out["x"] = np.concatenate([x[keep], xb])
+    out["kind"] = np.concatenate([cl["kind"][keep], np.full(m, wall, dtype=np.int32)])
+    out["normal"] = np.concatenate([cl["normal"][keep], nb])
+    out["body_wall"] = wall
+    return out
+
+
 def cfl_dt(dx: float, vmax: float, dim: int, cfl: float = 0.5) -> float:
     """Time step cfl * dx / max|v|, with max|v| = vmax*sqrt(dim) at the grid corner."""
     return cfl * dx / (vmax * math.sqrt(dim))
@@ -136,6 +171,19 @@ CONFIGS = {
     # 2D cavity for the adjoint: 101^2 points, 24^2 velocities in [-5,5]^2.
     "adjoint2d_n101_v24_f32": _params(2, 101, 24, 5.0, 0.1, 0.1, 1000, "f32", False, 2408005),
 }
+
+def _body(p: dict, centre, radius: float, u) -> dict:
+    q = dict(p)
+    q["body_wall"] = 2 * p["dim"] + 2
+    q["body_centre"] = list(centre) + [0.0] * (3 - len(centre))
+    q["body_radius"] = radius
+    q["body_u"] = list(u) + [0.0] * (3 - len(u))
+    return q
+
+
+# The ALE cavity with a disc of radius 0.1 starting at (0.4, 0.5) and moving with (0.1, 0).
+CONFIGS["body2d_ale_n201_v32_f32"] = _body(
+    _params(2, 201, 32, 6.0, 0.1, 0.1, 2000, "f32", True, 2408006), (0.4, 0.5), 0.1, (0.1, 0.0))
 KN_SWEEP_ALE = (0.01, 0.1, 1.0)
 
 
@@ -143,6 +191,9 @@ def config(name: str, **overrides) -> dict:
     """A copy of workload ``name`` with keyword overrides applied."""
     p = dict(CONFIGS[name])
     p["lid_u"] = list(p["lid_u"])
+    for k in ("body_u", "body_centre"):
+        if k in p:
+            p[k] = list(p[k])
     for k, v in overrides.items():
         p[k] = v
     if "n" in overrides and ("h" not in overrides):
@@ -178,7 +229,11 @@ def batched_cases(count: int = 64, seed0: int = 2408400) -> list[dict]:
 
 
 def cloud_for(p: dict) -> dict:
-    """The point cloud of a workload dict (cavity, or periodic box when p['periodic'])."""
+    """The point cloud of a workload dict (cavity, with a body when p['body_wall'], or
+    periodic box when p['periodic'])."""
     if p.get("periodic"):
         return periodic_box(p["dim"], p["n"])
-    return cavity(p["dim"], p["n"], p["seed"])
+    cl = cavity(p["dim"], p["n"], p["seed"])
+    if p.get("body_wall"):
+        cl = with_body(cl, p["body_centre"], p["body_radius"], p["body_wall"])
+    return cl

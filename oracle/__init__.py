@@ -55,6 +55,8 @@ class Params(C.Structure):
         ("lid_wall", C.c_int32), ("max_nbrs", C.c_int32), ("pad_", C.c_int32),
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
         ("guard", C.c_double), ("lid_u", C.c_double * 3),
+        ("body_wall", C.c_int32), ("pad2_", C.c_int32), ("body_u", C.c_double * 3),
+        ("body_c", C.c_double * 3), ("body_r", C.c_double),
     ]
 
 
@@ -69,6 +71,13 @@ def params(p: dict) -> Params:
     lu = list(p.get("lid_u", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
     for a in range(3):
         q.lid_u[a] = float(lu[a])
+    q.body_wall = int(p.get("body_wall", 0))
+    bu = list(p.get("body_u", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
+    bc = list(p.get("body_centre", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
+    for a in range(3):
+        q.body_u[a] = float(bu[a])
+        q.body_c[a] = float(bc[a])
+    q.body_r = float(p.get("body_radius", 0.0))
     return q
 
 
@@ -287,8 +296,13 @@ def boundary(p: dict, kind, normal, cnt, col, st: dict, f, rho, U, T) -> int:
 
 
 def move(p: dict, kind, U, x) -> int:
+    """x += dt U in place (Eqs. originalALE1, ALE1) with the wall and body guards; with a
+    body, its points move with it and p['body_centre'] advances.  Returns the clamps."""
     q = params(p)
-    return lib().or_move(C.byref(q), x.shape[0], _i(_i32(kind)), _d(_f64(U)), _d(x))
+    c = lib().or_move(C.byref(q), x.shape[0], _i(_i32(kind)), _d(_f64(U)), _d(x))
+    if q.body_wall > 0:
+        p["body_centre"] = [float(q.body_c[a]) for a in range(3)]
+    return c
 
 
 def manage(p: dict, x, kind, normal, f, cnt, col, rmin: float, min_nbrs: int, cap_out: int | None = None):
@@ -389,3 +403,10 @@ class Simulation:
             raise RuntimeError("oracle or_run failed with status %d" % st)
         self.clamps += int(cl[0])
         self.steps += nsteps
+        if self.q.body_wall > 0:
+            self.p["body_centre"] = self.body_c.tolist() + [0.0] * (3 - self.dim)
+
+    @property
+    def body_c(self) -> np.ndarray:
+        """Current centre of the moving body."""
+        return np.array([self.q.body_c[a] for a in range(self.dim)])

@@ -29,10 +29,13 @@
  *     tau = sqrt(2/pi) Kn / (rho sqrt(T)) (Eqs. tau, lambda).
  *   - Velocity nodes v_j = -vmax + j dv, j = 0..nv-1, dv = 2 vmax/(nv-1),
  *     quadrature weight dv per axis (Sec. 3.3); nv counts the nodes (N_v + 1).
- *   - Walls: diffuse reflection.  Velocities with v.n <= 0 (n inward) are
- *     reconstructed from interior neighbours by a linear WLS fit (a constant
- *     fit where fewer than dim+1 interior neighbours exist); velocities
- *     with v.n > 0 get rho_w M(v; 1, u_w, T_w), rho_w from zero net mass flux.
+ *   - Walls: diffuse reflection.  Velocities with (v - u_w).n <= 0 (n inward,
+ *     u_w the wall velocity) are reconstructed from interior neighbours by a
+ *     linear WLS fit (a constant fit where fewer than dim+1 interior neighbours
+ *     exist); velocities with (v - u_w).n > 0 get rho_w M(v; 1, u_w, T_w), rho_w
+ *     from zero net mass flux through the wall.
+ *   - A rigid body's boundary points move with the body (Sec. 3.4.1); interior
+ *     points are kept outside a guard sphere around its centre.
  *   - Sub-step order: neighbours and stencils, transport, moments, relaxation,
  *     boundary, point motion.  The transport uses U^n, the moments of the
  *     previous transported state (moments of f^0 at the first step).
@@ -55,6 +58,16 @@ typedef struct {
   int32_t pad_;
   double dt, h, alpha, wall_T, guard;
   double lid_u[3];
+  /* Rigid body moving through the gas (Sec. 3.4.1: boundary points move with the
+   * boundary).  body_wall > 0 is the wall id of its boundary points; they move with
+   * the constant velocity body_u, which is also their wall velocity.  body_c is the
+   * current centre of the body (advanced with the points by or_move and or_run);
+   * interior points are kept at distance >= body_r + guard from it. */
+  int32_t body_wall;
+  int32_t pad2_;
+  double body_u[3];
+  double body_c[3];
+  double body_r;
 } or_params;
 
 enum { OR_OK = 0, OR_E_OVERFLOW = 1, OR_E_SINGULAR = 2, OR_E_INVAL = 3, OR_E_NOMEM = 4 };
@@ -498,7 +511,8 @@ static void recon_at(const or_params* p, const double* y, const double* x, const
  *  - add: an interior point i that takes part in no merge and has fewer than
  *    min_nbrs neighbours gets a new interior point at x_i - (h/2) c/|c|, c the
  *    sum of the separations to its neighbours (away from them, into the hole),
- *    if that position lies in [guard, 1 - guard]^dim (wrapped in a periodic box)
+ *    if that position lies in [guard, 1 - guard]^dim (wrapped in a periodic box),
+ *    outside the body's guard sphere (distance >= body_r + guard from body_c)
  *    and no point of N(i) + {i} is closer than rmin to it;
  *  - f at a new position y is the linear WLS reconstruction at y from
  *    N(i) + {i} (all point kinds), the least-squares update of the paper.
@@ -565,6 +579,10 @@ int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t*
       y[a] = ya;
     }
     if (!ok) continue;
+    if (p->body_wall > 0) {
+      const double rg = p->body_r + p->guard;
+      if (dist2(dim, y, p->body_c, 0) < rg * rg) continue;
+    }
     if (dist2(dim, y, xi, p->periodic) < rmin2) continue;
     for (int s = 0; s < cnt[i] && ok; ++s)
       if (dist2(dim, y, x + (int64_t)col[i * cap + s] * dim, p->periodic) < rmin2) ok = 0;
@@ -737,11 +755,13 @@ void or_transport_relax_points(const or_params* p, int64_t nidx, const int64_t* 
 
 /* ---- diffuse-reflection walls (Sec. 5.1, 5.2; Table 3) ---- */
 
-/* At every wall point: v.n <= 0 reconstructed, f_b = sum_j recon_j f_j;
- * v.n > 0: rho_w M(v; 1, u_w, T_w) with
- * rho_w = sum_{v.n<=0} |v.n| g_b / sum_{v.n>0} (v.n) M(v; 1, u_w, T_w)   (g = first component).
- * u_w is the lid velocity on kind == lid_wall, zero elsewhere.  Then the wall
- * point's moments are taken from f_b.  Returns OR_OK or OR_E_SINGULAR (no flux). */
+/* At every wall point, with c_n = (v - u_w).n the normal velocity relative to the
+ * wall: c_n <= 0 reconstructed, f_b = sum_j recon_j f_j; c_n > 0: rho_w M(v; 1, u_w, T_w)
+ * with rho_w = sum_{c_n<=0} |c_n| g_b / sum_{c_n>0} c_n M(v; 1, u_w, T_w)  (g = first
+ * component), so that no mass crosses the (moving) wall.  u_w is the lid velocity on
+ * kind == lid_wall, the body velocity on kind == body_wall, zero elsewhere (the lid
+ * moves tangentially, so there c_n = v.n).  Then the wall point's moments are taken
+ * from f_b.  Returns OR_OK or OR_E_SINGULAR (no flux). */
 int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double* normal,
                 const int32_t* cnt, const int32_t* col, const double* recon, double* f,
                 double* rho, double* U, double* T) {
@@ -758,11 +778,13 @@ int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double
     double uw[3] = {0.0, 0.0, 0.0};
     if (kind[b] == p->lid_wall)
       for (int a = 0; a < dim; ++a) uw[a] = p->lid_u[a];
+    if (p->body_wall > 0 && kind[b] == p->body_wall)
+      for (int a = 0; a < dim; ++a) uw[a] = p->body_u[a];
     or_maxwellian(p, 1.0, uw, p->wall_T, Mw);
     double out_flux = 0.0, in_norm = 0.0;
     for (int64_t k = 0; k < NV; ++k) {
       double vn = 0.0;
-      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      for (int a = 0; a < dim; ++a) vn += (vel[k * dim + a] - uw[a]) * nb[a];
       if (vn <= 0.0) {
         for (int q = 0; q < nc; ++q) {
           double acc = 0.0;
@@ -782,7 +804,7 @@ int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double
     double rho_w = out_flux / in_norm;
     for (int64_t k = 0; k < NV; ++k) {
       double vn = 0.0;
-      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      for (int a = 0; a < dim; ++a) vn += (vel[k * dim + a] - uw[a]) * nb[a];
       if (vn > 0.0)
         for (int q = 0; q < nc; ++q) fb[q * NV + k] = rho_w * Mw[q * NV + k];
     }
@@ -795,23 +817,57 @@ int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double
 
 /* ---- point motion (Eq. originalALE1, ALE1): x^{n+1} = x^n + dt U^{n+1} ---- */
 
-/* Interior points only.  Cavity: each coordinate is clamped to [guard, 1 - guard];
- * periodic box: wrapped into [0, 1).  Returns the number of clamped coordinates. */
-int64_t or_move(const or_params* p, int64_t n, const int32_t* kind, const double* U, double* x) {
+/* Interior points: x += dt U.  Cavity: each coordinate is clamped to [guard, 1 - guard];
+ * periodic box: wrapped into [0, 1).  With a body, its centre advances first,
+ * c' = c + dt body_u, its boundary points move with it (x += dt body_u), and an
+ * interior point that ends closer than rg = body_r + guard to c' is put back on that
+ * sphere along the ray from c' (at c' + rg e_x if it sits on c' itself).  Returns the
+ * number of clamps (one per clamped coordinate, one per point put back); p->body_c
+ * becomes c'. */
+int64_t or_move(or_params* p, int64_t n, const int32_t* kind, const double* U, double* x) {
   int dim = p->dim;
   int64_t clamps = 0;
+  const int body = p->body_wall > 0;
+  double cn[3] = {0.0, 0.0, 0.0};
+  const double rg = p->body_r + p->guard, rg2 = rg * rg;
+  if (body)
+    for (int a = 0; a < dim; ++a) cn[a] = p->body_c[a] + p->dt * p->body_u[a];
   for (int64_t i = 0; i < n; ++i) {
-    if (kind[i] != 0) continue;
-    for (int a = 0; a < dim; ++a) {
-      double y = x[i * dim + a] + p->dt * U[i * dim + a];
-      if (p->periodic) {
-        if (y >= 1.0) y -= 1.0;
-        else if (y < 0.0) y += 1.0;
-      } else if (y < p->guard) { y = p->guard; ++clamps; }
-      else if (y > 1.0 - p->guard) { y = 1.0 - p->guard; ++clamps; }
-      x[i * dim + a] = y;
+    if (body && kind[i] == p->body_wall) {
+      for (int a = 0; a < dim; ++a) x[i * dim + a] = x[i * dim + a] + p->dt * p->body_u[a];
+      continue;
     }
+    if (kind[i] != 0) continue;
+    double y[3];
+    for (int a = 0; a < dim; ++a) {
+      double ya = x[i * dim + a] + p->dt * U[i * dim + a];
+      if (p->periodic) {
+        if (ya >= 1.0) ya -= 1.0;
+        else if (ya < 0.0) ya += 1.0;
+      } else if (ya < p->guard) { ya = p->guard; ++clamps; }
+      else if (ya > 1.0 - p->guard) { ya = 1.0 - p->guard; ++clamps; }
+      y[a] = ya;
+    }
+    if (body) {
+      double d[3], r2 = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        d[a] = y[a] - cn[a];
+        r2 = r2 + d[a] * d[a];
+      }
+      if (r2 < rg2) {
+        if (r2 > 0.0) {
+          const double s = rg / sqrt(r2);
+          for (int a = 0; a < dim; ++a) y[a] = cn[a] + d[a] * s;
+        } else {
+          for (int a = 0; a < dim; ++a) y[a] = cn[a] + (a == 0 ? rg : 0.0);
+        }
+        ++clamps;
+      }
+    }
+    for (int a = 0; a < dim; ++a) x[i * dim + a] = y[a];
   }
+  if (body)
+    for (int a = 0; a < dim; ++a) p->body_c[a] = cn[a];
   return clamps;
 }
 
@@ -913,7 +969,7 @@ int or_adjoint_step(const or_params* p, int64_t n, const int32_t* kind, const do
     /* arriving values f_b = sum_j r_bj y_j, and rho_w depends on them through F */
     for (int64_t k = 0; k < NV; ++k) {
       double vn = 0.0;
-      for (int a = 0; a < dim; ++a) vn += vel[k * dim + a] * nb[a];
+      for (int a = 0; a < dim; ++a) vn += (vel[k * dim + a] - uw[a]) * nb[a];
       if (vn > 0.0) continue;
       double l0 = lb[k] + mu * (-vn) / N;
       for (int s = 0; s < cnt[b]; ++s) {
@@ -1025,8 +1081,9 @@ double or_objective(const or_params* p, int64_t n, const int32_t* kind, const do
 /* nsteps steps in place on (x, f, rho, U, T).  rho/U/T hold the moments of the
  * last transported state (interior) or of f_b (walls) and supply U^n on entry.
  * Neighbours and stencils are rebuilt every step with ale = 1, once otherwise.
+ * With a body, p->body_c advances with the motion.
  * Returns OR_OK or an error code; *clamps accumulates wall-guard clamps. */
-int or_run(const or_params* p, int64_t n, double* x, const int32_t* kind, const double* normal,
+int or_run(or_params* p, int64_t n, double* x, const int32_t* kind, const double* normal,
            double* f, double* rho, double* U, double* T, int32_t nsteps, int64_t* clamps) {
   int dim = p->dim, cap = p->max_nbrs;
   int64_t row = ncomp_of(dim) * nvel_of(dim, p->nv);
