@@ -254,13 +254,43 @@ def _rate(g, torch, stream, p: dict, steps: int) -> dict:
     return {"value": upd / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps}
 
 
+def body_managed(g, torch, stream, steps: int = 400, every: int = 100) -> dict:
+    """The moving-disc ALE workload with a point-management pass every `every` steps;
+    time per step includes the passes."""
+    p = bi.config("body2d_ale_n201_v32_f32", spare_points=4000)
+    cl = bi.cloud_for(p)
+    s = g.Solver([p], [cl])
+    s.set_maxwellian(stream=stream)
+    s.step(3, stream=stream)
+    s.sync(stream)
+    rmin, mn = 0.3 * p["dx"], 14
+    merges = adds = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps // every):
+        s.step(every, stream=stream)
+        _, r, a = s.manage(rmin, mn, stream=stream)
+        merges, adds = merges + r, adds + a
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.sync(stream)
+    n = s.n[0]
+    s.close()
+    return {"ms_per_step": ms, "value": n * p["nv"] ** 2 / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "manage_every": every, "merges": merges, "adds": adds, "points_end": n}
+
+
 def extra_configs(g, torch, stream, workload: str) -> dict:
-    """The ALE workload over its Kn sweep, and the plain FP64 41^2 x 16^2 cavity."""
+    """The ALE workload over its Kn sweep, the same cavity with a moving disc (plain and
+    with point management), and the plain FP64 41^2 x 16^2 cavity."""
     out = {}
     p = bi.config(workload)
     if p.get("ale"):
         out["kn_sweep"] = {str(kn): _rate(g, torch, stream, bi.config(workload, kn=kn), 200)
                            for kn in bi.KN_SWEEP_ALE}
+    out["body2d_ale_n201_v32_f32"] = _rate(g, torch, stream, bi.config("body2d_ale_n201_v32_f32"), 200)
+    out["body2d_ale_n201_v32_f32_managed"] = body_managed(g, torch, stream)
     out["cavity2d_n41_v16_f64"] = _rate(g, torch, stream, bi.config("cavity2d_n41_v16_f64"), 100)
     return out
 

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 3
+#define BGK_ABI_VERSION 4
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -85,6 +85,22 @@ typedef struct bgk_params {
   int32_t spare_points; /* room for points that bgk_manage may add beyond the initial
                            count (every per-point array holds n + spare_points) */
   int32_t pad2_;
+  /* Rigid body moving through the gas (Sec. 3.4.1: boundary points move together
+   * with a moving boundary).  body_wall > 0 is the wall id of the body's boundary
+   * points (not lid_wall); 0 means no body.  Each step (ale = 1) the body's centre
+   * and boundary points advance by dt body_u, computed as x + dt*u in FP64 without
+   * fused multiply-add; body_u is also their wall velocity, so the diffuse reflection
+   * classifies velocities by (v - body_u).n and emits M(v; rho_w, body_u, wall_T).
+   * Interior points that end a step closer than body_radius + guard to the centre
+   * are put back on that sphere along the ray from the centre (counted as clamps),
+   * and bgk_manage adds no point inside it.  body_wall, body_centre and
+   * body_radius are fixed at bgk_init; body_u may change through bgk_set_params
+   * and must be zero unless ale = 1. */
+  int32_t body_wall;
+  int32_t pad3_;
+  double body_u[3];      /* body velocity */
+  double body_centre[3]; /* centre of the body at bgk_init */
+  double body_radius;    /* radius of the body's guard sphere (without guard) */
 } bgk_params;
 
 typedef struct bgk_stats {
@@ -163,20 +179,25 @@ int bgk_moments(bgk_ctx* ctx, int32_t c, double* rho, double* u, double* T, int3
 /* Case c's current positions x[n][dim] (host or device destination, as bgk_moments). */
 int bgk_get_positions(bgk_ctx* ctx, int32_t c, double* x, int32_t on_device, void* stream);
 
+/* Case c's current body centre, centre[dim] on the host (Sec. 3.4.1; the centre
+ * advances with the body's points).  Synchronous (waits for the device).  Returns
+ * BGK_E_INVAL when the case has no body (body_wall = 0). */
+int bgk_get_body(bgk_ctx* ctx, int32_t c, double* centre);
+
 /* Wait for the stream and return the first device-side error since the last
  * bgk_sync (then cleared), or BGK_OK. */
 int bgk_sync(bgk_ctx* ctx, void* stream);
 
-/* Checkpoint: the full state (positions, f, moments, step count) of every
- * case as one host blob.  bgk_get_state with blob == NULL stores the size
+/* Checkpoint: the full state (positions, f, moments, body centre, step count)
+ * of every case as one host blob.  bgk_get_state with blob == NULL stores the size
  * needed in *used.  Both calls are synchronous. */
 int bgk_get_state(bgk_ctx* ctx, void* blob, size_t cap, size_t* used);
 int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size);
 
 /* Change the physical parameters of case c: kn, tau_mode, dt, wall_T, lid_u,
- * lid_wall, ale and guard (the wall tables are rebuilt); the geometry, the
- * velocity grid, the storage and the neighbour settings must stay the same
- * (BGK_E_INVAL otherwise).  Synchronous. */
+ * lid_wall, ale, guard and body_u (the wall tables are rebuilt); the geometry,
+ * the body's wall id, centre and radius, the velocity grid, the storage and the
+ * neighbour settings must stay the same (BGK_E_INVAL otherwise).  Synchronous. */
 int bgk_set_params(bgk_ctx* ctx, int32_t c, const bgk_params* p);
 
 /* Point management of case c between steps (Sec. 3.5.2, adding and removing

@@ -42,6 +42,8 @@ class bgk_params(C.Structure):
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
         ("guard", C.c_double), ("lid_u", C.c_double * 3), ("skin", C.c_double),
         ("spare_points", C.c_int32), ("pad2_", C.c_int32),
+        ("body_wall", C.c_int32), ("pad3_", C.c_int32), ("body_u", C.c_double * 3),
+        ("body_centre", C.c_double * 3), ("body_radius", C.c_double),
     ]
 
 
@@ -68,6 +70,7 @@ _SIGS = {
     "bgk_step": (C.c_int, [_P, C.c_int32, _P]),
     "bgk_moments": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_int32, _P]),
     "bgk_get_positions": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P]),
+    "bgk_get_body": (C.c_int, [_P, C.c_int32, _PD]),
     "bgk_sync": (C.c_int, [_P, _P]),
     "bgk_get_state": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "bgk_set_state": (C.c_int, [_P, _P, C.c_size_t]),
@@ -203,6 +206,12 @@ def bgk_get_positions(ctx, case: int, x, stream=None) -> None:
     _check(lib().bgk_get_positions(ctx, case, _ptr(x), _on_device(x), _stream_ptr(stream)), ctx)
 
 
+def bgk_get_body(ctx, case: int, dim: int) -> np.ndarray:
+    c = np.zeros(dim)
+    _check(lib().bgk_get_body(ctx, case, c.ctypes.data_as(_PD)), ctx)
+    return c
+
+
 def bgk_sync(ctx, stream=None) -> None:
     _check(lib().bgk_sync(ctx, _stream_ptr(stream)), ctx)
 
@@ -306,6 +315,13 @@ def params_from(p: dict) -> bgk_params:
         q.lid_u[a] = float(lu[a])
     q.skin = float(p.get("skin", 0.2 if q.ale else 0.0))
     q.spare_points = int(p.get("spare_points", 0))
+    q.body_wall = int(p.get("body_wall", 0))
+    bu = list(p.get("body_u", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
+    bc = list(p.get("body_centre", [0.0, 0.0, 0.0])) + [0.0, 0.0, 0.0]
+    for a in range(3):
+        q.body_u[a] = float(bu[a])
+        q.body_centre[a] = float(bc[a])
+    q.body_radius = float(p.get("body_radius", 0.0))
     return q
 
 
@@ -388,6 +404,10 @@ class Solver:
         x = np.zeros((self.n[case], d))
         bgk_get_positions(self.ctx, case, x)
         return x
+
+    def body_centre(self, case: int = 0):
+        """Current centre of case's moving body."""
+        return bgk_get_body(self.ctx, case, int(self.params[case]["dim"]))
 
     def stats(self):
         return bgk_get_stats(self.ctx)

@@ -178,6 +178,21 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
   if (p.guard < 0 || p.guard >= 0.5) { *why = "guard must be in [0, 0.5)"; return 0; }
   if (!(p.skin >= 0 && p.skin <= 1)) { *why = "skin must be in [0, 1]"; return 0; }
   if (p.spare_points < 0 || n + p.spare_points > (int64_t)1 << 30) { *why = "spare_points out of range"; return 0; }
+  if (p.body_wall < 0) { *why = "body_wall must be >= 0"; return 0; }
+  if (p.body_wall > 0) {
+    if (p.body_wall == p.lid_wall) { *why = "body_wall must differ from lid_wall"; return 0; }
+    if (p.periodic) { *why = "a body needs a walled domain (periodic = 0)"; return 0; }
+    if (!(p.body_radius >= 0) || !std::isfinite(p.body_radius)) { *why = "body_radius must be finite and >= 0"; return 0; }
+    bool moving = false;
+    for (int a = 0; a < 3; ++a) {
+      if (!std::isfinite(p.body_u[a]) || !std::isfinite(p.body_centre[a])) {
+        *why = "body_u and body_centre must be finite";
+        return 0;
+      }
+      moving = moving || p.body_u[a] != 0.0;
+    }
+    if (moving && !p.ale) { *why = "a moving body (body_u != 0) needs ale = 1"; return 0; }
+  }
   return 1;
 }
 
@@ -482,6 +497,9 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.dv = 2.0 * q.vmax / (double)(q.nv - 1);
     for (int a = 0; a < 3; ++a) v.lid_u[a] = q.lid_u[a];
     v.skin = q.skin;
+    v.body_wall = q.body_wall;
+    for (int a = 0; a < 3; ++a) v.body_u[a] = q.body_u[a];
+    v.body_rg = q.body_radius + q.guard;
     // cells of side >= the search radius (h, or h (1 + skin) for the candidate lists)
     v.nc = (int)std::floor(1.0 / (q.h * (1.0 + q.skin) * (1.0 + 1e-9)));
     if (v.nc < 1) v.nc = 1;
@@ -561,7 +579,15 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     if ((st = dalloc(ctx, &v.wcls, (size_t)v.n_wall * v.NVp))) return bail(st);
     if ((st = dalloc_bytes(ctx, &v.wvn, (size_t)v.n_wall * v.NVp * c.c_bytes))) return bail(st);
     if ((st = dalloc(ctx, &v.winv, v.n_wall))) return bail(st);
-    if ((st = dalloc_bytes(ctx, &v.mw, (size_t)2 * v.NVp * c.c_bytes))) return bail(st);
+    if ((st = dalloc_bytes(ctx, &v.mw, (size_t)3 * v.NVp * c.c_bytes))) return bail(st);
+    if (q.body_wall > 0) {
+      if ((st = dalloc(ctx, &v.body, 1))) return bail(st);
+      BodyState b0;
+      memset(&b0, 0, sizeof(b0));
+      for (int a = 0; a < dim; ++a) b0.c[a] = q.body_centre[a];
+      if (cudaMemcpy(v.body, &b0, sizeof(b0), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(ctx, BGK_E_CUDA, "case %d: body state upload failed", ci));
+    }
     const size_t fbytes = (size_t)ncap * v.ncomp * v.NVp * c.s_bytes;
     for (int b = 0; b < 2; ++b) {
       if ((st = dalloc_bytes(ctx, &c.f[b], fbytes))) return bail(st);
@@ -809,6 +835,16 @@ int bgk_get_positions(bgk_ctx* ctx, int32_t ci, double* x, int32_t on_device, vo
   return BGK_OK;
 }
 
+int bgk_get_body(bgk_ctx* ctx, int32_t ci, double* centre) {
+  if (!ctx || !centre || ci < 0 || ci >= (int)ctx->cases.size())
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_get_body: bad argument") : BGK_E_INVAL;
+  CaseHost& c = ctx->cases[ci];
+  if (!c.cv.body) return fail(ctx, BGK_E_INVAL, "bgk_get_body: case %d has no body", ci);
+  CK(ctx, cudaDeviceSynchronize());
+  CK(ctx, cudaMemcpy(centre, reinterpret_cast<const double*>(c.cv.body), sizeof(double) * c.cv.dim, cudaMemcpyDeviceToHost));
+  return BGK_OK;
+}
+
 int bgk_sync(bgk_ctx* ctx, void* stream) {
   if (!ctx) return BGK_E_INVAL;
   CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));
@@ -832,7 +868,8 @@ int bgk_get_state(bgk_ctx* ctx, void* blob, size_t cap, size_t* used) {
   size_t need = 4 * sizeof(uint64_t);
   for (auto& c : ctx->cases)
     need += 4 * sizeof(int64_t) + sizeof(double) * c.cv.n * c.cv.dim +
-            (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes + sizeof(double) * c.cv.n * MOM_STRIDE;
+            (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes + sizeof(double) * c.cv.n * MOM_STRIDE +
+            sizeof(double) * 3;
   *used = need;
   if (!blob) return BGK_OK;
   if (cap < need) return fail(ctx, BGK_E_INVAL, "bgk_get_state: cap %zu < %zu", cap, need);
@@ -854,6 +891,10 @@ int bgk_get_state(bgk_ctx* ctx, void* blob, size_t cap, size_t* used) {
     b = sizeof(double) * c.cv.n * MOM_STRIDE;
     CK(ctx, cudaMemcpy(o, c.cv.mom, b, cudaMemcpyDeviceToHost));
     o += b;
+    double bc[3] = {0.0, 0.0, 0.0};
+    if (c.cv.body) CK(ctx, cudaMemcpy(bc, reinterpret_cast<const double*>(c.cv.body), sizeof(bc), cudaMemcpyDeviceToHost));
+    memcpy(o, bc, sizeof(bc));
+    o += sizeof(bc);
   }
   return BGK_OK;
 }
@@ -885,6 +926,13 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
     b = sizeof(double) * c.cv.n * MOM_STRIDE;
     CK(ctx, cudaMemcpy(c.cv.mom, o, b, cudaMemcpyHostToDevice));
     o += b;
+    if (c.cv.body) {
+      BodyState b0;
+      memset(&b0, 0, sizeof(b0));
+      memcpy(b0.c, o, sizeof(b0.c));
+      CK(ctx, cudaMemcpy(c.cv.body, &b0, sizeof(b0), cudaMemcpyHostToDevice));
+    }
+    o += 3 * sizeof(double);
     c.stencils_valid = false;
     if (int st = reset_skin(ctx, c)) return st;  // positions changed: rebuild the candidates
     c.cur = 0;
@@ -904,8 +952,11 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   if (!check_params(*p, c.cv.n, &why)) return fail(ctx, BGK_E_INVAL, "bgk_set_params: %s", why);
   if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
       p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin ||
-      p->spare_points != o.spare_points)
-    return fail(ctx, BGK_E_INVAL, "bgk_set_params: only kn, tau_mode, dt, wall_T, lid_u, lid_wall, ale, guard may change");
+      p->spare_points != o.spare_points || p->body_wall != o.body_wall || p->body_radius != o.body_radius ||
+      p->body_centre[0] != o.body_centre[0] || p->body_centre[1] != o.body_centre[1] ||
+      p->body_centre[2] != o.body_centre[2])
+    return fail(ctx, BGK_E_INVAL,
+                "bgk_set_params: only kn, tau_mode, dt, wall_T, lid_u, lid_wall, ale, guard, body_u may change");
   CK(ctx, cudaDeviceSynchronize());
   c.p = *p;
   CaseView& v = c.cv;
@@ -923,6 +974,8 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   v.ale = p->ale;
   v.guard = p->guard;
   for (int a = 0; a < 3; ++a) v.lid_u[a] = p->lid_u[a];
+  for (int a = 0; a < 3; ++a) v.body_u[a] = p->body_u[a];
+  v.body_rg = p->body_radius + p->guard;
   refresh_view(c);
   ctx->launches += launch_init_tables(v, 0);
   CKL(ctx);

@@ -23,6 +23,14 @@ struct SkinState {
   int32_t pad;
 };
 
+// Rigid body (body_wall > 0): its current centre and the CTA counter of the motion
+// kernel, whose last CTA advances the centre after every CTA has read it.
+struct BodyState {
+  double c[3];
+  uint32_t blocks;
+  int32_t pad;
+};
+
 struct DevStatus {
   int32_t flags;
   int32_t pad;
@@ -62,11 +70,13 @@ struct CaseView {
   void* P;       // [n][cap][dim*dim] projected frame vectors, compute type
   void* recon;   // [n][cap] wall reconstruction weights, compute type
 
-  // wall tables (fixed walls): per wall slot w = 0..n_wall-1
-  int8_t* wcls;    // [n_wall][NVp] 1 leaving (v.n > 0), 0 arriving
-  void* wvn;       // [n_wall][NVp] |v.n|, compute type
-  double* winv;    // [n_wall] 1 / sum_{v.n>0} (v.n) M_w(v)
-  void* mw;        // [2][NVp] wall Maxwellian G1 (or M) with rho = 1: [0] wall at rest, [1] lid
+  // wall tables: per wall slot w = 0..n_wall-1, with c_n = (v - u_w).n the normal
+  // velocity relative to the wall (constant in time: walls at rest, the lid moving
+  // tangentially, the body translating without rotation)
+  int8_t* wcls;    // [n_wall][NVp] 1 leaving (c_n > 0), 0 arriving
+  void* wvn;       // [n_wall][NVp] |c_n|, compute type
+  double* winv;    // [n_wall] 1 / sum_{c_n>0} c_n M_w(v)
+  void* mw;        // [3][NVp] wall Maxwellian G1 (or M) with rho = 1: [0] at rest, [1] lid, [2] body
 
   void* f_in;    // [n][ncomp][NVp] storage type
   void* f_out;   // [n][ncomp][NVp] storage type
@@ -82,6 +92,13 @@ struct CaseView {
   int32_t* ccnt;        // [n]
   int32_t* ccol;        // [n][ccap] candidates, ascending
   SkinState* sk;
+
+  // rigid body (body_wall = 0: none)
+  int32_t body_wall;
+  int32_t pad_body;
+  double body_u[3];
+  double body_rg;       // guard radius body_radius + guard
+  BodyState* body;
 };
 
 // Launchers (stream-ordered; each returns the number of kernels launched).

@@ -7,7 +7,8 @@
 // neighbour and closer than rmin merge at the midpoint (the survivor keeps i's
 // slot); an interior point in no merge with fewer than min_nbrs neighbours gets a
 // new interior point at x_i - (h/2) c/|c|, c the sum of its neighbour separations,
-// if that lies in [guard, 1 - guard]^dim (wrapped when periodic) and no point of
+// if that lies in [guard, 1 - guard]^dim (wrapped when periodic), outside the body's
+// guard sphere (distance >= body_radius + guard from its centre) and no point of
 // N(i) + {i} is within rmin of it.  f at a new position y is the linear WLS
 // reconstruction at y from N(i) + {i}: p_k = (1, x_k - y), w_k = exp(-alpha
 // |x_k - y|^2 / h^2), r_k = e_0^T (sum w p p^T)^-1 w_k p_k (the constant fit where
@@ -81,6 +82,15 @@ __global__ void k_pm_roles(CaseView cv, const int32_t* nn, double rmin2, int min
         if (cv.periodic) ya = wrap_unit(ya);
         else if (ya < cv.guard || ya > 1.0 - cv.guard) ok = false;
         y[a] = ya;
+      }
+      if (ok && cv.body) {
+        // not inside the body's guard sphere
+        double d2 = 0.0;
+        for (int a = 0; a < dim; ++a) {
+          const double d = __dadd_rn(cv.body->c[a], -y[a]);
+          d2 = __dadd_rn(d2, __dmul_rn(d, d));
+        }
+        ok = !(d2 < __dmul_rn(cv.body_rg, cv.body_rg));
       }
       if (ok) {
         double d2 = 0.0;

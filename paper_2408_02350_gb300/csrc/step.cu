@@ -457,7 +457,9 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   S* fb = f + (int64_t)b * rowlen;
   const int8_t* cls = cv.wcls + (int64_t)w * NVp;
   const C* vn = reinterpret_cast<const C*>(cv.wvn) + (int64_t)w * NVp;
-  const C* Mw = reinterpret_cast<const C*>(cv.mw) + (cv.kind[b] == cv.lid_wall ? NVp : 0);
+  const int kb = cv.kind[b];
+  const int mrow = kb == cv.lid_wall ? 1 : (cv.body_wall > 0 && kb == cv.body_wall ? 2 : 0);
+  const C* Mw = reinterpret_cast<const C*>(cv.mw) + (int64_t)mrow * NVp;
 
   C flux[1] = {(C)0};
   C part[DIM + 2];
@@ -593,9 +595,17 @@ int launch_walls(const CaseView& cv, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// wall tables (fixed walls): classification, |v.n|, 1/sum_{v.n>0} (v.n) M_w
-// and the unit-density wall Maxwellians, all evaluated in FP64
+// wall tables: classification by the normal velocity relative to the wall,
+// c_n = (v - u_w).n, |c_n|, 1/sum_{c_n>0} c_n M_w and the unit-density wall
+// Maxwellians, all evaluated in FP64.  u_w is lid_u on the lid, body_u on the
+// body, zero elsewhere; the tables stay valid while the walls translate.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ const double* wall_velocity(const CaseView& cv, int kb, const double* zero) {
+  if (kb == cv.lid_wall) return cv.lid_u;
+  if (cv.body_wall > 0 && kb == cv.body_wall) return cv.body_u;
+  return zero;
+}
+
 template <typename C, int DIM>
 __global__ void k_wall_tables(CaseView cv) {
   __shared__ double s_sum[32];
@@ -605,7 +615,8 @@ __global__ void k_wall_tables(CaseView cv) {
   double nb[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) nb[a] = cv.normal[(int64_t)b * DIM + a];
-  const bool lid = cv.kind[b] == cv.lid_wall;
+  const double zero[3] = {0.0, 0.0, 0.0};
+  const double* uw = wall_velocity(cv, cv.kind[b], zero);
   const double pi = 3.14159265358979323846, T = cv.wall_T;
   const double pref = DIM == 2 ? 1.0 / (2.0 * pi * T) : 1.0 / pow(2.0 * pi * T, 1.5);
   double acc = 0.0;
@@ -619,8 +630,8 @@ __global__ void k_wall_tables(CaseView cv) {
       for (int a = 0; a < DIM; ++a) {
         const double va = cv.vnodes[kk % nv];
         kk /= nv;
-        vn = __dadd_rn(vn, __dmul_rn(va, nb[a]));
-        const double c = va - (lid ? cv.lid_u[a] : 0.0);
+        const double c = __dadd_rn(va, -uw[a]);
+        vn = __dadd_rn(vn, __dmul_rn(c, nb[a]));
         c2 += c * c;
       }
       cl = vn > 0.0 ? 1 : 0;
@@ -647,19 +658,21 @@ __global__ void k_mw_table(CaseView cv) {
   if (k >= cv.NVp) return;
   const double pi = 3.14159265358979323846, T = cv.wall_T;
   const double pref = DIM == 2 ? 1.0 / (2.0 * pi * T) : 1.0 / pow(2.0 * pi * T, 1.5);
-  for (int lid = 0; lid < 2; ++lid) {
+  const double zero[3] = {0.0, 0.0, 0.0};
+  for (int row = 0; row < 3; ++row) {
+    const double* uw = row == 0 ? zero : (row == 1 ? cv.lid_u : cv.body_u);
     double M = 0.0;
     if (k < cv.NV) {
       int kk = k;
       double c2 = 0.0;
       for (int a = 0; a < DIM; ++a) {
-        const double c = cv.vnodes[kk % cv.nv] - (lid ? cv.lid_u[a] : 0.0);
+        const double c = cv.vnodes[kk % cv.nv] - uw[a];
         kk /= cv.nv;
         c2 += c * c;
       }
       M = pref * exp(-c2 / (2.0 * T));
     }
-    reinterpret_cast<C*>(cv.mw)[lid * cv.NVp + k] = (C)M;
+    reinterpret_cast<C*>(cv.mw)[row * cv.NVp + k] = (C)M;
   }
 }
 
@@ -698,58 +711,109 @@ int launch_init_tables(const CaseView& cv, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // point motion (Eqs. originalALE1, ALE1)
 // ---------------------------------------------------------------------------
-// x_i += dt U_i^{n+1} for one interior point (FP64 without fused multiply-add,
-// clamped to [guard, 1 - guard] or wrapped in a periodic box); with skin lists also
-// the FP32 split of x_i, and the squared displacement since the candidate build is
-// returned.
-__device__ __forceinline__ double move_point(const CaseView& cv, const int i) {
-  unsigned long long nclamp = 0;
+// Stores the new position y of point i; with skin lists also the FP32 split of y
+// (the prefilters read it; k_cell_assign sets it only when the cells are rebuilt),
+// and returns the squared displacement since the candidate build.
+__device__ __forceinline__ double store_position(const CaseView& cv, const int i, const double* y) {
   double d2 = 0.0;
   for (int a = 0; a < cv.dim; ++a) {
-    double* xa = cv.x + (int64_t)i * cv.dim + a;
-    double y = __dadd_rn(*xa, __dmul_rn(cv.dt, cv.mom[(int64_t)i * MOM_STRIDE + 1 + a]));
-    if (cv.periodic) {
-      if (y >= 1.0) y = __dadd_rn(y, -1.0);
-      else if (y < 0.0) y = __dadd_rn(y, 1.0);
-    } else if (y < cv.guard) { y = cv.guard; ++nclamp; }
-    else if (y > 1.0 - cv.guard) { y = 1.0 - cv.guard; ++nclamp; }
-    *xa = y;
+    cv.x[(int64_t)i * cv.dim + a] = y[a];
     if (cv.sk) {
-      // FP32 split for the prefilters (k_cell_assign sets it only when the cells are rebuilt)
-      const float hi = (float)y;
+      const float hi = (float)y[a];
       cv.xf[(int64_t)i * cv.dim + a] = hi;
-      cv.xlo[(int64_t)i * cv.dim + a] = (float)(y - (double)hi);
-      const double d = __dadd_rn(y, -cv.xb[(int64_t)i * cv.dim + a]);
+      cv.xlo[(int64_t)i * cv.dim + a] = (float)(y[a] - (double)hi);
+      const double d = __dadd_rn(y[a], -cv.xb[(int64_t)i * cv.dim + a]);
       d2 = __dadd_rn(d2, __dmul_rn(d, d));
     }
   }
-  if (nclamp) atomicAdd(&cv.status->clamps, nclamp);
   return d2;
 }
 
-// After every CTA has merged its maximum squared displacement (bits b) into disp2,
-// the last one decides whether the next list build rebuilds the candidates.
-__device__ __forceinline__ void skin_merge(const CaseView& cv, uint32_t b, double thr2) {
-  atomicMax(&cv.sk->disp2, b);
+// x_i += dt U_i^{n+1} for one interior point (FP64 without fused multiply-add),
+// clamped to [guard, 1 - guard] or wrapped in a periodic box.  With a body (cn =
+// its centre after this step, else null), a point that ends closer than body_rg to
+// cn is put back on that sphere along the ray from cn (at cn + body_rg e_x if it
+// sits on cn).  Every clamp is counted.
+__device__ __forceinline__ double move_point(const CaseView& cv, const int i, const double* cn) {
+  unsigned long long nclamp = 0;
+  double y[3];
+  for (int a = 0; a < cv.dim; ++a) {
+    double ya = __dadd_rn(cv.x[(int64_t)i * cv.dim + a], __dmul_rn(cv.dt, cv.mom[(int64_t)i * MOM_STRIDE + 1 + a]));
+    if (cv.periodic) {
+      if (ya >= 1.0) ya = __dadd_rn(ya, -1.0);
+      else if (ya < 0.0) ya = __dadd_rn(ya, 1.0);
+    } else if (ya < cv.guard) { ya = cv.guard; ++nclamp; }
+    else if (ya > 1.0 - cv.guard) { ya = 1.0 - cv.guard; ++nclamp; }
+    y[a] = ya;
+  }
+  if (cn) {
+    double d[3], r2 = 0.0;
+    for (int a = 0; a < cv.dim; ++a) {
+      d[a] = __dadd_rn(y[a], -cn[a]);
+      r2 = __dadd_rn(r2, __dmul_rn(d[a], d[a]));
+    }
+    const double rg = cv.body_rg;
+    if (r2 < __dmul_rn(rg, rg)) {
+      if (r2 > 0.0) {
+        const double sc = __ddiv_rn(rg, __dsqrt_rn(r2));
+        for (int a = 0; a < cv.dim; ++a) y[a] = __dadd_rn(cn[a], __dmul_rn(d[a], sc));
+      } else {
+        for (int a = 0; a < cv.dim; ++a) y[a] = __dadd_rn(cn[a], a == 0 ? rg : 0.0);
+      }
+      ++nclamp;
+    }
+  }
+  if (nclamp) atomicAdd(&cv.status->clamps, nclamp);
+  return store_position(cv, i, y);
+}
+
+// A boundary point of the body: x_b += dt body_u.
+__device__ __forceinline__ double move_body_point(const CaseView& cv, const int b) {
+  double y[3];
+  for (int a = 0; a < cv.dim; ++a) y[a] = __dadd_rn(cv.x[(int64_t)b * cv.dim + a], __dmul_rn(cv.dt, cv.body_u[a]));
+  return store_position(cv, b, y);
+}
+
+// After every CTA has read the body centre and merged its maximum squared
+// displacement (bits b) into disp2, the last one decides whether the next list
+// build rebuilds the candidates and advances the centre to cn.
+__device__ __forceinline__ void move_merge(const CaseView& cv, uint32_t b, double thr2, const double* cn) {
+  if (cv.sk) atomicMax(&cv.sk->disp2, b);
   __threadfence();
-  if (atomicAdd(&cv.sk->blocks, 1u) == gridDim.x - 1) {
+  uint32_t* ctr = cv.sk ? &cv.sk->blocks : &cv.body->blocks;
+  if (atomicAdd(ctr, 1u) == gridDim.x - 1) {
     __threadfence();
-    const uint32_t d = atomicOr(&cv.sk->disp2, 0u);
-    const int rb = (double)__uint_as_float(d) > thr2;
-    cv.sk->rebuild = rb;
-    if (rb) cv.sk->disp2 = 0u;
-    cv.sk->blocks = 0u;
+    if (cv.sk) {
+      const uint32_t d = atomicOr(&cv.sk->disp2, 0u);
+      const int rb = (double)__uint_as_float(d) > thr2;
+      cv.sk->rebuild = rb;
+      if (rb) cv.sk->disp2 = 0u;
+    }
+    if (cv.body)
+      for (int a = 0; a < cv.dim; ++a) cv.body->c[a] = cn[a];
+    *ctr = 0u;
   }
 }
 
-// With skin lists the kernel also tracks max |x - x_b|^2; its last CTA decides
-// whether the next list build rebuilds the candidates (max |x - x_b| > h skin / 2,
-// thr2 = (h skin / 2)^2 (1 - 1e-6)).
+// Threads [0, n_int) move the interior points, threads [n_int, n_int + n_wall) the
+// body's boundary points among the wall points (when there is a body).  With skin
+// lists the kernel also tracks max |x - x_b|^2; its last CTA decides whether the next
+// list build rebuilds the candidates (max |x - x_b| > h skin / 2, thr2 = (h skin /
+// 2)^2 (1 - 1e-6)) and advances the body centre.
 __global__ void __launch_bounds__(256) k_move(CaseView cv, double thr2) {
   __shared__ uint32_t s_max[8];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const double d2 = t < cv.n_int ? move_point(cv, cv.int_idx[t]) : 0.0;
-  if (cv.sk) {
+  double cn[3] = {0.0, 0.0, 0.0};
+  if (cv.body)
+    for (int a = 0; a < cv.dim; ++a) cn[a] = __dadd_rn(cv.body->c[a], __dmul_rn(cv.dt, cv.body_u[a]));
+  double d2 = 0.0;
+  if (t < cv.n_int) {
+    d2 = move_point(cv, cv.int_idx[t], cv.body ? cn : nullptr);
+  } else if (cv.body && t < cv.n_int + cv.n_wall) {
+    const int b = cv.wall_idx[t - cv.n_int];
+    if (cv.kind[b] == cv.body_wall) d2 = move_body_point(cv, b);
+  }
+  if (cv.sk || cv.body) {
     // CTA maximum of the displacement bits (non-negative floats order as integers)
     const uint32_t w = __reduce_max_sync(0xffffffffu, __float_as_uint(__double2float_ru(d2)));
     if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = w;
@@ -757,15 +821,16 @@ __global__ void __launch_bounds__(256) k_move(CaseView cv, double thr2) {
     if (threadIdx.x == 0) {
       uint32_t b = 0;
       for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b = max(b, s_max[k]);
-      skin_merge(cv, b, thr2);
+      move_merge(cv, b, thr2, cn);
     }
   }
 }
 
 int launch_move(const CaseView& cv, cudaStream_t s) {
-  if (cv.n_int == 0) return 0;
+  const int64_t n = (int64_t)cv.n_int + (cv.body ? cv.n_wall : 0);
+  if (n == 0) return 0;
   const double half = 0.5 * cv.h * cv.skin;
-  k_move<<<grid_for(cv.n_int, 256), 256, 0, s>>>(cv, half * half * (1.0 - 1e-6));
+  k_move<<<grid_for(n, 256), 256, 0, s>>>(cv, half * half * (1.0 - 1e-6));
   return 1;
 }
 

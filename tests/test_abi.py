@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in _declared() if not hasattr(h, n)]
     assert not missing, missing
     assert set(_declared()) <= set(lib.exported_symbols()) | {"bgk_version"}
-    assert lib.bgk_version() == 3
+    assert lib.bgk_version() == 4
 
 
 @pytest.mark.parametrize("struct", ["bgk_params", "bgk_stats"])
@@ -70,6 +70,25 @@ def test_init_rejects_bad_parameters_before_touching_the_device(lib, field, valu
         lib.bgk_init([q], [len(cl["kind"])], cl["x"], cl["kind"], cl["normal"])
     assert e.value.code == lib.BGK_E_INVAL
     assert "bgk_init" in lib.bgk_last_error(None)
+
+
+@pytest.mark.parametrize("change", ["moving_without_ale", "lid_id", "negative_radius", "negative_id"])
+def test_init_rejects_bad_body_parameters(lib, change):
+    p = bi.config("body2d_ale_n201_v32_f32", n=11, nv=4, storage="f64", body_radius=0.2, body_centre=[0.5, 0.5, 0.0])
+    cl = bi.cloud_for(p)
+    q = lib.params_from(p)
+    if change == "moving_without_ale":
+        q.ale = 0
+    elif change == "lid_id":
+        q.body_wall = q.lid_wall
+    elif change == "negative_radius":
+        q.body_radius = -0.1
+    else:
+        q.body_wall = -1
+    with pytest.raises(lib.BGKError) as e:
+        lib.bgk_init([q], [len(cl["kind"])], cl["x"], cl["kind"], cl["normal"])
+    assert e.value.code == lib.BGK_E_INVAL
+    assert "body" in lib.bgk_last_error(None)
 
 
 def test_product_path_does_not_import_the_oracle():
