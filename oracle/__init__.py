@@ -306,10 +306,11 @@ def move(p: dict, kind, U, x) -> int:
 
 
 def manage(p: dict, x, kind, normal, f, cnt, col, rmin: float, min_nbrs: int, cap_out: int | None = None):
-    """One pass of point management (Sec. 3.5.2): merge mutually nearest interior pairs
-    closer than rmin at their midpoint, add points into holes next to interior points
-    with fewer than min_nbrs neighbours; f at new positions by linear WLS
-    reconstruction.  Returns dict(x, kind, normal, f, origin, merges, adds)."""
+    """One pass of point management (Sec. 3.5.2): remove interior points closer than rmin
+    to a wall point, merge mutually nearest remaining interior pairs closer than rmin at
+    their midpoint, add points into holes next to interior points with fewer than
+    min_nbrs neighbours; f at new positions by linear WLS reconstruction.  Returns
+    dict(x, kind, normal, f, origin, merges, adds, wall_removals)."""
     q = params(p)
     x, f = _f64(x), _f64(f)
     n, dim = x.shape
@@ -319,14 +320,15 @@ def manage(p: dict, x, kind, normal, f, cnt, col, rmin: float, min_nbrs: int, ca
     no = np.zeros((cap_out, dim))
     fo = np.zeros((cap_out,) + f.shape[1:])
     org = np.zeros(cap_out, dtype=np.int64)
-    counts = np.zeros(2, dtype=np.int64)
+    counts = np.zeros(3, dtype=np.int64)
     m = lib().or_manage(C.byref(q), n, _d(x), _i(_i32(kind)), _d(_f64(normal)), _d(f), _i(_i32(cnt)), _i(_i32(col)),
                         float(rmin), int(min_nbrs), cap_out, _d(xo), _i(ko), _d(no), _d(fo),
                         org.ctypes.data_as(_PL), counts.ctypes.data_as(_PL))
     if m < 0:
         raise MemoryError("or_manage")
     return {"x": xo[:m].copy(), "kind": ko[:m].copy(), "normal": no[:m].copy(), "f": fo[:m].copy(),
-            "origin": org[:m].copy(), "merges": int(counts[0]), "adds": int(counts[1])}
+            "origin": org[:m].copy(), "merges": int(counts[0]), "adds": int(counts[1]),
+            "wall_removals": int(counts[2])}
 
 
 def adjoint_step(p: dict, kind, normal, cnt, col, st: dict, f, lam1):

@@ -505,9 +505,13 @@ static void recon_at(const or_params* p, const double* y, const double* x, const
 /*
  * One pass of point management on the neighbour lists cnt/col of x (radius h).
  * Readings (the paper names the operations, not their thresholds):
- *  - remove: interior points i and j that are each other's nearest interior
- *    neighbour (ties to the smaller index) and closer than rmin are replaced by
- *    one point at their midpoint (the survivor keeps i's slot, i < j);
+ *  - remove next to a wall: an interior point closer than rmin to a wall point
+ *    (any wall id, the body's included) is removed; the wall point stays on the
+ *    boundary;
+ *  - remove a pair: interior points i and j that stay after that, are each
+ *    other's nearest such neighbour (ties to the smaller index) and are closer
+ *    than rmin are replaced by one point at their midpoint (the survivor keeps
+ *    i's slot, i < j);
  *  - add: an interior point i that takes part in no merge and has fewer than
  *    min_nbrs neighbours gets a new interior point at x_i - (h/2) c/|c|, c the
  *    sum of the separations to its neighbours (away from them, into the hole),
@@ -520,7 +524,8 @@ static void recon_at(const or_params* p, const double* y, const double* x, const
  * midpoint), then the added points in the order of the points that made them;
  * at most cap_out points (later additions are dropped).  origin[k] is the old
  * index of output point k, -1 for an added point.  counts[0] = merged pairs,
- * counts[1] = added points.  Returns the new point count.
+ * counts[1] = added points, counts[2] = points removed next to a wall.  Returns
+ * the new point count.
  */
 int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t* kind, const double* normal,
                   const double* f, const int32_t* cnt, const int32_t* col, double rmin, int32_t min_nbrs,
@@ -530,19 +535,33 @@ int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t*
   const int64_t NV = nvel_of(dim, p->nv), row = (int64_t)ncomp_of(dim) * NV;
   const double rmin2 = rmin * rmin;
   int64_t* nn = (int64_t*)malloc(sizeof(int64_t) * n);
-  int32_t* role = (int32_t*)calloc(n, sizeof(int32_t)); /* 0 keep, 1 merge survivor, 2 merged away, 3 adds */
+  /* 0 keep, 1 merge survivor, 2 merged away, 3 adds, 4 removed next to a wall */
+  int32_t* role = (int32_t*)calloc(n, sizeof(int32_t));
   double* ynew = (double*)malloc(sizeof(double) * n * dim);
   int32_t* src = (int32_t*)malloc(sizeof(int32_t) * (cap + 1));
   double* r = (double*)malloc(sizeof(double) * (cap + 1));
   if (!nn || !role || !ynew || !src || !r) { free(nn); free(role); free(ynew); free(src); free(r); return -1; }
-  /* nearest interior neighbour */
+  /* interior points too close to a wall point */
+  int64_t wall_removed = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != 0) continue;
+    for (int s = 0; s < cnt[i]; ++s) {
+      int32_t j = col[i * cap + s];
+      if (kind[j] != 0 && dist2(dim, x + i * dim, x + (int64_t)j * dim, p->periodic) < rmin2) {
+        role[i] = 4;
+        ++wall_removed;
+        break;
+      }
+    }
+  }
+  /* nearest interior neighbour among the points that stay */
   for (int64_t i = 0; i < n; ++i) {
     nn[i] = -1;
-    if (kind[i] != 0) continue;
+    if (kind[i] != 0 || role[i] == 4) continue;
     double best = 0.0;
     for (int s = 0; s < cnt[i]; ++s) {
       int32_t j = col[i * cap + s];
-      if (kind[j] != 0) continue;
+      if (kind[j] != 0 || role[j] == 4) continue;
       double d2 = dist2(dim, x + i * dim, x + (int64_t)j * dim, p->periodic);
       if (nn[i] < 0 || d2 < best) { nn[i] = j; best = d2; }
     }
@@ -591,7 +610,7 @@ int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t*
   /* output: survivors, then additions */
   int64_t k = 0;
   for (int64_t i = 0; i < n && k < cap_out; ++i) {
-    if (role[i] == 2) continue;
+    if (role[i] == 2 || role[i] == 4) continue;
     for (int a = 0; a < dim; ++a) normal_out[k * dim + a] = normal[i * dim + a];
     kind_out[k] = kind[i];
     origin[k] = i;
@@ -642,6 +661,7 @@ int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t*
   }
   counts[0] = merges;
   counts[1] = adds;
+  counts[2] = wall_removed;
   free(nn); free(role); free(ynew); free(src); free(r);
   return k;
 }

@@ -66,7 +66,7 @@ def test_manage_matches_oracle(g, storage, tol):
     s = g.Solver([p], [cl])
     s.set_f(np.ascontiguousarray(f) if storage == "f64" else np.ascontiguousarray(f, dtype=np.float32))
     nn, removed, added = s.manage(rmin, mn)
-    assert (nn, removed, added) == (len(ref["x"]), ref["merges"], ref["adds"])
+    assert (nn, removed, added) == (len(ref["x"]), ref["merges"] + ref["wall_removals"], ref["adds"])
     assert np.array_equal(s.positions(), ref["x"])
     fg = s.get_f(0, np.float64)
     fo = ref["f"].reshape(fg.shape)
@@ -96,7 +96,7 @@ def test_steps_after_manage_match_oracle(g, ale):
     cl5 = {"x": sim.x, "kind": sim.kind, "normal": sim.normal}
     ref = _oracle_manage(p, cl5, sim.f, rmin, mn, n + 64)
     nn, removed, added = s.manage(rmin, mn)
-    assert (nn, removed, added) == (len(ref["x"]), ref["merges"], ref["adds"])
+    assert (nn, removed, added) == (len(ref["x"]), ref["merges"] + ref["wall_removals"], ref["adds"])
     assert np.abs(s.positions() - ref["x"]).max() < 1e-14
     s.step(10)
     s.sync()
@@ -116,7 +116,7 @@ def test_capacity_bounds_additions(g):
     n = len(cl["kind"])
     full = _oracle_manage(p, cl, _f0(p, n), rmin, mn, n + 64)
     assert full["adds"] > 2
-    merges = full["merges"]
+    merges = full["merges"] + full["wall_removals"]
     spare = 2
     p = dict(p, storage="f64", spare_points=spare)
     f = _f0(p, n)
@@ -125,7 +125,7 @@ def test_capacity_bounds_additions(g):
     s.set_f(np.ascontiguousarray(f))
     nn, removed, added = s.manage(rmin, mn)
     assert ref["adds"] < full["adds"] and ref["adds"] == min(full["adds"], merges + spare)
-    assert (nn, removed, added) == (len(ref["x"]), ref["merges"], ref["adds"]) and nn <= n + spare
+    assert (nn, removed, added) == (len(ref["x"]), ref["merges"] + ref["wall_removals"], ref["adds"]) and nn <= n + spare
     assert np.array_equal(s.positions(), ref["x"])
     s.close()
 
@@ -143,7 +143,7 @@ def test_second_pass_after_first(g):
     cl1 = {"x": r1["x"], "kind": r1["kind"], "normal": r1["normal"]}
     r2 = _oracle_manage(p, cl1, r1["f"], rmin, mn, n + 200)
     nn, removed, added = s.manage(rmin, mn)
-    assert (nn, removed, added) == (len(r2["x"]), r2["merges"], r2["adds"])
+    assert (nn, removed, added) == (len(r2["x"]), r2["merges"] + r2["wall_removals"], r2["adds"])
     assert np.array_equal(s.positions(), r2["x"])
     fg = s.get_f(0, np.float64)
     assert np.abs(fg - r2["f"].reshape(fg.shape)).max() <= 1e-12 * np.abs(r2["f"]).max()

@@ -196,3 +196,48 @@ def test_periodic_pair_merges_across_the_edge():
     s = list(out["origin"]).index(min(i, j))
     xm = out["x"][s, 0]
     assert abs(xm - (1.0 - 0.005 * dx)) < 1e-15 and abs(out["x"][s, 1] - 7 * dx) < 1e-15
+
+
+def test_point_next_to_a_wall_is_removed():
+    p, cl = _setup()
+    x = cl["x"].copy()
+    dx = 1.0 / (p["n"] - 1)
+    # the interior point next to the wall point at (0.5, 0), moved to 0.1 dx above it
+    w = int(np.argmin(np.sum((x - [0.5, 0.0]) ** 2, axis=1)))
+    i = int(np.argmin(np.sum((x - [0.5, dx]) ** 2, axis=1)))
+    assert cl["kind"][w] != 0 and cl["kind"][i] == 0
+    x[i] = x[w] + [0.0, 0.1 * dx]
+    cnt, col = _lists(p, x)
+    rng = np.random.default_rng(4)
+    f = rng.uniform(0.5, 1.5, size=(len(x),) + _f_shape(p))
+    out = oracle.manage(p, x, cl["kind"], cl["normal"], f, cnt, col, 0.25 * dx, 0)
+    assert out["wall_removals"] == 1 and out["merges"] == 0 and out["adds"] == 0
+    keep = np.array([k for k in range(len(x)) if k != i])
+    assert np.array_equal(out["origin"], keep)
+    assert np.array_equal(out["x"], x[keep]) and np.array_equal(out["f"], f[keep])
+
+
+def test_point_removed_at_a_wall_takes_no_partner():
+    # a is 0.1 dx above a wall point and b 0.2 dx above a (0.3 dx from the wall, so
+    # closer to a than rmin but not to the wall): a goes, b stays where it is
+    p, cl = _setup()
+    x = cl["x"].copy()
+    dx = 1.0 / (p["n"] - 1)
+    w = int(np.argmin(np.sum((x - [0.5, 0.0]) ** 2, axis=1)))
+    a = int(np.argmin(np.sum((x - [0.5, dx]) ** 2, axis=1)))
+    b = int(np.argmin(np.sum((x - [0.5, 2 * dx]) ** 2, axis=1)))
+    x[a] = x[w] + [0.0, 0.1 * dx]
+    x[b] = x[a] + [0.0, 0.2 * dx]
+    cnt, col = _lists(p, x)
+    f = np.ones((len(x),) + _f_shape(p))
+    out = oracle.manage(p, x, cl["kind"], cl["normal"], f, cnt, col, 0.25 * dx, 0)
+    assert out["wall_removals"] == 1 and out["merges"] == 0
+    assert a not in out["origin"] and b in out["origin"]
+    assert np.array_equal(out["x"][list(out["origin"]).index(b)], x[b])
+    # without the wall point's pull the two would merge
+    far = x.copy()
+    far[a] = x[a] + [0.0, 3 * dx]
+    far[b] = far[a] + [0.0, 0.2 * dx]
+    cnt2, col2 = _lists(p, far)
+    out2 = oracle.manage(p, far, cl["kind"], cl["normal"], f, cnt2, col2, 0.25 * dx, 0)
+    assert out2["wall_removals"] == 0 and out2["merges"] == 1
