@@ -202,20 +202,23 @@ int bgk_set_params(bgk_ctx* ctx, int32_t c, const bgk_params* p);
 
 /* Point management of case c between steps (Sec. 3.5.2, adding and removing
  * points), one pass on the current positions:
- *  - interior points that are each other's nearest interior neighbour and closer
- *    than rmin (absolute distance) are replaced by one point at their midpoint;
- *  - an interior point in no such pair with fewer than min_nbrs neighbours gets a
+ *  - an interior point closer than rmin (absolute distance) to a wall point is
+ *    removed (the wall point stays on the boundary);
+ *  - remaining interior points that are each other's nearest remaining interior
+ *    neighbour and closer than rmin are replaced by one point at their midpoint;
+ *  - an interior point in neither case with fewer than min_nbrs neighbours gets a
  *    new interior point at x_i - (h/2) c/|c|, c the sum of its neighbour
  *    separations, when that position lies in [guard, 1 - guard]^dim (wrapped in a
- *    periodic box) and no point of N(i) + {i} is within rmin of it;
+ *    periodic box), outside the body's guard sphere and no point of N(i) + {i} is
+ *    within rmin of it;
  *  - f at a new position is the linear WLS reconstruction there from N(i) + {i};
  *    the stored moments of every point are recomputed from f.
  * Surviving points keep their order (a merged pair keeps the smaller index);
  * added points follow in the order of the points that made them, up to the
  * capacity n + spare_points (later additions are dropped).  Point indices change:
  * host arrays of per-point data must be re-read.  counts (host, int64[3])
- * receives the new point count, the points removed by merging and the points
- * added.  Synchronous. */
+ * receives the new point count, the points removed (merged away or next to a
+ * wall) and the points added.  Synchronous. */
 int bgk_manage(bgk_ctx* ctx, int32_t c, double rmin, int32_t min_nbrs, int64_t* counts, void* stream);
 
 /* Objective of the current state of case c, not in the paper: the x-momentum flux

@@ -3,9 +3,10 @@
 // The paper names two operations: two points that come too close are replaced by
 // one point at their midpoint, and points are added where the moving cloud opens
 // holes; f at a new point is updated by least squares.  Readings (thresholds are
-// not given): interior points i < j that are each other's nearest interior
-// neighbour and closer than rmin merge at the midpoint (the survivor keeps i's
-// slot); an interior point in no merge with fewer than min_nbrs neighbours gets a
+// not given): an interior point closer than rmin to a wall point is removed (the
+// wall point stays on the boundary); remaining interior points i < j that are each
+// other's nearest remaining interior neighbour and closer than rmin merge at the
+// midpoint (the survivor keeps i's slot); an interior point in no merge with fewer than min_nbrs neighbours gets a
 // new interior point at x_i - (h/2) c/|c|, c the sum of its neighbour separations,
 // if that lies in [guard, 1 - guard]^dim (wrapped when periodic), outside the body's
 // guard sphere (distance >= body_radius + guard from its centre) and no point of
@@ -15,8 +16,8 @@
 // fewer than dim + 1 points or a singular system).  Survivors keep their order;
 // the added points follow in the order of the points that made them.
 //
-// Kernels: k_pm_nearest and k_pm_roles (one thread per point, FP64 without fused
-// multiply-add, so positions match a plain C evaluation bit for bit), k_pm_scan
+// Kernels: k_pm_wallnear, k_pm_nearest and k_pm_roles (one thread per point, FP64
+// without fused multiply-add, so positions match a plain C evaluation bit for bit), k_pm_scan
 // (one block: new indices of survivors and added points), k_pm_geom (new
 // positions, kinds, normals), k_pm_rows (one CTA per point: copy or reconstruct
 // rows of f), k_pm_lists (interior and wall index lists, wall map).
@@ -29,16 +30,43 @@ namespace {
 
 constexpr int PM_ROLE_KEEP = 0, PM_ROLE_MERGE = 1, PM_ROLE_GONE = 2, PM_ROLE_ADD = 3;
 
-__global__ void k_pm_nearest(CaseView cv, double rmin2, int32_t* nn) {
+__device__ __forceinline__ double pm_dist2(const CaseView& cv, int i, int j) {
+  double d2 = 0.0;
+  for (int a = 0; a < cv.dim; ++a) {
+    const double d = sep_d(cv.x[(int64_t)i * cv.dim + a], cv.x[(int64_t)j * cv.dim + a], cv.periodic);
+    d2 = __dadd_rn(d2, __dmul_rn(d, d));
+  }
+  return d2;
+}
+
+// role[i] = GONE for an interior point closer than rmin to a wall point, KEEP otherwise.
+__global__ void k_pm_wallnear(CaseView cv, double rmin2, int32_t* role) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cv.n) return;
+  int r = PM_ROLE_KEEP;
+  if (cv.kind[i] == 0) {
+    for (int s = 0; s < cv.cnt[i]; ++s) {
+      const int j = cv.col[(int64_t)i * cv.cap + s];
+      if (cv.kind[j] != 0 && pm_dist2(cv, i, j) < rmin2) {
+        r = PM_ROLE_GONE;
+        break;
+      }
+    }
+  }
+  role[i] = r;
+}
+
+// Nearest remaining interior neighbour closer than rmin (-1: none, or i is removed).
+__global__ void k_pm_nearest(CaseView cv, double rmin2, const int32_t* role, int32_t* nn) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cv.n) return;
   int best_j = -1;
   double best = 0.0;
-  if (cv.kind[i] == 0) {
+  if (cv.kind[i] == 0 && role[i] != PM_ROLE_GONE) {
     const int dim = cv.dim;
     for (int s = 0; s < cv.cnt[i]; ++s) {
       const int j = cv.col[(int64_t)i * cv.cap + s];
-      if (cv.kind[j] != 0) continue;
+      if (cv.kind[j] != 0 || role[j] == PM_ROLE_GONE) continue;
       double d2 = 0.0;
       for (int a = 0; a < dim; ++a) {
         const double d = sep_d(cv.x[(int64_t)i * dim + a], cv.x[(int64_t)j * dim + a], cv.periodic);
@@ -61,9 +89,9 @@ __global__ void k_pm_roles(CaseView cv, const int32_t* nn, double rmin2, int min
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cv.n) return;
   const int dim = cv.dim, cap = cv.cap;
-  int r = PM_ROLE_KEEP;
+  int r = role[i];  // GONE: removed next to a wall
   const int j = nn[i];
-  if (j >= 0 && nn[j] == i) r = i < j ? PM_ROLE_MERGE : PM_ROLE_GONE;
+  if (r == PM_ROLE_KEEP && j >= 0 && nn[j] == i) r = i < j ? PM_ROLE_MERGE : PM_ROLE_GONE;
   const int m = cv.cnt[i];
   if (r == PM_ROLE_KEEP && cv.kind[i] == 0 && m < min_nbrs && m > 0) {
     const double* xi = cv.x + (int64_t)i * dim;
@@ -346,10 +374,11 @@ __global__ void k_pm_lists(CaseView cv, const int32_t* role, const int32_t* newi
 int launch_manage_plan(const CaseView& cv, double rmin, int min_nbrs, int32_t* nn, int32_t* role, double* ynew,
                        int32_t* newidx, int32_t* addidx, int32_t* totals, cudaStream_t s) {
   const int B = 256, g = (cv.n + B - 1) / B;
-  k_pm_nearest<<<g, B, 0, s>>>(cv, rmin * rmin, nn);
+  k_pm_wallnear<<<g, B, 0, s>>>(cv, rmin * rmin, role);
+  k_pm_nearest<<<g, B, 0, s>>>(cv, rmin * rmin, role, nn);
   k_pm_roles<<<g, B, 0, s>>>(cv, nn, rmin * rmin, min_nbrs, role, ynew);
   k_pm_scan<<<1, 1024, 0, s>>>(cv.n, role, newidx, addidx, totals);
-  return 3;
+  return 4;
 }
 
 int launch_manage_apply(const CaseView& cv, int64_t cap_n, const int32_t* nn, const int32_t* role,

@@ -148,3 +148,30 @@ def test_second_pass_after_first(g):
     fg = s.get_f(0, np.float64)
     assert np.abs(fg - r2["f"].reshape(fg.shape)).max() <= 1e-12 * np.abs(r2["f"]).max()
     s.close()
+
+
+def test_points_next_to_walls_are_removed_as_in_oracle(g):
+    p, cl, rmin, mn = _cloud()
+    x = cl["x"].copy()
+    dx = 1.0 / (p["n"] - 1)
+    moved = 0
+    for wx in (0.3, 0.5, 0.7):
+        w = int(np.argmin(np.sum((x - [wx, 0.0]) ** 2, axis=1)))
+        i = int(np.argmin(np.sum((x - [wx, dx]) ** 2, axis=1)))
+        if cl["kind"][w] != 0 and cl["kind"][i] == 0:
+            x[i] = x[w] + [0.02 * dx, 0.1 * dx]
+            moved += 1
+    cl = dict(cl, x=x)
+    p = dict(p, storage="f64", spare_points=64)
+    n = len(cl["kind"])
+    f = _f0(p, n)
+    ref = _oracle_manage(p, cl, f, rmin, mn, n + 64)
+    assert ref["wall_removals"] == moved == 3
+    s = g.Solver([p], [cl])
+    s.set_f(np.ascontiguousarray(f))
+    nn, removed, added = s.manage(rmin, mn)
+    assert (nn, removed, added) == (len(ref["x"]), ref["merges"] + ref["wall_removals"], ref["adds"])
+    assert np.array_equal(s.positions(), ref["x"])
+    fg = s.get_f(0, np.float64)
+    assert np.abs(fg - ref["f"].reshape(fg.shape)).max() <= 1e-12 * np.abs(ref["f"]).max()
+    s.close()
