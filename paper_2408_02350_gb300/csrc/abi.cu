@@ -65,6 +65,7 @@ struct CaseHost {
   // of the step that uses that set waits for
   cudaEvent_t ev_recon[2] = {nullptr, nullptr};
   int64_t chain = 0;
+  int chain_grid = 0;  // CTAs of the cooperative side-chain kernel (0: not yet sized)
   int64_t cap_n = 0;  // capacity of the per-point arrays (initial points + spare_points)
   // point management scratch (allocated on first use, cap_n entries)
   int32_t *pm_nn = nullptr, *pm_role = nullptr, *pm_newidx = nullptr, *pm_addidx = nullptr, *pm_totals = nullptr;
@@ -302,16 +303,26 @@ int move_and_prebuild(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
   cudaStream_t q = ctx->side;
   CK(ctx, cudaEventRecord(c.ev_fork, s));
   CK(ctx, cudaStreamWaitEvent(q, c.ev_fork, 0));
-  if ((st = timed_begin(ctx, K_MOVE, q, &e))) return st;
-  ctx->launches += launch_move(c.cv, q);
-  CKL(ctx);
-  if ((st = timed_end(ctx, e, q))) return st;
   CaseView nx = c.cv;
   nx.cnt = c.nx_cnt;
   nx.col = c.nx_col;
   nx.P = c.nx_P;
   nx.recon = c.nx_recon;
-  if ((st = build_lists_into(ctx, nx, q, 1))) return st;
+  if (chain_eligible(nx)) {
+    // motion, lists and interior stencils in one cooperative launch (timed as lists)
+    if ((st = timed_begin(ctx, K_NBR, q, &e))) return st;
+    const int k = launch_chain(nx, &c.chain_grid, q);
+    if (k < 0) return fail(ctx, BGK_E_CUDA, "cooperative launch of the side chain failed");
+    ctx->launches += k;
+    CKL(ctx);
+    if ((st = timed_end(ctx, e, q))) return st;
+  } else {
+    if ((st = timed_begin(ctx, K_MOVE, q, &e))) return st;
+    ctx->launches += launch_move(c.cv, q);
+    CKL(ctx);
+    if ((st = timed_end(ctx, e, q))) return st;
+    if ((st = build_lists_into(ctx, nx, q, 1))) return st;
+  }
   CK(ctx, cudaEventRecord(c.ev_join, q));
   if ((st = timed_begin(ctx, K_STENCIL, q, &e))) return st;
   ctx->launches += launch_stencils(nx, q, 2);

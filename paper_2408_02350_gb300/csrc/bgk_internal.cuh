@@ -14,13 +14,15 @@ enum : int32_t { ST_OVERFLOW = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_TIMEOUT 
 
 // Verlet-list state of an ALE case: the largest squared displacement of an interior
 // point since the candidate build (FP32 bits, rounded up), the rebuild decision for
-// the next list build (taken by the last CTA of the motion kernel; set by the host
-// whenever positions or lists are reset), and that kernel's CTA counter.
+// the next list build (taken by the last CTA of the motion kernel or by the
+// side-chain kernel; set by the host whenever positions or lists are reset), the CTA
+// counter of those kernels (zero between kernels) and the generation of the
+// side-chain kernel's grid barrier.
 struct SkinState {
   uint32_t disp2;
   int32_t rebuild;
   uint32_t blocks;
-  int32_t pad;
+  uint32_t gen;
 };
 
 // Rigid body (body_wall > 0): its current centre and the CTA counter of the motion
@@ -115,6 +117,11 @@ int launch_manage_apply(const CaseView& cv, int64_t cap_n, const int32_t* nn, co
                         int32_t* wall_idx, int32_t* wall_of, int64_t n_new, cudaStream_t s);
 // ALE with a skin: rebuild the candidate lists if a point moved too far, then filter them.
 int launch_neighbours_skin(const CaseView& cv, cudaStream_t s);
+// ALE with a skin, FP32/BF16 storage: motion, candidate rebuild when due, filter and
+// interior stencils of the list set in cv as one cooperative launch (grid size cached
+// in *grid_cache); returns 1, or -1 when the cooperative launch is unavailable.
+bool chain_eligible(const CaseView& cv);
+int launch_chain(const CaseView& cv, int* grid_cache, cudaStream_t s);
 // part 0: all points; 1: interior stencils (all points for FP64 storage); 2: wall
 // reconstruction weights (nothing for FP64 storage).
 int launch_stencils(const CaseView& cv, cudaStream_t s, int part = 0);

@@ -20,6 +20,7 @@
 // k_move: x += dt U^{n+1} at interior points (FP64, no fused multiply-add).
 #include "bgk_internal.cuh"
 #include "device_common.cuh"
+#include "motion.cuh"
 #include "transport_wp.cuh"
 
 namespace bgk {
@@ -711,69 +712,6 @@ int launch_init_tables(const CaseView& cv, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // point motion (Eqs. originalALE1, ALE1)
 // ---------------------------------------------------------------------------
-// Stores the new position y of point i; with skin lists also the FP32 split of y
-// (the prefilters read it; k_cell_assign sets it only when the cells are rebuilt),
-// and returns the squared displacement since the candidate build.
-__device__ __forceinline__ double store_position(const CaseView& cv, const int i, const double* y) {
-  double d2 = 0.0;
-  for (int a = 0; a < cv.dim; ++a) {
-    cv.x[(int64_t)i * cv.dim + a] = y[a];
-    if (cv.sk) {
-      const float hi = (float)y[a];
-      cv.xf[(int64_t)i * cv.dim + a] = hi;
-      cv.xlo[(int64_t)i * cv.dim + a] = (float)(y[a] - (double)hi);
-      const double d = __dadd_rn(y[a], -cv.xb[(int64_t)i * cv.dim + a]);
-      d2 = __dadd_rn(d2, __dmul_rn(d, d));
-    }
-  }
-  return d2;
-}
-
-// x_i += dt U_i^{n+1} for one interior point (FP64 without fused multiply-add),
-// clamped to [guard, 1 - guard] or wrapped in a periodic box.  With a body (cn =
-// its centre after this step, else null), a point that ends closer than body_rg to
-// cn is put back on that sphere along the ray from cn (at cn + body_rg e_x if it
-// sits on cn).  Every clamp is counted.
-__device__ __forceinline__ double move_point(const CaseView& cv, const int i, const double* cn) {
-  unsigned long long nclamp = 0;
-  double y[3];
-  for (int a = 0; a < cv.dim; ++a) {
-    double ya = __dadd_rn(cv.x[(int64_t)i * cv.dim + a], __dmul_rn(cv.dt, cv.mom[(int64_t)i * MOM_STRIDE + 1 + a]));
-    if (cv.periodic) {
-      if (ya >= 1.0) ya = __dadd_rn(ya, -1.0);
-      else if (ya < 0.0) ya = __dadd_rn(ya, 1.0);
-    } else if (ya < cv.guard) { ya = cv.guard; ++nclamp; }
-    else if (ya > 1.0 - cv.guard) { ya = 1.0 - cv.guard; ++nclamp; }
-    y[a] = ya;
-  }
-  if (cn) {
-    double d[3], r2 = 0.0;
-    for (int a = 0; a < cv.dim; ++a) {
-      d[a] = __dadd_rn(y[a], -cn[a]);
-      r2 = __dadd_rn(r2, __dmul_rn(d[a], d[a]));
-    }
-    const double rg = cv.body_rg;
-    if (r2 < __dmul_rn(rg, rg)) {
-      if (r2 > 0.0) {
-        const double sc = __ddiv_rn(rg, __dsqrt_rn(r2));
-        for (int a = 0; a < cv.dim; ++a) y[a] = __dadd_rn(cn[a], __dmul_rn(d[a], sc));
-      } else {
-        for (int a = 0; a < cv.dim; ++a) y[a] = __dadd_rn(cn[a], a == 0 ? rg : 0.0);
-      }
-      ++nclamp;
-    }
-  }
-  if (nclamp) atomicAdd(&cv.status->clamps, nclamp);
-  return store_position(cv, i, y);
-}
-
-// A boundary point of the body: x_b += dt body_u.
-__device__ __forceinline__ double move_body_point(const CaseView& cv, const int b) {
-  double y[3];
-  for (int a = 0; a < cv.dim; ++a) y[a] = __dadd_rn(cv.x[(int64_t)b * cv.dim + a], __dmul_rn(cv.dt, cv.body_u[a]));
-  return store_position(cv, b, y);
-}
-
 // After every CTA has read the body centre and merged its maximum squared
 // displacement (bits b) into disp2, the last one decides whether the next list
 // build rebuilds the candidates and advances the centre to cn.
@@ -803,16 +741,9 @@ __device__ __forceinline__ void move_merge(const CaseView& cv, uint32_t b, doubl
 __global__ void __launch_bounds__(256) k_move(CaseView cv, double thr2) {
   __shared__ uint32_t s_max[8];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double cn[3] = {0.0, 0.0, 0.0};
-  if (cv.body)
-    for (int a = 0; a < cv.dim; ++a) cn[a] = __dadd_rn(cv.body->c[a], __dmul_rn(cv.dt, cv.body_u[a]));
-  double d2 = 0.0;
-  if (t < cv.n_int) {
-    d2 = move_point(cv, cv.int_idx[t], cv.body ? cn : nullptr);
-  } else if (cv.body && t < cv.n_int + cv.n_wall) {
-    const int b = cv.wall_idx[t - cv.n_int];
-    if (cv.kind[b] == cv.body_wall) d2 = move_body_point(cv, b);
-  }
+  double cn[3];
+  body_centre_next(cv, cn);
+  const double d2 = move_thread(cv, t, cn);
   if (cv.sk || cv.body) {
     // CTA maximum of the displacement bits (non-negative floats order as integers)
     const uint32_t w = __reduce_max_sync(0xffffffffu, __float_as_uint(__double2float_ru(d2)));
