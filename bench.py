@@ -283,7 +283,8 @@ def body_managed(g, torch, stream, steps: int = 400, every: int = 100) -> dict:
 
 def extra_configs(g, torch, stream, workload: str) -> dict:
     """The ALE workload over its Kn sweep, the same cavity with a moving disc (plain and
-    with point management), and the plain FP64 41^2 x 16^2 cavity."""
+    with point management), the plain FP64 41^2 x 16^2 cavity and the 3D 41^3 x 16^3
+    cavity (FP32)."""
     out = {}
     p = bi.config(workload)
     if p.get("ale"):
@@ -292,6 +293,7 @@ def extra_configs(g, torch, stream, workload: str) -> dict:
     out["body2d_ale_n201_v32_f32"] = _rate(g, torch, stream, bi.config("body2d_ale_n201_v32_f32"), 200)
     out["body2d_ale_n201_v32_f32_managed"] = body_managed(g, torch, stream)
     out["cavity2d_n41_v16_f64"] = _rate(g, torch, stream, bi.config("cavity2d_n41_v16_f64"), 100)
+    out["cavity3d_n41_v16_f32"] = _rate(g, torch, stream, bi.config("cavity3d_n41_v16_f32"), 10)
     return out
 
 

@@ -380,4 +380,149 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
   finish_point<S, DIM, ROW, VPL>(cv, i, s_v, rsum, rcmp);
 }
 
+// Fixed points (the transport uses c = v): a velocity v and its mirror -v, which the
+// symmetric grid stores at NV - 1 - k, share their projections p_d = v.P_d, since
+//   m(v) = sum_d min(p_d, 0)  and  m(-v) = sum_d min(-p_d, 0) = m(v) - sum_d p_d.
+// A lane takes the 4 consecutive velocities k0..k0+3 of a grid row in the first half
+// (k0 < NV/2) and the mirror chunk NV-4-k0..NV-1-k0, whose element e holds -v_{3-e};
+// so m(-v) of the lane's pair (v_{2q}, v_{2q+1}) is the mirror chunk's pair 1 - q with
+// its halves swapped.  Each neighbour row then costs the projections once for 8
+// velocities.  Requires nv % 4 == 0 and NV % 8 == 0 (then NVp = NV).
+template <typename S, int DIM, bool KS>
+__device__ __forceinline__ void transport_point_mirror(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
+                                                       float* s_P, float* s_k) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  constexpr int DD = DIM * DIM;
+  constexpr int VPL = 4, NP = 2;
+  const int lane = threadIdx.x & 31;
+  const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const float inv_nv = 1.0f / (float)nv;
+  const int m = cv.cnt[i];
+  for (int q = lane; q < nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  {
+    const int32_t* col = cv.col + (int64_t)i * cap;
+    const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
+    for (int q = lane; q < m; q += 32) s_col[q] = col[q];
+    for (int q = lane; q < m * DD; q += 32) s_P[q] = P[q];
+  }
+  __syncwarp();
+
+  const int nchunk = NV / (2 * VPL);
+  const int nslice = (nchunk + 31) >> 5;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  const S* fbase = reinterpret_cast<const S*>(cv.f_in);
+  const float two_dt = (float)(2.0 * cv.dt);
+  const float2 neg1 = f2(-1.0f, -1.0f);
+
+  float rsum[DIM + 2], rcmp[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) { rsum[q] = 0.0f; rcmp[q] = 0.0f; }
+  if (KS) {
+#pragma unroll
+    for (int q = 0; q < 2 * (DIM + 2); ++q) s_k[q * 32 + lane] = 0.0f;
+  }
+
+  for (int sl = 0; sl < nslice; ++sl) {
+    const int chunk = sl * 32 + lane;
+    if (chunk >= nchunk) break;
+    const int k0 = VPL * chunk, km = NV - VPL - k0;
+    float acc[NC][VPL], sk[VPL], accm[NC][VPL], skm[VPL];
+    {
+      float vel[VPL][DIM];
+      bool kin[VPL];
+      chunk_velocities<DIM, VPL, true>(k0, nv, NV, inv_nv, s_v, vel, kin);
+      float2 cx[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) cx[q] = f2(vel[2 * q][0], vel[2 * q + 1][0]);
+      float crest[DIM - 1];
+#pragma unroll
+      for (int a = 1; a < DIM; ++a) crest[a - 1] = vel[0][a];
+      float2 skp[NP], ap[NC][NP], skq[NP], aq[NC][NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        skp[q] = f2(0.0f, 0.0f);
+        skq[q] = f2(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { ap[c][q] = f2(0.0f, 0.0f); aq[c][q] = f2(0.0f, 0.0f); }
+      }
+      const S* fj0 = fbase + k0;
+      const S* fm0 = fbase + km;
+#pragma unroll 2
+      for (int s = 0; s < m; ++s) {
+        const int j = s_col[s];
+        float P[DD];
+#pragma unroll
+        for (int q = 0; q < DD; ++q) P[q] = s_P[s * DD + q];
+        const int64_t o = (int64_t)j * rowlen;
+        float fv[NC][VPL], fw[NC][VPL];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          ldv_ro<S, VPL>(fj0 + o + (int64_t)c * NVp, fv[c]);
+          ldv_ro<S, VPL>(fm0 + o + (int64_t)c * NVp, fw[c]);
+        }
+        float2 mk[NP], ps[NP];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          float b = crest[0] * P[d * DIM + 1];
+#pragma unroll
+          for (int a = 2; a < DIM; ++a) b = fmaf(crest[a - 1], P[d * DIM + a], b);
+          const float2 px = f2(P[d * DIM], P[d * DIM]), bb = f2(b, b);
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const float2 p = __ffma2_rn(cx[q], px, bb);
+            mk[q] = d == 0 ? min0(p) : __fadd2_rn(mk[q], min0(p));
+            ps[q] = d == 0 ? p : __fadd2_rn(ps[q], p);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          skp[q] = __fadd2_rn(skp[q], mk[q]);
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            ap[c][q] = __ffma2_rn(mk[q], f2(fv[c][2 * q], fv[c][2 * q + 1]), ap[c][q]);
+          const float2 mm = __ffma2_rn(ps[q], neg1, mk[q]);  // m of (-v_{2q}, -v_{2q+1})
+          const float2 mr = f2(mm.y, mm.x);                  // as mirror pair 1 - q
+          const int r = NP - 1 - q;
+          skq[r] = __fadd2_rn(skq[r], mr);
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            aq[c][r] = __ffma2_rn(mr, f2(fw[c][2 * r], fw[c][2 * r + 1]), aq[c][r]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        sk[2 * q] = skp[q].x; sk[2 * q + 1] = skp[q].y;
+        skm[2 * q] = skq[q].x; skm[2 * q + 1] = skq[q].y;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          acc[c][2 * q] = ap[c][q].x; acc[c][2 * q + 1] = ap[c][q].y;
+          accm[c][2 * q] = aq[c][q].x; accm[c][2 * q + 1] = aq[c][q].y;
+        }
+      }
+    }
+    float vel[VPL][DIM], velm[VPL][DIM];
+    bool kin[VPL];
+    chunk_velocities<DIM, VPL, true>(k0, nv, NV, inv_nv, s_v, vel, kin);
+#pragma unroll
+    for (int e = 0; e < VPL; ++e)
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) velm[e][a] = -vel[VPL - 1 - e][a];
+    if (KS) {
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+    }
+    slice_out<S, DIM, NC, VPL>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
+    slice_out<S, DIM, NC, VPL>(cv, i, km, velm, kin, accm, skm, two_dt, rsum, rcmp);
+    if (KS) {
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
+    }
+  }
+  if (KS) {
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+  }
+  finish_point<S, DIM, true, VPL>(cv, i, s_v, rsum, rcmp);
+}
+
 }  // namespace bgk
