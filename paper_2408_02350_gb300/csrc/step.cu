@@ -360,8 +360,13 @@ __global__ void __launch_bounds__(256, BGK_MIRROR_MIN_BLOCKS) k_transport_mirror
 // Many cases in one persistent launch: items[k] = (case, interior slot), tiles of W
 // consecutive items per CTA, tiles taken in grid-stride order.  Every warp reads
 // its case's descriptor; the ROW4 / ALE variants are chosen per warp.
+// 3 CTAs per SM (80 registers, some spills) beats 2 (114 registers, no spills) on the
+// 64-cavity sweep: 4.54 against 4.99 ms per step.
+#ifndef BGK_BATCH_MIN_BLOCKS
+#define BGK_BATCH_MIN_BLOCKS 3
+#endif
 template <typename S, int DIM>
-__global__ void __launch_bounds__(256, 3) k_transport_batch(const CaseView* __restrict__ cases, const int2* __restrict__ items,
+__global__ void __launch_bounds__(256, BGK_BATCH_MIN_BLOCKS) k_transport_batch(const CaseView* __restrict__ cases, const int2* __restrict__ items,
                                                              int n_items, int capmax) {
   constexpr int DD = DIM * DIM;
   extern __shared__ __align__(16) unsigned char smem[];
