@@ -55,7 +55,7 @@ class Params(C.Structure):
         ("lid_wall", C.c_int32), ("max_nbrs", C.c_int32), ("pad_", C.c_int32),
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
         ("guard", C.c_double), ("lid_u", C.c_double * 3),
-        ("body_wall", C.c_int32), ("pad2_", C.c_int32), ("body_u", C.c_double * 3),
+        ("body_wall", C.c_int32), ("wls_order", C.c_int32), ("body_u", C.c_double * 3),
         ("body_c", C.c_double * 3), ("body_r", C.c_double),
     ]
 
@@ -78,6 +78,7 @@ def params(p: dict) -> Params:
         q.body_u[a] = float(bu[a])
         q.body_c[a] = float(bc[a])
     q.body_r = float(p.get("body_radius", 0.0))
+    q.wls_order = int(p.get("wls_order", 1))
     return q
 
 

@@ -64,7 +64,9 @@ typedef struct {
    * current centre of the body (advanced with the points by or_move and or_run);
    * interior points are kept at distance >= body_r + guard from it. */
   int32_t body_wall;
-  int32_t pad2_;
+  /* order of the Taylor expansion behind the interior derivative stencils (Sec. 3.4.1):
+   * 0 or 1 linear (the paper's scheme), 2 quadratic (its higher-order variant) */
+  int32_t wls_order;
   double body_u[3];
   double body_c[3];
   double body_r;
@@ -311,10 +313,10 @@ int64_t or_neighbours_cells(int32_t dim, int64_t n, const double* x, double h, i
 
 /* ---- weighted least squares (Sec. 3.4.1) ---- */
 
-/* Inverse of a small symmetric matrix by Gauss-Jordan elimination with partial
- * pivoting.  Returns 0, or OR_E_SINGULAR when a pivot is not above tol * max|A|. */
+/* Inverse of a small symmetric matrix (m <= 9) by Gauss-Jordan elimination with
+ * partial pivoting.  Returns 0, or OR_E_SINGULAR when a pivot is not above tol * max|A|. */
 static int gj_inverse(int m, const double* A, double* Ainv) {
-  double a[4][8];
+  double a[9][18];
   double amax = 0.0;
   for (int r = 0; r < m; ++r)
     for (int c = 0; c < m; ++c) {
@@ -363,10 +365,24 @@ void or_frame(int32_t dim, const double* dr, double* frame /* [dim][dim], rows n
   }
 }
 
+/* Basis of the second-order Taylor fit at x_i for neighbour x_j: (dr, then the
+ * products dr_a dr_b for a <= b, halved on the diagonal), dim + dim (dim + 1) / 2 entries. */
+static void quad_basis(int dim, const double* xi, const double* xj, int periodic, double* b) {
+  double dr[3];
+  for (int a = 0; a < dim; ++a) dr[a] = sep(xi[a], xj[a], periodic);
+  int k = 0;
+  for (int a = 0; a < dim; ++a) b[k++] = dr[a];
+  for (int a = 0; a < dim; ++a)
+    for (int c = a; c < dim; ++c) b[k++] = a == c ? 0.5 * dr[a] * dr[a] : dr[a] * dr[c];
+}
+
 /* Stencils of every point.
  * Interior i: S = (M^T W M)^-1 (Eq. solution), gradient coefficients
  *   coef_j = w_j S dr_j, i.e. (alpha_ij, beta_ij, gamma_ij) of Eqs. (x_derivative)-(z_derivative);
  *   frame_j (rows n, t, b) and the projected coefficients abar_j = frame_j coef_j.
+ * With wls_order = 2 the interior fit also carries the second derivatives (the
+ * higher-order Taylor expansion of Sec. 3.4.1) and coef_j are the gradient rows of its
+ * solution; frames and projected coefficients follow as above.
  * Wall b: linear WLS reconstruction over interior neighbours, p_j = (1, dr_j):
  *   recon_j = e_0^T (sum_k w_k p_k p_k^T)^-1 w_j p_j, so that f_b = sum_j recon_j f_j;
  *   with fewer than dim+1 interior neighbours (3D corners) the constant fit
@@ -383,7 +399,42 @@ int or_stencils(const or_params* p, int64_t n, const double* x, const int32_t* k
   memset(recon, 0, sizeof(double) * n * cap);
   for (int64_t i = 0; i < n; ++i) {
     const double* xi = x + i * dim;
-    if (kind[i] == 0) {
+    if (kind[i] == 0 && p->wls_order == 2) {
+      /* second-order Taylor expansion f_j - f_i = grad f . dr + 1/2 dr^T H dr: unknowns
+       * q = (grad f, the dim (dim + 1) / 2 entries of H), basis b_j = (dr, dr_a dr_b /
+       * (1 + [a == b])), coef_j = the gradient rows of (sum_k w_k b_k b_k^T)^-1 w_j b_j */
+      const int mq = dim + dim * (dim + 1) / 2;
+      double A[81] = {0}, S[81];
+      for (int s = 0; s < cnt[i]; ++s) {
+        const double* xj = x + (int64_t)col[i * cap + s] * dim;
+        double b[9];
+        quad_basis(dim, xi, xj, p->periodic, b);
+        double w = weight(p, dist2(dim, xi, xj, p->periodic));
+        for (int a = 0; a < mq; ++a)
+          for (int c = 0; c < mq; ++c) A[a * mq + c] += w * b[a] * b[c];
+      }
+      if (cnt[i] < mq || gj_inverse(mq, A, S) != OR_OK) { status = OR_E_SINGULAR; continue; }
+      for (int s = 0; s < cnt[i]; ++s) {
+        int64_t slot = i * cap + s;
+        const double* xj = x + (int64_t)col[slot] * dim;
+        double dr[3], fr[9], b[9];
+        for (int a = 0; a < dim; ++a) dr[a] = sep(xi[a], xj[a], p->periodic);
+        quad_basis(dim, xi, xj, p->periodic, b);
+        double w = weight(p, dist2(dim, xi, xj, p->periodic));
+        for (int a = 0; a < dim; ++a) {
+          double acc = 0.0;
+          for (int c = 0; c < mq; ++c) acc += S[a * mq + c] * b[c];
+          coef[slot * dim + a] = w * acc;
+        }
+        or_frame(dim, dr, fr);
+        for (int d = 0; d < dim; ++d) {
+          double acc = 0.0;
+          for (int a = 0; a < dim; ++a) acc += fr[d * dim + a] * coef[slot * dim + a];
+          abar[slot * dim + d] = acc;
+        }
+        for (int q = 0; q < dim * dim; ++q) frame[slot * dim * dim + q] = fr[q];
+      }
+    } else if (kind[i] == 0) {
       double A[9] = {0}, S[9];
       for (int s = 0; s < cnt[i]; ++s) {
         const double* xj = x + (int64_t)col[i * cap + s] * dim;

@@ -223,3 +223,25 @@ def test_managed_moving_body_run_matches_oracle(g):
     assert _rel(rho, sim.rho) < 1e-9 and _rel(T, sim.T) < 1e-9 and _rel(u, sim.U) < 1e-9
     assert np.array_equal(s.body_centre(), sim.body_c)
     s.close()
+
+
+def test_moving_ball_3d_matches_oracle(g):
+    # a ball of boundary points on a Fibonacci sphere in a 3D cavity, FP64
+    p = bi.config("cavity3d_n41_v16_f32", n=11, nv=6, vmax=4.0, storage="f64", ale=1, skin=0.3)
+    p.update(body_wall=8, body_u=[0.3, -0.2, 0.1], body_radius=0.25, body_centre=[0.5, 0.48, 0.52])
+    cl = bi.cloud_for(p)
+    assert (cl["kind"] == 8).sum() > 20
+    s = g.Solver([p], [cl])
+    s.set_maxwellian()
+    s.step(5)
+    s.sync()
+    sim = oracle.Simulation(p, cl)
+    sim.run(5)
+    body = cl["kind"] == 8
+    x = s.positions()
+    assert np.array_equal(x[body], sim.x[body]) and np.array_equal(s.body_centre(), sim.body_c)
+    assert np.abs(x - sim.x).max() < 1e-13
+    rho, u, T = s.moments()
+    assert _rel(rho, sim.rho) < 1e-10 and _rel(T, sim.T) < 1e-10 and _rel(u, sim.U) < 1e-10
+    assert s.stats()["clamps"] == sim.clamps
+    s.close()

@@ -166,3 +166,50 @@ def test_unjittered_lattice_has_no_tangential_coefficient():
     far = np.where(np.all((idx >= 3) & (idx <= 5), axis=1))[0]
     for i in far:
         assert np.abs(st["abar"][i, : cnt[i], 1:]).max() < 1e-10 * st["abar"][i, : cnt[i], 0].max()
+
+
+def _quad_case(dim, n, order, seed=11):
+    name = "cavity2d_n41_v16_f64" if dim == 2 else "cavity3d_n41_v16_f32"
+    p = bi.config(name, n=n, nv=4, wls_order=order)
+    c = bi.cavity(dim, n, seed, 0.1)
+    cnt, col = oracle.neighbours(c["x"], p["h"], False, p["max_nbrs"])
+    st = oracle.stencils(p, c["x"], c["kind"], cnt, col)
+    return p, c, cnt, col, st
+
+
+@pytest.mark.parametrize("dim,n", [(2, 15), (3, 7)])
+def test_quadratic_fit_gradient_is_exact_on_quadratics(dim, n):
+    # Sec. 3.4.1: the higher-order Taylor expansion.  For q = a + b.x + x^T H x / 2 the
+    # second-order fit's gradient rows give grad q(x_i) = b + H x_i exactly; the linear
+    # fit's carry an O(h) error, which the test must see.
+    rng = np.random.default_rng(3)
+    b = rng.uniform(-1, 1, dim)
+    H = rng.uniform(-2, 2, (dim, dim))
+    H = H + H.T
+    _, c, cnt, col, st2 = _quad_case(dim, n, 2)
+    _, _, _, _, st1 = _quad_case(dim, n, 1)
+    q = 0.3 + c["x"] @ b + 0.5 * np.einsum("ni,ij,nj->n", c["x"], H, c["x"])
+    err1 = 0.0
+    for i in np.where(c["kind"] == 0)[0]:
+        k = cnt[i]
+        exact = b + H @ c["x"][i]
+        dq = q[col[i, :k]] - q[i]
+        g2 = (st2["coef"][i, :k] * dq[:, None]).sum(0)
+        assert np.abs(g2 - exact).max() < 1e-10 * max(1.0, np.abs(exact).max())
+        # linear functions stay exact too: sum_j coef_j dr_j^T = I
+        assert np.allclose(st2["coef"][i, :k].T @ _dr(c, i, col, cnt), np.eye(dim), atol=1e-11)
+        g1 = (st1["coef"][i, :k] * dq[:, None]).sum(0)
+        err1 = max(err1, np.abs(g1 - exact).max())
+    assert err1 > 1e-4
+
+
+@pytest.mark.parametrize("dim,n", [(2, 15), (3, 7)])
+def test_quadratic_fit_projected_coefficients(dim, n):
+    # the same frame construction as the linear fit: abar_d = e_d . coef_j and
+    # sum_d abar_d e_d = coef_j
+    _, c, cnt, col, st = _quad_case(dim, n, 2)
+    for i in np.where(c["kind"] == 0)[0][:40]:
+        for s in range(cnt[i]):
+            fr = st["frame"][i, s]
+            assert np.allclose(fr @ st["coef"][i, s], st["abar"][i, s], atol=1e-12)
+            assert np.allclose(fr.T @ st["abar"][i, s], st["coef"][i, s], atol=1e-12)
