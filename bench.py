@@ -282,15 +282,18 @@ def body_managed(g, torch, stream, steps: int = 400, every: int = 100) -> dict:
 
 
 def extra_configs(g, torch, stream, workload: str) -> dict:
-    """The ALE workload over its Kn sweep, the same cavity with a moving disc (plain and
-    with point management), the plain FP64 41^2 x 16^2 cavity and the 3D 41^3 x 16^3
-    cavity (FP32)."""
+    """The ALE workload over its Kn sweep and with the second-order WLS stencils, the same
+    cavity with a moving disc (plain and with point management), the plain FP64 41^2 x
+    16^2 cavity and the 3D 41^3 x 16^3 cavity (FP32)."""
     out = {}
     p = bi.config(workload)
     if p.get("ale"):
         out["kn_sweep"] = {str(kn): _rate(g, torch, stream, bi.config(workload, kn=kn), 200)
                            for kn in bi.KN_SWEEP_ALE}
     out["body2d_ale_n201_v32_f32"] = _rate(g, torch, stream, bi.config("body2d_ale_n201_v32_f32"), 200)
+    if p.get("ale"):
+        # the same ALE workload with the second-order (quadratic) WLS stencils
+        out[workload + "_quadratic_wls"] = _rate(g, torch, stream, bi.config(workload, wls_order=2), 50)
     out["body2d_ale_n201_v32_f32_managed"] = body_managed(g, torch, stream)
     out["cavity2d_n41_v16_f64"] = _rate(g, torch, stream, bi.config("cavity2d_n41_v16_f64"), 100)
     out["cavity3d_n41_v16_f32"] = _rate(g, torch, stream, bi.config("cavity3d_n41_v16_f32"), 10)

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 4
+#define BGK_ABI_VERSION 5
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -95,9 +95,14 @@ typedef struct bgk_params {
    * are put back on that sphere along the ray from the centre (counted as clamps),
    * and bgk_manage adds no point inside it.  body_wall, body_centre and
    * body_radius are fixed at bgk_init; body_u may change through bgk_set_params
-   * and must be zero unless ale = 1. */
+   * and must be zero unless ale = 1.  (wls_order, between body_wall and body_u, is
+   * described at its field.) */
   int32_t body_wall;
-  int32_t pad3_;
+  int32_t wls_order;     /* interior derivative stencils from the linear (0 or 1: the paper's
+                            scheme) or the second-order (2) Taylor expansion of Sec. 3.4.1;
+                            the second-order fit needs dim + dim (dim + 1) / 2 neighbours per
+                            point and is solved in FP64 for every storage type.  Fixed at
+                            bgk_init. */
   double body_u[3];      /* body velocity */
   double body_centre[3]; /* centre of the body at bgk_init */
   double body_radius;    /* radius of the body's guard sphere (without guard) */

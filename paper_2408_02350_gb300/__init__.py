@@ -42,7 +42,7 @@ class bgk_params(C.Structure):
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
         ("guard", C.c_double), ("lid_u", C.c_double * 3), ("skin", C.c_double),
         ("spare_points", C.c_int32), ("pad2_", C.c_int32),
-        ("body_wall", C.c_int32), ("pad3_", C.c_int32), ("body_u", C.c_double * 3),
+        ("body_wall", C.c_int32), ("wls_order", C.c_int32), ("body_u", C.c_double * 3),
         ("body_centre", C.c_double * 3), ("body_radius", C.c_double),
     ]
 
@@ -322,6 +322,7 @@ def params_from(p: dict) -> bgk_params:
         q.body_u[a] = float(bu[a])
         q.body_centre[a] = float(bc[a])
     q.body_radius = float(p.get("body_radius", 0.0))
+    q.wls_order = int(p.get("wls_order", 1))
     return q
 
 

@@ -179,6 +179,7 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
   if (p.guard < 0 || p.guard >= 0.5) { *why = "guard must be in [0, 0.5)"; return 0; }
   if (!(p.skin >= 0 && p.skin <= 1)) { *why = "skin must be in [0, 1]"; return 0; }
   if (p.spare_points < 0 || n + p.spare_points > (int64_t)1 << 30) { *why = "spare_points out of range"; return 0; }
+  if (p.wls_order < 0 || p.wls_order > 2) { *why = "wls_order must be 0, 1 or 2"; return 0; }
   if (p.body_wall < 0) { *why = "body_wall must be >= 0"; return 0; }
   if (p.body_wall > 0) {
     if (p.body_wall == p.lid_wall) { *why = "body_wall must differ from lid_wall"; return 0; }
@@ -511,6 +512,7 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.body_wall = q.body_wall;
     for (int a = 0; a < 3; ++a) v.body_u[a] = q.body_u[a];
     v.body_rg = q.body_radius + q.guard;
+    v.wls_order = q.wls_order;
     // cells of side >= the search radius (h, or h (1 + skin) for the candidate lists)
     v.nc = (int)std::floor(1.0 / (q.h * (1.0 + q.skin) * (1.0 + 1e-9)));
     if (v.nc < 1) v.nc = 1;
@@ -963,7 +965,8 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   if (!check_params(*p, c.cv.n, &why)) return fail(ctx, BGK_E_INVAL, "bgk_set_params: %s", why);
   if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
       p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin ||
-      p->spare_points != o.spare_points || p->body_wall != o.body_wall || p->body_radius != o.body_radius ||
+      p->spare_points != o.spare_points || p->wls_order != o.wls_order || p->body_wall != o.body_wall ||
+      p->body_radius != o.body_radius ||
       p->body_centre[0] != o.body_centre[0] || p->body_centre[1] != o.body_centre[1] ||
       p->body_centre[2] != o.body_centre[2])
     return fail(ctx, BGK_E_INVAL,

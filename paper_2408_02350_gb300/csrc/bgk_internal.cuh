@@ -97,7 +97,7 @@ struct CaseView {
 
   // rigid body (body_wall = 0: none)
   int32_t body_wall;
-  int32_t pad_body;
+  int32_t wls_order;  // 2: second-order Taylor fit for the interior stencils, else linear
   double body_u[3];
   double body_rg;       // guard radius body_radius + guard
   BodyState* body;

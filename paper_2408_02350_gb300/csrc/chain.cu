@@ -133,7 +133,7 @@ void bounds(int dim, double r, float* lo, float* hi) {
 
 }  // namespace
 
-bool chain_eligible(const CaseView& cv) { return cv.ale && cv.sk && cv.storage != 0; }
+bool chain_eligible(const CaseView& cv) { return cv.ale && cv.sk && cv.storage != 0 && cv.wls_order != 2; }
 
 int launch_chain(const CaseView& cv, int* grid_cache, cudaStream_t s) {
   const size_t smem = sizeof(int32_t) * (size_t)cv.ccap * CHAIN_WARPS;

@@ -159,6 +159,97 @@ __device__ bool solve_e0(double (&B)[M][M], double (&z)[M]) {
   return true;
 }
 
+// Interior stencil of the second-order Taylor fit (Sec. 3.4.1, higher-order
+// approximation), FP64, one thread per point: basis b_j = (dr, dr_a dr_b for a <= b,
+// halved on the diagonal), B = sum_j w_j b_j b_j^T (MQ x MQ, MQ = dim + dim (dim + 1) / 2),
+// G = the first dim columns of B^-1 by Gauss-Jordan elimination with partial pivoting
+// on [B | e_0 .. e_{dim-1}] (B is symmetric, so they are its gradient rows), coef_j =
+// w_j G^T b_j; frames and projected coefficients as for the linear fit.
+template <int DIM>
+__device__ __forceinline__ void quad_basis_d(const double* xi, const double* xj, int periodic, double* b, double* dr) {
+  for (int a = 0; a < DIM; ++a) dr[a] = sep_d(xi[a], xj[a], periodic);
+  int k = 0;
+  for (int a = 0; a < DIM; ++a) b[k++] = dr[a];
+  for (int a = 0; a < DIM; ++a)
+    for (int c = a; c < DIM; ++c) b[k++] = a == c ? 0.5 * dr[a] * dr[a] : dr[a] * dr[c];
+}
+
+template <typename C, int DIM>
+__device__ void quad_stencil_point(const CaseView& cv, const int i, const double* xi, const int32_t* row,
+                                   const int m, C* P) {
+  constexpr int MQ = DIM + DIM * (DIM + 1) / 2;
+  const double nah2 = -cv.alpha, hh = cv.h * cv.h;
+  double B[MQ][MQ + DIM];
+  for (int a = 0; a < MQ; ++a)
+    for (int c = 0; c < MQ + DIM; ++c) B[a][c] = 0.0;
+  for (int s = 0; s < m; ++s) {
+    double xj[DIM], b[MQ], dr[DIM];
+    for (int a = 0; a < DIM; ++a) xj[a] = cv.x[(int64_t)row[s] * DIM + a];
+    quad_basis_d<DIM>(xi, xj, cv.periodic, b, dr);
+    const double w = exp(nah2 * dist2_d<DIM>(xi, xj, cv.periodic) / hh);
+    for (int a = 0; a < MQ; ++a)
+      for (int c = 0; c < MQ; ++c) B[a][c] += w * b[a] * b[c];
+  }
+  double amax = 0.0;
+  for (int a = 0; a < MQ; ++a) {
+    for (int c = 0; c < MQ; ++c) amax = fmax(amax, fabs(B[a][c]));
+    for (int c = 0; c < DIM; ++c) B[a][MQ + c] = a == c ? 1.0 : 0.0;
+  }
+  bool ok = m >= MQ && amax > 0.0;
+  for (int c = 0; c < MQ && ok; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < MQ; ++r)
+      if (fabs(B[r][c]) > fabs(B[piv][c])) piv = r;
+    if (!(fabs(B[piv][c]) > 1e-12 * amax)) { ok = false; break; }
+    if (piv != c)
+      for (int k = 0; k < MQ + DIM; ++k) { const double t = B[c][k]; B[c][k] = B[piv][k]; B[piv][k] = t; }
+    const double d = B[c][c];
+    for (int k = 0; k < MQ + DIM; ++k) B[c][k] /= d;
+    for (int r = 0; r < MQ; ++r) {
+      if (r == c) continue;
+      const double f = B[r][c];
+      for (int k = 0; k < MQ + DIM; ++k) B[r][k] -= f * B[c][k];
+    }
+  }
+  if (!ok) {
+    set_status(cv.status, ST_SINGULAR);
+    for (int s = 0; s < m * DIM * DIM; ++s) P[s] = (C)0;
+    return;
+  }
+  for (int s = 0; s < m; ++s) {
+    double xj[DIM], b[MQ], dr[DIM];
+    for (int a = 0; a < DIM; ++a) xj[a] = cv.x[(int64_t)row[s] * DIM + a];
+    quad_basis_d<DIM>(xi, xj, cv.periodic, b, dr);
+    const double r2 = dist2_d<DIM>(xi, xj, cv.periodic);
+    const double w = exp(nah2 * r2 / hh);
+    double coef[DIM];
+    for (int a = 0; a < DIM; ++a) {
+      double acc = 0.0;
+      for (int c = 0; c < MQ; ++c) acc += B[c][MQ + a] * b[c];
+      coef[a] = w * acc;
+    }
+    const double r = sqrt(r2);
+    double E[DIM][DIM];  // rows n, t(, b)
+    if constexpr (DIM == 2) {
+      const double nx = dr[0] / r, ny = dr[1] / r;
+      E[0][0] = nx; E[0][1] = ny;
+      E[1][0] = -ny; E[1][1] = nx;
+    } else {
+      const double rxy = sqrt(dr[0] * dr[0] + dr[1] * dr[1]);
+      const double cphi = rxy > 0.0 ? dr[0] / rxy : 1.0, sphi = rxy > 0.0 ? dr[1] / rxy : 0.0;
+      const double cth = dr[2] / r, sth = rxy / r;
+      E[0][0] = dr[0] / r; E[0][1] = dr[1] / r; E[0][2] = dr[2] / r;
+      E[1][0] = cth * cphi; E[1][1] = cth * sphi; E[1][2] = -sth;
+      E[2][0] = -sphi; E[2][1] = cphi; E[2][2] = 0.0;
+    }
+    for (int d = 0; d < DIM; ++d) {
+      double ab = 0.0;
+      for (int a = 0; a < DIM; ++a) ab += E[d][a] * coef[a];
+      for (int a = 0; a < DIM; ++a) P[(s * DIM + d) * DIM + a] = (C)(ab * E[d][a]);
+    }
+  }
+}
+
 template <typename C, int DIM>
 __global__ void k_stencils(CaseView cv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -171,7 +262,9 @@ __global__ void k_stencils(CaseView cv) {
   const double nah2 = -cv.alpha, hh = cv.h * cv.h;
   C* P = (C*)cv.P + (int64_t)i * cap * DIM * DIM;
   C* R = (C*)cv.recon + (int64_t)i * cap;
-  if (cv.kind[i] == 0) {
+  if (cv.kind[i] == 0 && cv.wls_order == 2) {
+    quad_stencil_point<C, DIM>(cv, i, xi, row, m, P);
+  } else if (cv.kind[i] == 0) {
     double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int s = 0; s < m; ++s) {
       const int j = row[s];
@@ -403,10 +496,17 @@ __global__ void __launch_bounds__(256) k_recon_grp(CaseView cv) {
 int launch_stencils(const CaseView& cv, cudaStream_t s, int part) {
   const int B = 128;
   const bool f64 = cv.storage == 0;
-  if (f64) {
+  if (f64 || cv.wls_order == 2) {
+    // one FP64 thread per point for every point (the second-order fit: also for
+    // FP32/BF16 storage, the coefficients then rounded to FP32)
     if (part == 2) return 0;
-    if (cv.dim == 2) k_stencils<double, 2><<<grid_for(cv.n, B), B, 0, s>>>(cv);
-    else k_stencils<double, 3><<<grid_for(cv.n, B), B, 0, s>>>(cv);
+    if (f64) {
+      if (cv.dim == 2) k_stencils<double, 2><<<grid_for(cv.n, B), B, 0, s>>>(cv);
+      else k_stencils<double, 3><<<grid_for(cv.n, B), B, 0, s>>>(cv);
+    } else {
+      if (cv.dim == 2) k_stencils<float, 2><<<grid_for(cv.n, B), B, 0, s>>>(cv);
+      else k_stencils<float, 3><<<grid_for(cv.n, B), B, 0, s>>>(cv);
+    }
     return 1;
   }
   constexpr int LPP = 4;
