@@ -516,6 +516,14 @@ def main():
                 "hbm": {"achieved": hbm_achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                         "frac": hbm_achieved / peaks.get("hbm_gbs", 6800.0),
                         "bytes_per_update": bytes_per_update}}
+    # the FP32 FMA rate measured on this device by the project's microbenchmark
+    try:
+        pk = g.bgk_peak_fp32(stream)
+        roofline["peak_measured"] = {"fma_tflops_scalar": pk["fma_per_s"] / 1e12,
+                                     "fma_tflops_packed_pairs": pk["fma2_per_s"] / 1e12, "n_sm": pk["n_sm"],
+                                     "frac_of_scalar_fma": achieved / (pk["fma_per_s"] / 1e12)}
+    except g.BGKError as e:
+        roofline["peak_measured"] = {"error": str(e)}
     kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in per_kernel.items()}
 
     if rank == 0:

@@ -124,6 +124,14 @@ typedef struct bgk_stats {
 /* Library ABI version (BGK_ABI_VERSION). */
 int bgk_version(void);
 
+/* Measurement support, not part of the method: the FP32 fused-multiply-add rate of
+ * the current device (the ceiling of the ALU-bound transport), from a kernel in which
+ * every thread runs 8 independent FMA chains on 8 CTAs of 256 threads per SM, timed
+ * with CUDA events (best of three after a warm-up launch).  fma_per_s: scalar FMAs per
+ * second; fma2_per_s: FMAs per second with packed pairs; n_sm: the multiprocessor
+ * count.  Synchronous; a few ms. */
+int bgk_peak_fp32(double* fma_per_s, double* fma2_per_s, int32_t* n_sm, void* stream);
+
 /* Create a context for n_cases independent problems (Sec. 5; several cavities
  * of different sizes and parameters may share one context).  p[n_cases],
  * n_points[n_cases]; x, kind, normal are host arrays concatenated over the

@@ -60,6 +60,7 @@ _PL = C.POINTER(C.c_int64)
 
 _SIGS = {
     "bgk_version": (C.c_int, []),
+    "bgk_peak_fp32": (C.c_int, [_PD, _PD, _PI, _P]),
     "bgk_init": (C.c_int, [C.POINTER(bgk_params), C.c_int32, _PL, _PD, _PI, _PD, C.POINTER(_P)]),
     "bgk_set_maxwellian": (C.c_int, [_P, C.c_double, _PD, C.c_double, _P]),
     "bgk_set_f": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
@@ -144,6 +145,13 @@ def _on_device(a) -> int:
 
 def bgk_version() -> int:
     return lib().bgk_version()
+
+
+def bgk_peak_fp32(stream=None) -> dict:
+    """Measured FP32 FMA rates of the device: scalar and packed FMAs per second, SM count."""
+    a, b, n = C.c_double(0.0), C.c_double(0.0), C.c_int32(0)
+    _check(lib().bgk_peak_fp32(C.byref(a), C.byref(b), C.byref(n), _stream_ptr(stream)))
+    return {"fma_per_s": a.value, "fma2_per_s": b.value, "n_sm": n.value}
 
 
 def bgk_init(params: list, n_points, x, kind, normal) -> int:

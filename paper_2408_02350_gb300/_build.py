@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbgk.so")
-SOURCES = ["abi.cu", "nbr_stencil.cu", "step.cu", "chain.cu", "adjoint.cu", "manage.cu", "noalloc.cu"]
+SOURCES = ["abi.cu", "nbr_stencil.cu", "step.cu", "chain.cu", "adjoint.cu", "manage.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]
