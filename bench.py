@@ -521,7 +521,8 @@ def main():
         pk = g.bgk_peak_fp32(stream)
         roofline["peak_measured"] = {"fma_tflops_scalar": pk["fma_per_s"] / 1e12,
                                      "fma_tflops_packed_pairs": pk["fma2_per_s"] / 1e12, "n_sm": pk["n_sm"],
-                                     "frac_of_scalar_fma": achieved / (pk["fma_per_s"] / 1e12)}
+                                     "frac_of_scalar_fma": achieved / (pk["fma_per_s"] / 1e12),
+                                     "fp64_fma_tflops": g.bgk_peak_fp64(stream) / 1e12}
     except g.BGKError as e:
         roofline["peak_measured"] = {"error": str(e)}
     kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in per_kernel.items()}

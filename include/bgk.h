@@ -132,6 +132,10 @@ int bgk_version(void);
  * count.  Synchronous; a few ms. */
 int bgk_peak_fp32(double* fma_per_s, double* fma2_per_s, int32_t* n_sm, void* stream);
 
+/* The same for FP64: dfma_per_s = FP64 FMAs per second (the ceiling of the plain FP64
+ * path).  Synchronous. */
+int bgk_peak_fp64(double* dfma_per_s, void* stream);
+
 /* Create a context for n_cases independent problems (Sec. 5; several cavities
  * of different sizes and parameters may share one context).  p[n_cases],
  * n_points[n_cases]; x, kind, normal are host arrays concatenated over the

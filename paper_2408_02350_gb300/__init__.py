@@ -61,6 +61,7 @@ _PL = C.POINTER(C.c_int64)
 _SIGS = {
     "bgk_version": (C.c_int, []),
     "bgk_peak_fp32": (C.c_int, [_PD, _PD, _PI, _P]),
+    "bgk_peak_fp64": (C.c_int, [_PD, _P]),
     "bgk_init": (C.c_int, [C.POINTER(bgk_params), C.c_int32, _PL, _PD, _PI, _PD, C.POINTER(_P)]),
     "bgk_set_maxwellian": (C.c_int, [_P, C.c_double, _PD, C.c_double, _P]),
     "bgk_set_f": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
@@ -152,6 +153,13 @@ def bgk_peak_fp32(stream=None) -> dict:
     a, b, n = C.c_double(0.0), C.c_double(0.0), C.c_int32(0)
     _check(lib().bgk_peak_fp32(C.byref(a), C.byref(b), C.byref(n), _stream_ptr(stream)))
     return {"fma_per_s": a.value, "fma2_per_s": b.value, "n_sm": n.value}
+
+
+def bgk_peak_fp64(stream=None) -> float:
+    """Measured FP64 FMAs per second of the device."""
+    a = C.c_double(0.0)
+    _check(lib().bgk_peak_fp64(C.byref(a), _stream_ptr(stream)))
+    return a.value
 
 
 def bgk_init(params: list, n_points, x, kind, normal) -> int:
