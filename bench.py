@@ -167,7 +167,24 @@ def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
     upd = n * p["nv"] ** p["dim"] * nsteps
     return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d full time step(s) of the %d^%d x %d^%d cavity (%d points), FP64, one thread, %.1f s"
-                      % (nsteps, p["n"], p["dim"], p["nv"], p["dim"], n, dt)}
+                      % (nsteps, p["n"], p["dim"], p["nv"], p["dim"], n, dt),
+            "host": _host_cpu()}
+
+
+def _host_cpu() -> dict:
+    """The host's CPU model and logical core count (the oracle uses one of them)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                if key == "model name":
+                    break
+    except OSError:
+        pass
+    return {"model": model, "machine": platform.machine(), "logical_cores": os.cpu_count()}
 
 
 def adjoint_cost(g, torch, stream) -> dict:
