@@ -368,7 +368,8 @@ def run_reference(args, p: dict) -> None:
                        "ale": True, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step: one full FP64 time step of a %d^2-point cavity with the same "
-                                       "32^2 velocity grid, ALE, Kn %.2g (%d points)" % (sample_n, q["kn"], n)},
+                                       "32^2 velocity grid, ALE, Kn %.2g (%d points)" % (sample_n, q["kn"], n),
+                             "host": _host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
