@@ -124,6 +124,16 @@ typedef struct bgk_stats {
 /* Library ABI version (BGK_ABI_VERSION). */
 int bgk_version(void);
 
+/* Failure detection (not in the paper): the number of polls after which a bounded
+ * device wait gives up (the grid barriers of the fused ALE list-build kernel); 0
+ * restores the default of about one second.  A wait that gives up records
+ * BGK_E_TIMEOUT for the next bgk_sync and its CTAs leave the kernel, so no later phase
+ * runs on incomplete data; the lists of that step are then partly stale (every index
+ * still valid) until positions or lists are reset (bgk_set_state, bgk_manage,
+ * bgk_set_params).  A limit of 1 makes the waits give up at once, which tests that
+ * path without a hang. */
+int bgk_set_watchdog(bgk_ctx* ctx, int64_t max_polls);
+
 /* Measurement support, not part of the method: the FP32 fused-multiply-add rate of
  * the current device (the ceiling of the ALU-bound transport), from a kernel in which
  * every thread runs 8 independent FMA chains on 8 CTAs of 256 threads per SM, timed

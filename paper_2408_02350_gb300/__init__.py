@@ -77,6 +77,7 @@ _SIGS = {
     "bgk_get_state": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "bgk_set_state": (C.c_int, [_P, _P, C.c_size_t]),
     "bgk_set_timing": (C.c_int, [_P, C.c_int32]),
+    "bgk_set_watchdog": (C.c_int, [_P, C.c_int64]),
     "bgk_get_timing": (C.c_int, [_P, C.c_int32, _PD, _PL]),
     "bgk_get_stats": (C.c_int, [_P, C.POINTER(bgk_stats)]),
     "bgk_last_error": (C.c_char_p, [_P]),
@@ -226,6 +227,10 @@ def bgk_get_body(ctx, case: int, dim: int) -> np.ndarray:
     c = np.zeros(dim)
     _check(lib().bgk_get_body(ctx, case, c.ctypes.data_as(_PD)), ctx)
     return c
+
+
+def bgk_set_watchdog(ctx, max_polls: int) -> None:
+    _check(lib().bgk_set_watchdog(ctx, int(max_polls)), ctx)
 
 
 def bgk_sync(ctx, stream=None) -> None:

@@ -94,6 +94,7 @@ struct bgk_ctx {
   int64_t steps = 0, launches = 0;
   bool timing = false;
   int32_t timing_mask = 0;  // bit k: time kernel id k
+  int64_t watchdog = 0;     // polls a bounded device wait makes before it gives up (0: default)
   std::vector<EvPair> ev;
   size_t ev_used = 0;
   double t_ms[K_COUNT] = {0, 0, 0, 0, 0, 0, 0};
@@ -300,6 +301,9 @@ int move_and_prebuild(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
     if ((st = dalloc(ctx, &c.nx_col, n * cap))) return st;
     if ((st = dalloc_bytes(ctx, &c.nx_P, n * cap * dim * dim * c.c_bytes))) return st;
     if ((st = dalloc_bytes(ctx, &c.nx_recon, n * cap * c.c_bytes))) return st;
+    // empty rows until the first build fills them (a build cut short by a watchdog
+    // timeout leaves the rows it did not reach as they were)
+    CK(ctx, cudaMemset(c.nx_cnt, 0, sizeof(int32_t) * n));
   }
   cudaStream_t q = ctx->side;
   CK(ctx, cudaEventRecord(c.ev_fork, s));
@@ -312,7 +316,7 @@ int move_and_prebuild(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
   if (chain_eligible(nx)) {
     // motion, lists and interior stencils in one cooperative launch (timed as lists)
     if ((st = timed_begin(ctx, K_NBR, q, &e))) return st;
-    const int k = launch_chain(nx, &c.chain_grid, q);
+    const int k = launch_chain(nx, &c.chain_grid, ctx->watchdog, q);
     if (k < 0) return fail(ctx, BGK_E_CUDA, "cooperative launch of the side chain failed");
     ctx->launches += k;
     CKL(ctx);
@@ -1162,6 +1166,12 @@ int bgk_autotune(bgk_ctx* ctx, void* stream) {
   ctx->batch_warps = bw;
   ctx->batch_grid = bg;
   drop_graphs(ctx);
+  return BGK_OK;
+}
+
+int bgk_set_watchdog(bgk_ctx* ctx, int64_t max_polls) {
+  if (!ctx || max_polls < 0) return ctx ? fail(ctx, BGK_E_INVAL, "bgk_set_watchdog: max_polls < 0") : BGK_E_INVAL;
+  ctx->watchdog = max_polls;
   return BGK_OK;
 }
 

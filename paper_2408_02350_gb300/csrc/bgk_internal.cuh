@@ -119,9 +119,11 @@ int launch_manage_apply(const CaseView& cv, int64_t cap_n, const int32_t* nn, co
 int launch_neighbours_skin(const CaseView& cv, cudaStream_t s);
 // ALE with a skin, FP32/BF16 storage: motion, candidate rebuild when due, filter and
 // interior stencils of the list set in cv as one cooperative launch (grid size cached
-// in *grid_cache); returns 1, or -1 when the cooperative launch is unavailable.
+// in *grid_cache); returns 1, or -1 when the cooperative launch is unavailable.  A grid
+// barrier waits at most max_spins polls (0: about a second), then the kernel records
+// ST_TIMEOUT and its CTAs return.
 bool chain_eligible(const CaseView& cv);
-int launch_chain(const CaseView& cv, int* grid_cache, cudaStream_t s);
+int launch_chain(const CaseView& cv, int* grid_cache, long long max_spins, cudaStream_t s);
 // part 0: all points; 1: interior stencils (all points for FP64 storage); 2: wall
 // reconstruction weights (nothing for FP64 storage).
 int launch_stencils(const CaseView& cv, cudaStream_t s, int part = 0);

@@ -12,8 +12,10 @@
 // co-resident (cooperative launch, grid from the occupancy calculator) and every
 // thread reaches every barrier: the only branch around barriers is the rebuild
 // decision, which every thread takes the same way.  The grid barrier is a counter
-// and a generation in the case's skin state; its wait is bounded (about a second),
-// after which the kernel records ST_TIMEOUT and goes on, so it cannot hang.
+// and a generation in the case's skin state; its wait is bounded (about a second by
+// default), after which the CTA records ST_TIMEOUT and returns, so the kernel cannot
+// hang and no phase runs on the incomplete results of the one before it (a CTA that
+// passes a barrier does so only after every CTA has arrived there).
 #include <cmath>
 
 #include "bgk_internal.cuh"
@@ -28,10 +30,13 @@ namespace {
 constexpr long long BARRIER_SPIN_LIMIT = 20000000;  // x 64 ns sleep: about a second
 
 // Grid-wide barrier over the co-resident CTAs: the last CTA to arrive resets the
-// counter and advances the generation; the others wait (bounded) for the new one.
-__device__ __forceinline__ void grid_barrier(SkinState* sk, DevStatus* status) {
+// counter and advances the generation; the others wait, at most max_spins polls, for
+// the new one.  Returns false (in every thread of the CTA) when the wait gave up.
+__device__ __forceinline__ bool grid_barrier(SkinState* sk, DevStatus* status, long long max_spins) {
+  __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
+    int ok = 1;
     volatile uint32_t* vgen = &sk->gen;
     const uint32_t g = *vgen;
     __threadfence();
@@ -42,16 +47,19 @@ __device__ __forceinline__ void grid_barrier(SkinState* sk, DevStatus* status) {
     } else {
       long long it = 0;
       while (*vgen == g) {
-        if (++it > BARRIER_SPIN_LIMIT) {
+        if (++it > max_spins) {
           set_status(status, ST_TIMEOUT);
+          ok = 0;
           break;
         }
         __nanosleep(64);
       }
     }
     __threadfence();
+    s_ok = ok;
   }
   __syncthreads();
+  return s_ok != 0;
 }
 
 constexpr int CHAIN_THREADS = 256, CHAIN_WARPS = CHAIN_THREADS / 32;
@@ -59,7 +67,7 @@ constexpr int TILE = 8;  // points per warp in the filter + stencil phase (8 gro
 
 template <int DIM>
 __global__ void __launch_bounds__(CHAIN_THREADS) k_chain(CaseView cv, double thr2, float clo, float chi, float lo,
-                                                         float hi) {
+                                                         float hi, long long max_spins) {
   extern __shared__ int32_t s_buf[];  // [CHAIN_WARPS][ccap] candidate rows
   __shared__ uint32_t s_max[CHAIN_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -84,7 +92,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_chain(CaseView cv, double thr
     for (int k = 0; k < CHAIN_WARPS; ++k) b = max(b, s_max[k]);
     atomicMax(&sk->disp2, b);
   }
-  grid_barrier(sk, cv.status);
+  if (!grid_barrier(sk, cv.status, max_spins)) return;
   // every thread has read the old centre
   if (gtid == 0 && cv.body)
     for (int a = 0; a < cv.dim; ++a) cv.body->c[a] = cn[a];
@@ -93,7 +101,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_chain(CaseView cv, double thr
 
   if (rebuild) {
     for (int64_t i = gtid; i < cv.n; i += nthreads) cell_assign_point(cv, (int)i);
-    grid_barrier(sk, cv.status);
+    if (!grid_barrier(sk, cv.status, max_spins)) return;
     if (blockIdx.x == 0) {
       cell_scan_block(cv);
       // every thread has read disp2 and the rebuild flag
@@ -102,12 +110,12 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_chain(CaseView cv, double thr
         sk->rebuild = 0;
       }
     }
-    grid_barrier(sk, cv.status);
+    if (!grid_barrier(sk, cv.status, max_spins)) return;
     for (int64_t i = gtid; i < cv.n; i += nthreads) cell_fill_point(cv, (int)i);
-    grid_barrier(sk, cv.status);
+    if (!grid_barrier(sk, cv.status, max_spins)) return;
     for (int i = gwarp; i < cv.n; i += nwarps)
       nbr_warp_point<DIM, true>(cv, i, lane, s_buf + warp * cv.ccap, clo, chi);
-    grid_barrier(sk, cv.status);
+    if (!grid_barrier(sk, cv.status, max_spins)) return;
   }
 
   // exact lists of the new positions and the interior stencils, a tile of TILE
@@ -135,7 +143,7 @@ void bounds(int dim, double r, float* lo, float* hi) {
 
 bool chain_eligible(const CaseView& cv) { return cv.ale && cv.sk && cv.storage != 0 && cv.wls_order != 2; }
 
-int launch_chain(const CaseView& cv, int* grid_cache, cudaStream_t s) {
+int launch_chain(const CaseView& cv, int* grid_cache, long long max_spins, cudaStream_t s) {
   const size_t smem = sizeof(int32_t) * (size_t)cv.ccap * CHAIN_WARPS;
   const void* fn = cv.dim == 2 ? (const void*)k_chain<2> : (const void*)k_chain<3>;
   if (*grid_cache <= 0) {
@@ -156,7 +164,8 @@ int launch_chain(const CaseView& cv, int* grid_cache, cudaStream_t s) {
   bounds(cv.dim, cv.h * (1.0 + cv.skin), &clo, &chi);
   bounds(cv.dim, cv.h, &lo, &hi);
   CaseView v = cv;
-  void* args[] = {&v, &thr2, &clo, &chi, &lo, &hi};
+  long long spins = max_spins > 0 ? max_spins : BARRIER_SPIN_LIMIT;
+  void* args[] = {&v, &thr2, &clo, &chi, &lo, &hi, &spins};
   if (cudaLaunchCooperativeKernel(fn, dim3(*grid_cache), dim3(CHAIN_THREADS), args, smem, s) != cudaSuccess)
     return -1;
   return 1;
