@@ -325,14 +325,22 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
         for (int c = 0; c < NC; ++c) { acc[c][2 * q] = ap[c][q].x; acc[c][2 * q + 1] = ap[c][q].y; }
       }
     } else {
-      float cvel[VPL][DIM];
+      // velocity pairs in packed FP32x2 arithmetic; the lane's velocities need not share
+      // a grid row, so each pair carries its own (c_y, c_z) and the base of c.P_d is a
+      // packed product too
+      float2 cx[NP], cy[NP], cz[NP];
 #pragma unroll
-      for (int e = 0; e < VPL; ++e) {
-        sk[e] = 0.0f;
+      for (int q = 0; q < NP; ++q) {
+        cx[q] = f2(vel[2 * q][0] - U[0], vel[2 * q + 1][0] - U[0]);
+        cy[q] = f2(vel[2 * q][1] - U[1], vel[2 * q + 1][1] - U[1]);
+        cz[q] = DIM == 3 ? f2(vel[2 * q][DIM - 1] - U[DIM - 1], vel[2 * q + 1][DIM - 1] - U[DIM - 1]) : f2(0.0f, 0.0f);
+      }
+      float2 skp[NP], ap[NC][NP];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c][e] = 0.0f;
+      for (int q = 0; q < NP; ++q) {
+        skp[q] = f2(0.0f, 0.0f);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) cvel[e][a] = vel[e][a] - U[a];
+        for (int c = 0; c < NC; ++c) ap[c][q] = f2(0.0f, 0.0f);
       }
 #pragma unroll 2
       for (int s = 0; s < m; ++s) {
@@ -344,20 +352,30 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
         float fv[NC][VPL];
 #pragma unroll
         for (int c = 0; c < NC; ++c) ldv_ro<S, VPL>(fj + (int64_t)c * NVp, fv[c]);
+        float2 mk[NP];
 #pragma unroll
-        for (int e = 0; e < VPL; ++e) {
-          float mk = 0.0f;
+        for (int d = 0; d < DIM; ++d) {
+          const float2 px = f2(P[d * DIM], P[d * DIM]), py = f2(P[d * DIM + 1], P[d * DIM + 1]);
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            float p = cvel[e][0] * P[d * DIM];
-#pragma unroll
-            for (int a = 1; a < DIM; ++a) p = fmaf(cvel[e][a], P[d * DIM + a], p);
-            mk = d == 0 ? fminf(p, 0.0f) : mk + fminf(p, 0.0f);
+          for (int q = 0; q < NP; ++q) {
+            float2 bb = __fmul2_rn(cy[q], py);
+            if (DIM == 3) bb = __ffma2_rn(cz[q], f2(P[d * DIM + DIM - 1], P[d * DIM + DIM - 1]), bb);
+            const float2 mq = min0(__ffma2_rn(cx[q], px, bb));
+            mk[q] = d == 0 ? mq : __fadd2_rn(mk[q], mq);
           }
-          sk[e] += mk;
-#pragma unroll
-          for (int c = 0; c < NC; ++c) acc[c][e] = fmaf(mk, fv[c][e], acc[c][e]);
         }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          skp[q] = __fadd2_rn(skp[q], mk[q]);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ap[c][q] = __ffma2_rn(mk[q], f2(fv[c][2 * q], fv[c][2 * q + 1]), ap[c][q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        sk[2 * q] = skp[q].x; sk[2 * q + 1] = skp[q].y;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { acc[c][2 * q] = ap[c][q].x; acc[c][2 * q + 1] = ap[c][q].y; }
       }
     }
     }
