@@ -1,0 +1,91 @@
+"""Edge cases of the GPU path against the oracle: the smallest velocity grids (2 and 3 nodes
+per axis, a ragged last chunk of velocities), the largest the ABI admits (64 nodes per
+axis in 2D, NV = 8000 of 8192 in 3D), clouds whose point count leaves ragged CTA tiles, and a
+set of collinear interior points whose stencils are singular.
+"""
+import numpy as np
+import pytest
+
+import bgk_inputs as bi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_02350_gb300 import _build
+    _build.build()
+    import paper_2408_02350_gb300 as g
+    return g
+
+
+def _name(dim):
+    return "cavity2d_n41_v16_f64" if dim == 2 else "cavity3d_n41_v16_f32"
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _run_both(g, p, cl, steps):
+    sim = oracle.Simulation(p, cl)
+    sim.run(steps)
+    s = g.Solver([p], [cl])
+    s.set_maxwellian()
+    s.step(steps)
+    s.sync()
+    rho, u, T = s.moments()
+    f = s.get_f(0, np.float64)
+    s.close()
+    return sim, f, rho, u, T
+
+
+@pytest.mark.parametrize("dim,nv,ale,storage,tol", [
+    (2, 2, 0, "f64", 1e-10), (2, 3, 0, "f32", 1e-4), (2, 3, 1, "f64", 1e-10), (2, 2, 1, "f32", 1e-4),
+    (3, 2, 0, "f64", 1e-10), (3, 3, 0, "f32", 1e-4)])
+def test_smallest_velocity_grids(g, dim, nv, ale, storage, tol):
+    n = 13 if dim == 2 else 6
+    p = bi.config(_name(dim), n=n, nv=nv, vmax=2.0, storage=storage, ale=ale)
+    cl = bi.cloud_for(p)
+    sim, f, rho, u, T = _run_both(g, p, cl, 6)
+    assert _rel(rho, sim.rho) < tol and _rel(T, sim.T) < tol
+    assert np.abs(f - sim.f).max() < 10 * tol * np.abs(sim.f).max()
+
+
+@pytest.mark.parametrize("dim,n,nv", [(2, 9, 64), (3, 5, 20)])
+def test_largest_velocity_grids(g, dim, n, nv):
+    # the largest grids the ABI admits: nv = 64 per axis in 2D, NV = 8000 of 8192 in 3D
+    # (FP32: the project's 1e-4 bar on the moments)
+    p = bi.config(_name(dim), n=n, nv=nv, vmax=5.0, storage="f32")
+    cl = bi.cloud_for(p)
+    sim, f, rho, u, T = _run_both(g, p, cl, 2)
+    assert _rel(rho, sim.rho) < 1e-4 and _rel(T, sim.T) < 1e-4
+    assert np.abs(f - sim.f).max() < 1e-4 * np.abs(sim.f).max()
+
+
+@pytest.mark.parametrize("n", [7, 10, 23])
+def test_ragged_point_counts(g, n):
+    # 49, 100 and 529 points: interior counts that fill no whole tile of 8 warps
+    p = bi.config("cavity2d_ale_n201_v32_f32", n=n, nv=6, vmax=3.0, storage="f64")
+    cl = bi.cloud_for(p)
+    sim, f, rho, u, T = _run_both(g, p, cl, 5)
+    assert _rel(rho, sim.rho) < 1e-10 and _rel(T, sim.T) < 1e-10 and _rel(u, sim.U) < 1e-10
+
+
+def test_collinear_interior_stencil_is_singular(g):
+    # every neighbour of the interior points lies on one line: A = sum w dr dr^T has rank 1
+    x = np.array([[0.35, 0.5], [0.65, 0.5], [0.4, 0.5], [0.5, 0.5], [0.6, 0.5]])
+    kind = np.array([5, 5, 0, 0, 0], np.int32)
+    nrm = np.array([[1.0, 0.0], [-1.0, 0.0], [0, 0], [0, 0], [0, 0]])
+    p = bi.config("cavity2d_n41_v16_f64", n=5, nv=4, h=0.2)
+    s = g.Solver([p], [{"x": x, "kind": kind, "normal": nrm}])
+    s.set_maxwellian()
+    s.step(1)
+    with pytest.raises(g.BGKError) as e:
+        s.sync()
+    assert e.value.code == g.BGK_E_SINGULAR
+    s.close()
