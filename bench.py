@@ -184,6 +184,8 @@ def _host_cpu() -> dict:
                     break
     except OSError:
         pass
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    model = arm_parts.get(model.lower(), model)
     return {"model": model, "machine": platform.machine(), "logical_cores": os.cpu_count()}
 
 
