@@ -890,16 +890,84 @@ __global__ void k_moments(CaseView cv, const S* f) {
   }
 }
 
+// FP32/BF16 storage: one warp per point, each lane 4 consecutive velocities per chunk
+// (16-byte loads, velocity nodes staged in shared memory as FP32), the lanes'
+// Kahan-compensated FP32 sums added by warp shuffles as in the transport kernel, the
+// moments finished in FP64.
+template <typename S, int DIM, bool ROW>
+__global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
+  constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4;
+  __shared__ float s_v[64];
+  for (int t = threadIdx.x; t < cv.nv; t += blockDim.x) s_v[t] = (float)cv.vnodes[t];
+  __syncthreads();
+  const int W = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * W + (threadIdx.x >> 5);
+  if (i >= cv.n) return;
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const float inv_nv = 1.0f / (float)nv;
+  const S* fi = f + (int64_t)i * NC * NVp;
+  float msum[DIM + 2], mcmp[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) { msum[q] = 0.0f; mcmp[q] = 0.0f; }
+  for (int chunk = lane; chunk * VPL < NVp; chunk += 32) {
+    const int k0 = chunk * VPL;
+    float vel[VPL][DIM];
+    bool kin[VPL];
+    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float g[NC][VPL];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, g[c]);
+    float ps[DIM + 2];
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < VPL; ++e) {
+      const float g0 = kin[e] ? g[0][e] : 0.0f;
+      float v2 = 0.0f;
+      ps[0] += g0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g0, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
+      ps[DIM + 1] = fmaf(v2, g0, ps[DIM + 1]);
+      if (NC == 2) ps[DIM + 1] += kin[e] ? g[NC - 1][e] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) {
+      const float y = ps[q] - mcmp[q];
+      const float t = msum[q] + y;
+      mcmp[q] = (t - msum[q]) - y;
+      msum[q] = t;
+    }
+  }
+  double tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = (double)warp_sum(msum[q] - mcmp[q]);
+  if (lane == 0) {
+    double rho, Un[3] = {0, 0, 0}, T;
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    finish_moments<DIM>(tot, wv, &rho, Un, &T);
+    double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
+    mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
+  }
+}
+
 int launch_moments(const CaseView& cv, const void* f, cudaStream_t s) {
+  const int W = 8, grid = (cv.n + W - 1) / W;
+  const bool row = cv.nv % 4 == 0;
+#define BGK_MOM_WP(S, D)                                                                               \
+  {                                                                                                    \
+    if (row) k_moments_wp<S, D, true><<<grid, 32 * W, 0, s>>>(cv, (const S*)f);                        \
+    else k_moments_wp<S, D, false><<<grid, 32 * W, 0, s>>>(cv, (const S*)f);                           \
+  }
   if (cv.dim == 2) {
     if (cv.storage == 0) k_moments<double, double, 2><<<cv.n, 256, 0, s>>>(cv, (const double*)f);
-    else if (cv.storage == 1) k_moments<float, float, 2><<<cv.n, 256, 0, s>>>(cv, (const float*)f);
-    else k_moments<__nv_bfloat16, float, 2><<<cv.n, 256, 0, s>>>(cv, (const __nv_bfloat16*)f);
+    else if (cv.storage == 1) BGK_MOM_WP(float, 2)
+    else BGK_MOM_WP(__nv_bfloat16, 2)
   } else {
     if (cv.storage == 0) k_moments<double, double, 3><<<cv.n, 256, 0, s>>>(cv, (const double*)f);
-    else if (cv.storage == 1) k_moments<float, float, 3><<<cv.n, 256, 0, s>>>(cv, (const float*)f);
-    else k_moments<__nv_bfloat16, float, 3><<<cv.n, 256, 0, s>>>(cv, (const __nv_bfloat16*)f);
+    else if (cv.storage == 1) BGK_MOM_WP(float, 3)
+    else BGK_MOM_WP(__nv_bfloat16, 3)
   }
+#undef BGK_MOM_WP
   return 1;
 }
 
