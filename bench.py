@@ -300,10 +300,34 @@ def body_managed(g, torch, stream, steps: int = 400, every: int = 100) -> dict:
             "manage_every": every, "merges": merges, "adds": adds, "points_end": n}
 
 
+def sharded_rate(torch, stream, p: dict, parts: int, steps: int) -> dict:
+    """Workload p as `parts` velocity slabs on this GPU (a context each, their sums added
+    by bgk_shard_allreduce): device time per step of all slabs after 3 warm-up steps, and
+    the bytes of the two exchanges per step (what an allreduce over `parts` GPUs carries)."""
+    from paper_2408_02350_gb300.sharded import ShardedSolver
+    cl = bi.cloud_for(p)
+    s = ShardedSolver.on_one_device(p, cl, parts)
+    s.set_maxwellian(stream=stream)
+    s.step(3, stream=stream)
+    s.sync(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.sync(stream)
+    xbytes = 8 * (s.slabs[0].xm.numel() + s.slabs[0].xw.numel())
+    s.close()
+    upd = len(cl["kind"]) * p["nv"] ** p["dim"]
+    return {"value": upd / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "slabs": parts,
+            "exchange_bytes_per_step": xbytes}
+
+
 def extra_configs(g, torch, stream, workload: str) -> dict:
     """The ALE workload over its Kn sweep and with the second-order WLS stencils, the same
     cavity with a moving disc (plain and with point management), the plain FP64 41^2 x
-    16^2 cavity and the 3D 41^3 x 16^3 cavity (FP32)."""
+    16^2 cavity, the 3D 41^3 x 16^3 cavity (FP32) and the workload in velocity slabs."""
     out = {}
     p = bi.config(workload)
     if p.get("ale"):
@@ -316,6 +340,9 @@ def extra_configs(g, torch, stream, workload: str) -> dict:
     out["body2d_ale_n201_v32_f32_managed"] = body_managed(g, torch, stream)
     out["cavity2d_n41_v16_f64"] = _rate(g, torch, stream, bi.config("cavity2d_n41_v16_f64"), 100)
     out["cavity3d_n41_v16_f32"] = _rate(g, torch, stream, bi.config("cavity3d_n41_v16_f32"), 10)
+    # the workload through the velocity-sharded step: one slab (the split's own cost
+    # against the fused step) and 4 slabs sharing this GPU
+    out[workload + "_sharded"] = {str(k): sharded_rate(torch, stream, p, k, 100) for k in (1, 4)}
     return out
 
 

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 5
+#define BGK_ABI_VERSION 6
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -106,6 +106,12 @@ typedef struct bgk_params {
   double body_u[3];      /* body velocity */
   double body_centre[3]; /* centre of the body at bgk_init */
   double body_radius;    /* radius of the body's guard sphere (without guard) */
+  /* Velocity slab for the sharded step (bgk_shard_*): the case holds only the
+   * velocities with flattened grid index k in [vk_lo, vk_hi), and every layout of f
+   * ([n][ncomp][NV]) then has NV = vk_hi - vk_lo.  vk_hi = 0 (with vk_lo = 0) holds
+   * the whole grid.  vk_lo must be a multiple of 4.  Fixed at bgk_init. */
+  int32_t vk_lo;
+  int32_t vk_hi;
 } bgk_params;
 
 typedef struct bgk_stats {
@@ -157,12 +163,15 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
 
 /* f^0 = Maxwellian(rho0, u0[dim], T0) at every point of every case
  * (Sec. 2.1: g1 = G1, g2 = T0 G1 in 2D), and the stored moments (rho, U, T)
- * are those of f^0 (the transport of the first step uses their U). */
+ * are those of f^0 (the transport of the first step uses their U).  A case that
+ * holds a proper velocity slab (vk_lo, vk_hi) gets its slab of f^0 only; its
+ * moments come from bgk_shard_partial and bgk_shard_set_moments. */
 int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, void* stream);
 
 /* Copy case c's distribution in or out, layout [n][ncomp][NV] with element
  * type dtype (bgk_storage), from/to host memory (on_device = 0) or device
- * memory (on_device = 1).  bgk_set_f also recomputes the stored moments.
+ * memory (on_device = 1).  bgk_set_f also recomputes the stored moments (not for
+ * a proper velocity slab: see bgk_set_maxwellian).
  * Host copies are synchronous (direct between host memory and the distribution
  * buffer when dtype is the storage type and NV needs no padding, else staged
  * and converted on the device); device copies are stream-ordered. */
@@ -194,8 +203,50 @@ int bgk_get_stencils(bgk_ctx* ctx, int32_t c, double* P, double* recon, int64_t 
  * walls, and with ale = 1 the motion x^{n+1} = x^n + dt U^{n+1}.  Asynchronous:
  * with ale = 1 the motion and the next step's lists run on an internal stream
  * concurrently with the wall kernel, and every such piece of work is ordered
- * before later work on `stream` when the call returns. */
+ * before later work on `stream` when the call returns.  BGK_E_STATE when a case
+ * holds a proper velocity slab (such cases step with bgk_shard_*). */
 int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream);
+
+/* Velocity-sharded step, not in the paper (Sec. 5 parallelises over points on one
+ * GPU): the step split over the discrete velocities, for several GPUs.  R cases -- in R contexts on R GPUs, or in one or several contexts on one GPU --
+ * hold the same points and disjoint velocity slabs [vk_lo, vk_hi) that cover the
+ * grid.  Transport and relaxation act on each velocity separately; the slabs couple
+ * only through sums over velocities, so positions, neighbour lists, stencils and
+ * moments are replicated and evolve identically in every slab as long as each slab
+ * receives the same sums.  One step of case c of every slab is
+ *   bgk_shard_transport(xm)       then xm <- sum of xm over the slabs (allreduce)
+ *   bgk_shard_relax(xm, xw)       then xw <- sum of xw over the slabs (allreduce)
+ *   bgk_shard_walls(xw)
+ * and equals a bgk_step of the whole grid up to the order of the velocity sums.
+ * Exchange buffers are caller-owned device arrays of doubles:
+ *   xm  [n][dim + 2]      raw moment sums (sum g, sum v g, sum |v|^2 g (+ sum h))
+ *                         of f~ (transport: interior rows; other rows untouched)
+ *                         or of f (bgk_shard_partial: every row)
+ *   xw  [n_wall][2 dim + 6], wall points in ascending index order: sum over the
+ *       arriving velocities of |c_n| g, sum over the leaving ones of c_n M_w, the
+ *       moment sums of the arriving half, those of M_w over the leaving half
+ * (bgk_shard_sizes gives the two lengths).  The buffers must stay valid until the
+ * stream has run the call's kernels; the summed buffer must hold identical bits in
+ * every slab (NCCL's allreduce and bgk_shard_allreduce both do).  Calls out of this
+ * order return BGK_E_STATE.  Stream-ordered.  With ale = 1 the motion and the next
+ * lists run on the internal stream after bgk_shard_relax, as in bgk_step.
+ * bgk_stats.steps counts the bgk_shard_walls calls of case 0. */
+int bgk_shard_sizes(bgk_ctx* ctx, int32_t c, int64_t* n_xm, int64_t* n_xw);
+int bgk_shard_transport(bgk_ctx* ctx, int32_t c, double* xm, void* stream);
+int bgk_shard_relax(bgk_ctx* ctx, int32_t c, const double* xm, double* xw, void* stream);
+int bgk_shard_walls(bgk_ctx* ctx, int32_t c, const double* xw, void* stream);
+
+/* Stored moments of a sharded case from its current f: bgk_shard_partial writes the
+ * slab's raw sums of every point to xm, and after the sum over the slabs
+ * bgk_shard_set_moments sets (rho, U, T) of every point from it (after
+ * bgk_set_maxwellian, bgk_set_f or bgk_set_state).  Stream-ordered. */
+int bgk_shard_partial(bgk_ctx* ctx, int32_t c, double* xm, void* stream);
+int bgk_shard_set_moments(bgk_ctx* ctx, int32_t c, const double* xm, void* stream);
+
+/* Sum for slabs that share one GPU: bufs[nbufs] device arrays of count doubles
+ * (1 <= nbufs <= 16); every element becomes the sum over the buffers, added in
+ * buffer order, in every buffer.  Stream-ordered. */
+int bgk_shard_allreduce(double* const* bufs, int32_t nbufs, int64_t count, void* stream);
 
 /* Case c's stored moments: rho[n], u[n][dim], T[n] (interior points: moments
  * of the last transported state; wall points: moments of f_b).  Host
@@ -245,7 +296,8 @@ int bgk_set_params(bgk_ctx* ctx, int32_t c, const bgk_params* p);
  * capacity n + spare_points (later additions are dropped).  Point indices change:
  * host arrays of per-point data must be re-read.  counts (host, int64[3])
  * receives the new point count, the points removed (merged away or next to a
- * wall) and the points added.  Synchronous. */
+ * wall) and the points added.  Synchronous.  BGK_E_STATE for a proper velocity
+ * slab. */
 int bgk_manage(bgk_ctx* ctx, int32_t c, double rmin, int32_t min_nbrs, int64_t* counts, void* stream);
 
 /* Objective of the current state of case c, not in the paper: the x-momentum flux
@@ -254,7 +306,8 @@ int bgk_manage(bgk_ctx* ctx, int32_t c, double rmin, int32_t min_nbrs, int64_t* 
  * component, normal to the lid; g = g1 in 2D, f in 3D).  J (device, one double) is
  * incremented by J; when lam is not NULL, lam += scale dJ/df.  lam has the internal
  * layout [n][ncomp][NVp] (NVp from bgk_get_stats) of the compute type: double
- * for BGK_F64 storage, float otherwise.  Stream-ordered. */
+ * for BGK_F64 storage, float otherwise.  Stream-ordered.  BGK_E_STATE for a proper
+ * velocity slab (as bgk_adjoint_step). */
 int bgk_objective(bgk_ctx* ctx, int32_t c, double* J, void* lam, double scale, void* stream);
 
 /* One step of the discrete adjoint of bgk_step for fixed points (ale = 0), not in

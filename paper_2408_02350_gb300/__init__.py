@@ -44,6 +44,7 @@ class bgk_params(C.Structure):
         ("spare_points", C.c_int32), ("pad2_", C.c_int32),
         ("body_wall", C.c_int32), ("wls_order", C.c_int32), ("body_u", C.c_double * 3),
         ("body_centre", C.c_double * 3), ("body_radius", C.c_double),
+        ("vk_lo", C.c_int32), ("vk_hi", C.c_int32),
     ]
 
 
@@ -90,6 +91,13 @@ _SIGS = {
     "bgk_adjoint_step": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "bgk_neighbours_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, C.c_double, C.c_int32, C.c_int32, _P, _P,
                                          C.c_int32, _P]),
+    "bgk_shard_sizes": (C.c_int, [_P, C.c_int32, _PL, _PL]),
+    "bgk_shard_transport": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "bgk_shard_relax": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "bgk_shard_walls": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "bgk_shard_partial": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "bgk_shard_set_moments": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "bgk_shard_allreduce": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int64, _P]),
 }
 
 _lib = None
@@ -319,6 +327,41 @@ def bgk_neighbours_noalloc(dim: int, n: int, x, h: float, periodic: int, cap: in
         raise BGKError(code, "bgk_neighbours_noalloc")
 
 
+def bgk_shard_sizes(ctx, case: int):
+    """Lengths (doubles) of the two exchange buffers of the sharded step: (xm, xw)."""
+    a, b = C.c_int64(0), C.c_int64(0)
+    _check(lib().bgk_shard_sizes(ctx, case, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def bgk_shard_transport(ctx, case: int, xm, stream=None) -> None:
+    _check(lib().bgk_shard_transport(ctx, case, _ptr(xm), _stream_ptr(stream)), ctx)
+
+
+def bgk_shard_relax(ctx, case: int, xm, xw, stream=None) -> None:
+    _check(lib().bgk_shard_relax(ctx, case, _ptr(xm), _ptr(xw) if xw is not None else None, _stream_ptr(stream)), ctx)
+
+
+def bgk_shard_walls(ctx, case: int, xw, stream=None) -> None:
+    _check(lib().bgk_shard_walls(ctx, case, _ptr(xw) if xw is not None else None, _stream_ptr(stream)), ctx)
+
+
+def bgk_shard_partial(ctx, case: int, xm, stream=None) -> None:
+    _check(lib().bgk_shard_partial(ctx, case, _ptr(xm), _stream_ptr(stream)), ctx)
+
+
+def bgk_shard_set_moments(ctx, case: int, xm, stream=None) -> None:
+    _check(lib().bgk_shard_set_moments(ctx, case, _ptr(xm), _stream_ptr(stream)), ctx)
+
+
+def bgk_shard_allreduce(bufs: list, count: int, stream=None) -> None:
+    """Elementwise sum of device buffers (tensors of float64) into each of them."""
+    arr = (_P * len(bufs))(*[_ptr(b) for b in bufs])
+    code = lib().bgk_shard_allreduce(arr, len(bufs), int(count), _stream_ptr(stream))
+    if code != BGK_OK:
+        raise BGKError(code, "bgk_shard_allreduce")
+
+
 # ---- convenience ----
 
 def params_from(p: dict) -> bgk_params:
@@ -344,6 +387,7 @@ def params_from(p: dict) -> bgk_params:
         q.body_centre[a] = float(bc[a])
     q.body_radius = float(p.get("body_radius", 0.0))
     q.wls_order = int(p.get("wls_order", 1))
+    q.vk_lo, q.vk_hi = int(p.get("vk_lo", 0)), int(p.get("vk_hi", 0))
     return q
 
 
@@ -371,9 +415,11 @@ class Solver:
             pass
 
     def dims(self, case: int = 0):
+        """(dim, ncomp, NV): NV velocities per row of f (those of the slab [vk_lo, vk_hi) if set)."""
         p = self.params[case]
         d = int(p["dim"])
-        return d, (2 if d == 2 else 1), int(p["nv"]) ** d
+        hi = int(p.get("vk_hi", 0))
+        return d, (2 if d == 2 else 1), (hi - int(p.get("vk_lo", 0)) if hi else int(p["nv"]) ** d)
 
     def set_maxwellian(self, rho0=1.0, u0=(0.0, 0.0, 0.0), T0=1.0, stream=None):
         bgk_set_maxwellian(self.ctx, rho0, u0, T0, stream)

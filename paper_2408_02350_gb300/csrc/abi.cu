@@ -50,6 +50,12 @@ struct CaseHost {
   int32_t* wall_of = nullptr;
   bool tslot_valid = false;
   int32_t nlid = 0;
+  // velocity slab: a proper part of the grid (only the sharded calls step it); the
+  // sharded step's next call (0 transport, 1 relax, 2 walls) and the side chain whose
+  // wall weights its wall kernel waits for
+  bool slab = false;
+  int shard_phase = 0;
+  int64_t shard_recon = -1;
   // ALE: the lists of the next step (second set of cnt, col, P, recon) are built on
   // the side stream right after the motion, while the wall kernel runs; they are
   // swapped in at the next step.  ev_fork orders the side work after the transport,
@@ -168,6 +174,10 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
   if (p.nv < 2 || p.nv > 64) { *why = "nv must be in [2, 64]"; return 0; }
   int64_t NV = p.dim == 2 ? (int64_t)p.nv * p.nv : (int64_t)p.nv * p.nv * p.nv;
   if (NV > 8192) { *why = "nv^dim must be <= 8192"; return 0; }
+  if (p.vk_hi == 0 ? p.vk_lo != 0 : (p.vk_lo < 0 || p.vk_lo >= p.vk_hi || p.vk_hi > NV || p.vk_lo % 4 != 0)) {
+    *why = "velocity slab must satisfy 0 <= vk_lo < vk_hi <= nv^dim, vk_lo % 4 == 0 (or vk_lo = vk_hi = 0)";
+    return 0;
+  }
   if (!(p.vmax > 0) || !(p.dt > 0) || !(p.h > 0) || !(p.alpha > 0) || !(p.wall_T > 0)) {
     *why = "vmax, dt, h, alpha, wall_T must be positive";
     return 0;
@@ -356,7 +366,7 @@ bool batch_eligible(const bgk_ctx* ctx) {
   const CaseHost& c0 = ctx->cases[0];
   if (c0.cv.dim != 2) return false;  // the batched kernels are the 2D ones
   for (const CaseHost& c : ctx->cases) {
-    if (c.cv.ale || c.p.storage == 0 || c.p.storage != c0.p.storage || c.cv.dim != c0.cv.dim || c.cur != c0.cur)
+    if (c.slab || c.cv.ale || c.p.storage == 0 || c.p.storage != c0.p.storage || c.cv.dim != c0.cv.dim || c.cur != c0.cur)
       return false;
   }
   return true;
@@ -495,6 +505,11 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.dim = dim;
     v.nv = q.nv;
     v.NV = dim == 2 ? q.nv * q.nv : q.nv * q.nv * q.nv;
+    if (q.vk_hi > 0) {
+      c.slab = q.vk_lo != 0 || q.vk_hi != v.NV;
+      v.vk0 = q.vk_lo;
+      v.NV = q.vk_hi - q.vk_lo;
+    }
     v.NVp = (v.NV + 3) / 4 * 4;
     v.ncomp = dim == 2 ? 2 : 1;
     v.cap = q.max_nbrs;
@@ -647,7 +662,7 @@ int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, v
   for (auto& c : ctx->cases) {
     refresh_view(c);
     ctx->launches += launch_set_maxwellian(c.cv, rho0, u0, T0, s);
-    ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
+    if (!c.slab) ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
     CKL(ctx);
   }
   return BGK_OK;
@@ -674,7 +689,7 @@ int bgk_set_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype, int32_t on
     }
     ctx->launches += launch_pack_f(c.cv, src, dtype, c.f[c.cur], s);
   }
-  ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
+  if (!c.slab) ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
   CKL(ctx);
   if (!on_device) CK(ctx, cudaStreamSynchronize(s));
   return BGK_OK;
@@ -769,6 +784,8 @@ int bgk_get_stencils(bgk_ctx* ctx, int32_t ci, double* P, double* recon, int64_t
 
 int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
   if (!ctx || nsteps < 0) return ctx ? fail(ctx, BGK_E_INVAL, "bgk_step: nsteps < 0") : BGK_E_INVAL;
+  for (const CaseHost& c : ctx->cases)
+    if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_step: a case holds a velocity slab (step it with bgk_shard_*)");
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   EvPair* e;
@@ -825,6 +842,136 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
   for (auto& c : ctx->cases)
     if (c.next_ready && (st = join_side(ctx, c, s))) return st;
   return BGK_OK;
+}
+
+// ---- velocity-sharded step ----
+
+static int shard_case(bgk_ctx* ctx, int32_t ci, const void* buf, const char* fn, CaseHost** out) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !buf)
+    return ctx ? fail(ctx, BGK_E_INVAL, "%s: bad argument", fn) : BGK_E_INVAL;
+  *out = &ctx->cases[ci];
+  refresh_view(**out);
+  return BGK_OK;
+}
+
+int bgk_shard_sizes(bgk_ctx* ctx, int32_t ci, int64_t* n_xm, int64_t* n_xw) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !n_xm || !n_xw)
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_shard_sizes: bad argument") : BGK_E_INVAL;
+  const CaseView& v = ctx->cases[ci].cv;
+  *n_xm = (int64_t)v.n * (v.dim + 2);
+  *n_xw = (int64_t)v.n_wall * (2 * v.dim + 6);
+  return BGK_OK;
+}
+
+int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
+  CaseHost* cp;
+  int st;
+  if ((st = shard_case(ctx, ci, xm, "bgk_shard_transport", &cp))) return st;
+  CaseHost& c = *cp;
+  if (c.shard_phase != 0) return fail(ctx, BGK_E_STATE, "bgk_shard_transport: the previous sharded step is not finished");
+  cudaStream_t s = (cudaStream_t)stream;
+  invalidate_batch(ctx);
+  // the lists of this step, as in bgk_step
+  c.shard_recon = -1;
+  if (c.next_ready && c.stencils_valid && c.cv.ale) {
+    swap_in_next(c);
+    CK(ctx, cudaStreamWaitEvent(s, c.ev_join, 0));
+    c.shard_recon = c.chain - 1;
+  } else if (c.cv.ale || !c.stencils_valid) {
+    if ((st = build_lists(ctx, c, s))) return st;
+  }
+  EvPair* e;
+  CaseView v = c.cv;
+  v.xs = xm;
+  if ((st = timed_begin(ctx, K_TRANSPORT, s, &e))) return st;
+  ctx->launches += launch_shard_transport(v, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  c.shard_phase = 1;
+  return BGK_OK;
+}
+
+int bgk_shard_relax(bgk_ctx* ctx, int32_t ci, const double* xm, double* xw, void* stream) {
+  CaseHost* cp;
+  int st;
+  if ((st = shard_case(ctx, ci, xm, "bgk_shard_relax", &cp))) return st;
+  CaseHost& c = *cp;
+  if (!xw && c.cv.n_wall > 0) return fail(ctx, BGK_E_INVAL, "bgk_shard_relax: bad argument");
+  if (c.shard_phase != 1) return fail(ctx, BGK_E_STATE, "bgk_shard_relax: call bgk_shard_transport first");
+  cudaStream_t s = (cudaStream_t)stream;
+  EvPair* e;
+  CaseView v = c.cv;
+  v.xs = const_cast<double*>(xm);
+  if ((st = timed_begin(ctx, K_TRANSPORT, s, &e))) return st;
+  ctx->launches += launch_shard_relax(v, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  // the motion reads U^{n+1}, which the relaxation has just stored
+  if (c.cv.ale && (st = move_and_prebuild(ctx, c, s))) return st;
+  if (c.shard_recon >= 0) CK(ctx, cudaStreamWaitEvent(s, c.ev_recon[c.shard_recon & 1], 0));
+  v.xs = xw;
+  if ((st = timed_begin(ctx, K_WALLS, s, &e))) return st;
+  ctx->launches += launch_shard_walls(v, 1, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  c.shard_phase = 2;
+  return BGK_OK;
+}
+
+int bgk_shard_walls(bgk_ctx* ctx, int32_t ci, const double* xw, void* stream) {
+  CaseHost* cp;
+  int st;
+  if (ctx && ci >= 0 && ci < (int)ctx->cases.size() && !xw && ctx->cases[ci].cv.n_wall == 0) {
+    static const double none = 0.0;
+    xw = &none;  // no wall points: nothing is read
+  }
+  if ((st = shard_case(ctx, ci, xw, "bgk_shard_walls", &cp))) return st;
+  CaseHost& c = *cp;
+  if (c.shard_phase != 2) return fail(ctx, BGK_E_STATE, "bgk_shard_walls: call bgk_shard_relax first");
+  cudaStream_t s = (cudaStream_t)stream;
+  EvPair* e;
+  CaseView v = c.cv;
+  v.xs = const_cast<double*>(xw);
+  if ((st = timed_begin(ctx, K_WALLS, s, &e))) return st;
+  ctx->launches += launch_shard_walls(v, 2, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  c.cur = 1 - c.cur;
+  refresh_view(c);
+  if (c.next_ready && (st = join_side(ctx, c, s))) return st;
+  c.shard_phase = 0;
+  if (ci == 0) ctx->steps += 1;
+  return BGK_OK;
+}
+
+int bgk_shard_partial(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
+  CaseHost* cp;
+  int st;
+  if ((st = shard_case(ctx, ci, xm, "bgk_shard_partial", &cp))) return st;
+  CaseView v = cp->cv;
+  v.xs = xm;
+  ctx->launches += launch_shard_partial(v, (cudaStream_t)stream);
+  CKL(ctx);
+  return BGK_OK;
+}
+
+int bgk_shard_set_moments(bgk_ctx* ctx, int32_t ci, const double* xm, void* stream) {
+  CaseHost* cp;
+  int st;
+  if ((st = shard_case(ctx, ci, xm, "bgk_shard_set_moments", &cp))) return st;
+  CaseView v = cp->cv;
+  v.xs = const_cast<double*>(xm);
+  ctx->launches += launch_shard_moments(v, (cudaStream_t)stream);
+  CKL(ctx);
+  return BGK_OK;
+}
+
+int bgk_shard_allreduce(double* const* bufs, int32_t nbufs, int64_t count, void* stream) {
+  if (!bufs || nbufs < 1 || nbufs > SHARD_MAX_BUFS || count < 0) return BGK_E_INVAL;
+  for (int r = 0; r < nbufs; ++r)
+    if (!bufs[r]) return BGK_E_INVAL;
+  launch_shard_allreduce(bufs, nbufs, count, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
 int bgk_moments(bgk_ctx* ctx, int32_t ci, double* rho, double* u, double* T, int32_t on_device, void* stream) {
@@ -951,6 +1098,7 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
     }
     o += 3 * sizeof(double);
     c.stencils_valid = false;
+    c.shard_phase = 0;
     if (int st = reset_skin(ctx, c)) return st;  // positions changed: rebuild the candidates
     c.cur = 0;
     refresh_view(c);
@@ -970,6 +1118,7 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
       p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin ||
       p->spare_points != o.spare_points || p->wls_order != o.wls_order || p->body_wall != o.body_wall ||
+      p->vk_lo != o.vk_lo || p->vk_hi != o.vk_hi ||
       p->body_radius != o.body_radius ||
       p->body_centre[0] != o.body_centre[0] || p->body_centre[1] != o.body_centre[1] ||
       p->body_centre[2] != o.body_centre[2])
@@ -1007,6 +1156,7 @@ int bgk_manage(bgk_ctx* ctx, int32_t ci, double rmin, int32_t min_nbrs, int64_t*
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_manage: bad argument") : BGK_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CaseHost& c = ctx->cases[ci];
+  if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_manage: not available for a velocity slab");
   int st;
   if ((st = join_side(ctx, c, s))) return st;
   refresh_view(c);
@@ -1077,6 +1227,7 @@ int bgk_objective(bgk_ctx* ctx, int32_t ci, double* J, void* lam, double scale, 
   if (!ctx || ci < 0 || ci >= (int)ctx->cases.size())
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_objective: bad argument") : BGK_E_INVAL;
   CaseHost& c = ctx->cases[ci];
+  if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_objective: not available for a velocity slab");
   refresh_view(c);
   ctx->launches += launch_objective(c.cv, c.nlid, J, lam, scale, (cudaStream_t)stream);
   CKL(ctx);
@@ -1088,6 +1239,7 @@ int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_adjoint_step: bad argument") : BGK_E_INVAL;
   CaseHost& c = ctx->cases[ci];
   if (c.cv.ale) return fail(ctx, BGK_E_STATE, "bgk_adjoint_step: the adjoint is for fixed points (ale = 0)");
+  if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_adjoint_step: not available for a velocity slab");
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   refresh_view(c);

@@ -101,6 +101,12 @@ struct CaseView {
   double body_u[3];
   double body_rg;       // guard radius body_radius + guard
   BodyState* body;
+
+  // velocity slab of a sharded case: its rows of f hold the velocities with flattened
+  // grid index vk0 .. vk0 + NV - 1 (vk0 = 0 and NV = nv^dim for the whole grid)
+  int32_t vk0;
+  int32_t pad_vk;
+  double* xs;  // exchange buffer of the current sharded phase (device, caller-owned), else null
 };
 
 // Launchers (stream-ordered; each returns the number of kernels launched).
@@ -124,6 +130,23 @@ int launch_neighbours_skin(const CaseView& cv, cudaStream_t s);
 // ST_TIMEOUT and its CTAs return.
 bool chain_eligible(const CaseView& cv);
 int launch_chain(const CaseView& cv, int* grid_cache, long long max_spins, cudaStream_t s);
+// Velocity-sharded step (slabs of the velocity grid, coupled only through velocity sums;
+// cv.xs is the exchange buffer of the phase):
+//  transport: f~ of the slab into f_out, raw moment sums of f~ over the slab into
+//             xs[i][dim + 2] (interior rows i);
+//  relax:     moments of interior points from the summed xs, relaxation of f_out in place;
+//  walls 1:   arriving half of every wall row and the wall sums xs[w][2 dim + 6];
+//  walls 2:   leaving half and the wall moments from the summed xs;
+//  partial:   raw moment sums of f_in over the slab, xs[i][dim + 2] for every point;
+//  moments:   moments of every point from the summed xs;
+//  allreduce: sum of nbufs device buffers of count doubles into each of them.
+int launch_shard_transport(const CaseView& cv, cudaStream_t s);
+int launch_shard_relax(const CaseView& cv, cudaStream_t s);
+int launch_shard_walls(const CaseView& cv, int phase, cudaStream_t s);
+int launch_shard_partial(const CaseView& cv, cudaStream_t s);
+int launch_shard_moments(const CaseView& cv, cudaStream_t s);
+int launch_shard_allreduce(double* const* bufs, int nbufs, int64_t count, cudaStream_t s);
+constexpr int SHARD_MAX_BUFS = 16;
 // part 0: all points; 1: interior stencils (all points for FP64 storage); 2: wall
 // reconstruction weights (nothing for FP64 storage).
 int launch_stencils(const CaseView& cv, cudaStream_t s, int part = 0);

@@ -86,7 +86,79 @@ __device__ __forceinline__ void block_sum0(const T (&v)[NVAL], double (&out)[NVA
 // ---------------------------------------------------------------------------
 // transport + moments + relaxation
 // ---------------------------------------------------------------------------
-template <typename S, typename C, int DIM, int NCH, bool ALE>
+// Moments of f~_i from the raw sums tot, tau and the Maxwellian (one thread, FP64,
+// broadcast through shared memory), then f^{n+1} = (tau f~ + dt M)/(tau + dt) for the
+// thread's chunks, written to the output row.  vk0: first grid velocity of the row.
+template <typename S, typename C, int DIM, int NCH>
+__device__ __forceinline__ void relax_cta(const CaseView& cv, const int i, const double (&tot)[DIM + 2],
+                                          const C (&ft)[NCH][DIM == 2 ? 2 : 1][4], const C* s_v, double* s_red,
+                                          const int vk0) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const int nchunk = NVp >> 2;
+  const int64_t rowlen = (int64_t)NC * NVp;
+  // moments, tau and relaxation coefficients (one thread, FP64), broadcast through shared memory
+  C* s_fin = reinterpret_cast<C*>(s_red + 6 * 32);  // past the slots block_sum0 uses (5 x 32)
+  if (threadIdx.x == 0) {
+    double rho, Un[3] = {0, 0, 0}, T;
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    finish_moments<DIM>(tot, wv, &rho, Un, &T);
+    double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
+    mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
+    double a = 1.0, b = 0.0, pref = 0.0, inv2T = 0.0;
+    if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T)) {
+      set_status(cv.status, ST_NONFINITE);
+    } else if (cv.tau_mode != 2) {
+      const double pi = 3.14159265358979323846;
+      const double tau = cv.tau_mode == 1 ? sqrt(2.0 / pi) * cv.kn : sqrt(2.0 / pi) * cv.kn / (rho * sqrt(T));
+      a = tau / (tau + cv.dt);
+      b = cv.dt / (tau + cv.dt);
+      pref = DIM == 2 ? rho / (2.0 * pi * T) : rho / pow(2.0 * pi * T, 1.5);
+      inv2T = 1.0 / (2.0 * T);
+    }
+    s_fin[0] = (C)a; s_fin[1] = (C)b; s_fin[2] = (C)pref; s_fin[3] = (C)inv2T; s_fin[4] = (C)T;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s_fin[5 + d] = (C)Un[d];
+  }
+  __syncthreads();
+  const C ca = s_fin[0], cb = s_fin[1], pref = s_fin[2], inv2T = s_fin[3], Tn = s_fin[4];
+  C Un[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) Un[d] = s_fin[5 + d];
+
+  S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * rowlen;
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int chunk = threadIdx.x + q * blockDim.x;
+    if (chunk < nchunk) {
+      C out[NC][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = 4 * chunk + e;
+        if (k < NV) {
+          int kk = k + vk0;
+          C c2 = (C)0;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            const C d = s_v[kk % nv] - Un[a];
+            kk /= nv;
+            c2 += d * d;
+          }
+          const C M = pref * expc<C>(-c2 * inv2T);
+          out[0][e] = ca * ft[q][0][e] + cb * M;
+          if (NC == 2) out[NC - 1][e] = ca * ft[q][NC - 1][e] + cb * Tn * M;
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) out[c][e] = (C)0;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, out[c]);
+    }
+  }
+}
+
+template <typename S, typename C, int DIM, int NCH, bool ALE, bool SH = false>
 __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   constexpr int DD = DIM * DIM;
@@ -100,6 +172,7 @@ __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
   const int m = cv.cnt[i];
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const int nchunk = NVp >> 2;
+  const int vk0 = SH ? cv.vk0 : 0;
   {
     const int32_t* col = cv.col + (int64_t)i * cv.cap;
     const C* P = reinterpret_cast<const C*>(cv.P) + (int64_t)i * cv.cap * DD;
@@ -121,7 +194,7 @@ __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k = 4 * chunk + e;
-      int kk = k < NV ? k : 0;
+      int kk = k < NV ? k + vk0 : 0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         cvel[q][e][a] = k < NV ? s_v[kk % nv] - U[a] : (C)0;
@@ -193,7 +266,7 @@ __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
         for (int c = 0; c < NC; ++c) ft[q][c][e] = fiv[c][e] - two_dt * (acc[q][c][e] - sk[q][e] * fiv[c][e]);
         const int k = 4 * chunk + e;
         if (k < NV) {
-          int kk = k;
+          int kk = k + vk0;
           C v2 = (C)0;
           const C g = ft[q][0][e];
           part[0] += g;
@@ -218,92 +291,102 @@ __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
   double tot[DIM + 2];
   block_sum0<DIM + 2, C>(part, tot, s_red);
 
-  // moments, tau and relaxation coefficients (one thread, FP64), broadcast through shared memory
-  C* s_fin = reinterpret_cast<C*>(s_red + 6 * 32);  // past the slots block_sum0 uses (5 x 32)
-  if (threadIdx.x == 0) {
-    double rho, Un[3] = {0, 0, 0}, T;
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
-    finish_moments<DIM>(tot, wv, &rho, Un, &T);
-    double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
-    mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
-    double a = 1.0, b = 0.0, pref = 0.0, inv2T = 0.0;
-    if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T)) {
-      set_status(cv.status, ST_NONFINITE);
-    } else if (cv.tau_mode != 2) {
-      const double pi = 3.14159265358979323846;
-      const double tau = cv.tau_mode == 1 ? sqrt(2.0 / pi) * cv.kn : sqrt(2.0 / pi) * cv.kn / (rho * sqrt(T));
-      a = tau / (tau + cv.dt);
-      b = cv.dt / (tau + cv.dt);
-      pref = DIM == 2 ? rho / (2.0 * pi * T) : rho / pow(2.0 * pi * T, 1.5);
-      inv2T = 1.0 / (2.0 * T);
+  if constexpr (SH) {
+    // sharded step: the slab's sums to the exchange buffer, f~ to the output row
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = tot[q];
     }
-    s_fin[0] = (C)a; s_fin[1] = (C)b; s_fin[2] = (C)pref; s_fin[3] = (C)inv2T; s_fin[4] = (C)T;
+    S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * rowlen;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) s_fin[5 + d] = (C)Un[d];
-  }
-  __syncthreads();
-  const C ca = s_fin[0], cb = s_fin[1], pref = s_fin[2], inv2T = s_fin[3], Tn = s_fin[4];
-  C Un[DIM];
+    for (int q = 0; q < NCH; ++q) {
+      const int chunk = threadIdx.x + q * blockDim.x;
+      if (chunk < nchunk) {
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) Un[d] = s_fin[5 + d];
-
-  S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * rowlen;
-#pragma unroll
-  for (int q = 0; q < NCH; ++q) {
-    const int chunk = threadIdx.x + q * blockDim.x;
-    if (chunk < nchunk) {
-      C out[NC][4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = 4 * chunk + e;
-        if (k < NV) {
-          int kk = k;
-          C c2 = (C)0;
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) {
-            const C d = s_v[kk % nv] - Un[a];
-            kk /= nv;
-            c2 += d * d;
-          }
-          const C M = pref * expc<C>(-c2 * inv2T);
-          out[0][e] = ca * ft[q][0][e] + cb * M;
-          if (NC == 2) out[NC - 1][e] = ca * ft[q][NC - 1][e] + cb * Tn * M;
-        } else {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) out[c][e] = (C)0;
-        }
+        for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, ft[q][c]);
       }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) st4(fo + (int64_t)c * NVp + 4 * chunk, out[c]);
     }
+  } else {
+    relax_cta<S, C, DIM, NCH>(cv, i, tot, ft, s_v, s_red, 0);
   }
 }
 
-template <typename S, typename C, int DIM, int NCH>
+template <typename S, typename C, int DIM, int NCH, bool SH = false>
 static void launch_transport_t(const CaseView& cv, int threads, size_t smem, cudaStream_t s) {
   if (cv.ale) {
-    auto k = k_transport<S, C, DIM, NCH, true>;
+    auto k = k_transport<S, C, DIM, NCH, true, SH>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<cv.n_int, threads, smem, s>>>(cv);
   } else {
-    auto k = k_transport<S, C, DIM, NCH, false>;
+    auto k = k_transport<S, C, DIM, NCH, false, SH>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<cv.n_int, threads, smem, s>>>(cv);
+  }
+}
+
+// Sharded step, FP64 storage: one CTA per interior point (the launch shape of
+// k_transport) relaxes f~ in the output row with the moments of the summed sums.
+template <typename S, typename C, int DIM, int NCH>
+__global__ void __launch_bounds__(256) k_shard_relax_cta(const CaseView cv) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  __shared__ double s_red[8 * 32];
+  __shared__ C s_v[64];
+  const int i = cv.int_idx[blockIdx.x];
+  const int NVp = cv.NVp, nchunk = NVp >> 2;
+  for (int t = threadIdx.x; t < cv.nv; t += blockDim.x) s_v[t] = (C)cv.vnodes[t];
+  const S* fo = reinterpret_cast<const S*>(cv.f_out) + (int64_t)i * NC * NVp;
+  C ft[NCH][NC][4];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int chunk = threadIdx.x + q * blockDim.x;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (chunk < nchunk) {
+        ld4(fo + (int64_t)c * NVp + 4 * chunk, ft[q][c]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ft[q][c][e] = (C)0;
+      }
+    }
+  }
+  double tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = cv.xs[(int64_t)i * (DIM + 2) + q];
+  __syncthreads();
+  relax_cta<S, C, DIM, NCH>(cv, i, tot, ft, s_v, s_red, cv.vk0);
+}
+
+// CTA shape of the FP64 transport: NCH chunks of 4 velocities per thread, at most 256 threads.
+static inline void cta_shape(int NVp, int* nch, int* threads) {
+  const int nchunk = NVp / 4;
+  int q = 1;
+  while ((nchunk + q - 1) / q > 256) q *= 2;
+  *nch = q;
+  *threads = (((nchunk + q - 1) / q) + 31) / 32 * 32;
+}
+
+template <typename S, typename C, int DIM, bool SH = false>
+static void launch_transport_d(const CaseView& cv, cudaStream_t s) {
+  int nch, threads;
+  cta_shape(cv.NVp, &nch, &threads);
+  const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * cv.cap) + sizeof(C) * cv.cap * DIM * DIM;
+  switch (nch) {
+    case 1: launch_transport_t<S, C, DIM, 1, SH>(cv, threads, smem, s); break;
+    case 2: launch_transport_t<S, C, DIM, 2, SH>(cv, threads, smem, s); break;
+    case 4: launch_transport_t<S, C, DIM, 4, SH>(cv, threads, smem, s); break;
+    default: launch_transport_t<S, C, DIM, 8, SH>(cv, threads, smem, s); break;
   }
 }
 
 template <typename S, typename C, int DIM>
-static void launch_transport_d(const CaseView& cv, cudaStream_t s) {
-  const int nchunk = cv.NVp / 4;
-  int nch = 1;
-  while ((nchunk + nch - 1) / nch > 256) nch *= 2;
-  const int threads = (((nchunk + nch - 1) / nch) + 31) / 32 * 32;
-  const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * cv.cap) + sizeof(C) * cv.cap * DIM * DIM;
+static void launch_shard_relax_d(const CaseView& cv, cudaStream_t s) {
+  int nch, threads;
+  cta_shape(cv.NVp, &nch, &threads);
   switch (nch) {
-    case 1: launch_transport_t<S, C, DIM, 1>(cv, threads, smem, s); break;
-    case 2: launch_transport_t<S, C, DIM, 2>(cv, threads, smem, s); break;
-    case 4: launch_transport_t<S, C, DIM, 4>(cv, threads, smem, s); break;
-    default: launch_transport_t<S, C, DIM, 8>(cv, threads, smem, s); break;
+    case 1: k_shard_relax_cta<S, C, DIM, 1><<<cv.n_int, threads, 0, s>>>(cv); break;
+    case 2: k_shard_relax_cta<S, C, DIM, 2><<<cv.n_int, threads, 0, s>>>(cv); break;
+    case 4: k_shard_relax_cta<S, C, DIM, 4><<<cv.n_int, threads, 0, s>>>(cv); break;
+    default: k_shard_relax_cta<S, C, DIM, 8><<<cv.n_int, threads, 0, s>>>(cv); break;
   }
 }
 
@@ -315,7 +398,7 @@ __host__ __device__ inline size_t wp_smem_bytes(int W, int cap) {
          sizeof(float) * kahan_floats<DIM>() * W;
 }
 
-template <typename S, int DIM, bool ALE, bool ROW, int VPL>
+template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool SH = false>
 __global__ void __launch_bounds__(256, VPL == 4 ? 4 : 2) k_transport_wp(const CaseView cv) {
   constexpr int DD = DIM * DIM;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -328,7 +411,25 @@ __global__ void __launch_bounds__(256, VPL == 4 ? 4 : 2) k_transport_wp(const Ca
   float* s_k = s_P0 + (size_t)W * cap * DD + warp * kahan_floats<DIM>();
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
-  transport_point_wp<S, DIM, ALE, ROW, VPL, VPL == 4>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
+  transport_point_wp<S, DIM, ALE, ROW, VPL, VPL == 4, SH>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
+}
+
+// Sharded step, FP32/BF16 storage: one warp per interior point relaxes f~ in the
+// output row with the moments of the summed sums (the relaxation of k_transport_wp).
+template <typename S, int DIM, bool ROW>
+__global__ void __launch_bounds__(256) k_shard_relax_wp(const CaseView cv) {
+  __shared__ float s_vall[8 * 64];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* s_v = s_vall + warp * 64;
+  const int t = blockIdx.x * W + warp;
+  if (t >= cv.n_int) return;
+  for (int q = lane; q < cv.nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  __syncwarp();
+  const int i = cv.int_idx[t];
+  float tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = (float)cv.xs[(int64_t)i * (DIM + 2) + q];
+  relax_point<S, DIM, ROW, 4, true>(cv, i, s_v, tot);
 }
 
 // Fixed points with a mirror-symmetric velocity grid (nv % 4 == 0, NV % 8 == 0): one
@@ -465,7 +566,15 @@ int launch_transport(const CaseView& cv, cudaStream_t s) {
 // walls
 // ---------------------------------------------------------------------------
 // The per-wall-point body (one CTA), shared by the single-case and batched kernels.
-template <typename S, typename C, int DIM>
+// PH = 0: the whole step.  The sharded step splits it around the sum over all slabs:
+// PH = 1 writes the arriving half and the wall sums of the slab to cv.xs[w][2 dim + 6]
+//   [0] sum_{arriving} |c_n| g   [1] sum_{leaving} c_n M_w   [2, dim + 4) moment sums of
+//   the arriving half   [dim + 4, 2 dim + 6) moment sums of M_w over the leaving half;
+// PH = 2 reads the summed cv.xs, writes rho_w M_w to the leaving half and the moments.
+template <int DIM>
+__host__ __device__ constexpr int wall_sums() { return 2 * DIM + 6; }
+
+template <typename S, typename C, int DIM, int PH = 0>
 __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, unsigned char* smem) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   double* s_red = reinterpret_cast<double*>(smem);
@@ -474,7 +583,8 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   C* s_r = reinterpret_cast<C*>(smem + RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)));
   const int b = cv.wall_idx[w];
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
-  if (threadIdx.x < 32) {
+  const int vk0 = PH ? cv.vk0 : 0;
+  if (PH != 2 && threadIdx.x < 32) {
     // warp 0 stages the interior neighbours in list order (ballot compaction)
     const int lane = threadIdx.x, m = cv.cnt[b];
     const int32_t* col = cv.col + (int64_t)b * cv.cap;
@@ -496,7 +606,7 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   }
   for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (C)cv.vnodes[t];
   __syncthreads();
-  const int mi = s_j[0];
+  const int mi = PH != 2 ? s_j[0] : 0;
   const int64_t rowlen = (int64_t)NC * NVp;
   S* f = reinterpret_cast<S*>(cv.f_out);
   S* fb = f + (int64_t)b * rowlen;
@@ -505,64 +615,118 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   const int kb = cv.kind[b];
   const int mrow = kb == cv.lid_wall ? 1 : (cv.body_wall > 0 && kb == cv.body_wall ? 2 : 0);
   const C* Mw = reinterpret_cast<const C*>(cv.mw) + (int64_t)mrow * NVp;
+  const C cT = (C)cv.wall_T;
 
-  C flux[1] = {(C)0};
-  C part[DIM + 2];
+  // flux[0]: sum |c_n| g over the arriving half; flux[1] (PH 1): sum c_n M_w over the
+  // leaving half; part: moment sums of the arriving half (PH 0: of the whole row);
+  // unit (PH 1): moment sums of M_w over the leaving half
+  C flux[2] = {(C)0, (C)0};
+  C part[DIM + 2], unit[DIM + 2];
 #pragma unroll
-  for (int t = 0; t < DIM + 2; ++t) part[t] = (C)0;
-  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
-    if (cls[k] == 0) {
-      C g[NC];
+  for (int t = 0; t < DIM + 2; ++t) { part[t] = (C)0; unit[t] = (C)0; }
+  if (PH != 2) {
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+      if (cls[k] == 0) {
+        C g[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) g[c] = (C)0;
-      for (int s = 0; s < mi; ++s) {
-        const S* fj = f + (int64_t)s_j[1 + s] * rowlen;
-        const C r = s_r[s];
+        for (int c = 0; c < NC; ++c) g[c] = (C)0;
+        for (int s = 0; s < mi; ++s) {
+          const S* fj = f + (int64_t)s_j[1 + s] * rowlen;
+          const C r = s_r[s];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) g[c] += r * ld1(fj + (int64_t)c * NVp + k);
+          for (int c = 0; c < NC; ++c) g[c] += r * ld1(fj + (int64_t)c * NVp + k);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) st1(fb + (int64_t)c * NVp + k, g[c]);
+        flux[0] += vn[k] * g[0];
+        int kk = k + vk0;
+        C v2 = (C)0;
+        part[0] += g[0];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const C va = s_v[kk % nv];
+          kk /= nv;
+          part[1 + a] += va * g[0];
+          v2 += va * va;
+        }
+        part[DIM + 1] += v2 * g[0];
+        if (NC == 2) part[DIM + 1] += g[NC - 1];
+      } else if (PH == 1) {
+        const C m0 = Mw[k];
+        flux[1] += vn[k] * m0;
+        int kk = k + vk0;
+        C v2 = (C)0;
+        unit[0] += m0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const C va = s_v[kk % nv];
+          kk /= nv;
+          unit[1 + a] += va * m0;
+          v2 += va * va;
+        }
+        unit[DIM + 1] += v2 * m0;
+        if (NC == 2) unit[DIM + 1] += cT * m0;
       }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) st1(fb + (int64_t)c * NVp + k, g[c]);
-      flux[0] += vn[k] * g[0];
-      int kk = k;
-      C v2 = (C)0;
-      part[0] += g[0];
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const C va = s_v[kk % nv];
-        kk /= nv;
-        part[1 + a] += va * g[0];
-        v2 += va * va;
-      }
-      part[DIM + 1] += v2 * g[0];
-      if (NC == 2) part[DIM + 1] += g[NC - 1];
     }
   }
-  double ftot[1];
-  block_sum0<1, C>(flux, ftot, s_red);
-  const double rho_w = ftot[0] * cv.winv[w];
-  const C crw = (C)rho_w, cT = (C)cv.wall_T;
+  if constexpr (PH == 1) {
+    double t1[DIM + 4], t2[DIM + 2];
+    C v1[DIM + 4];
+    v1[0] = flux[0];
+    v1[1] = flux[1];
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) v1[2 + q] = part[q];
+    block_sum0<DIM + 4, C>(v1, t1, s_red);
+    block_sum0<DIM + 2, C>(unit, t2, s_red);
+    if (threadIdx.x == 0) {
+      double* xw = cv.xs + (int64_t)w * wall_sums<DIM>();
+#pragma unroll
+      for (int q = 0; q < DIM + 4; ++q) xw[q] = t1[q];
+#pragma unroll
+      for (int q = 0; q < DIM + 2; ++q) xw[DIM + 4 + q] = t2[q];
+    }
+    return;
+  }
+  double rho_w;
+  if constexpr (PH == 2) {
+    const double* xw = cv.xs + (int64_t)w * wall_sums<DIM>();
+    rho_w = xw[0] / xw[1];
+  } else {
+    double ftot[1];
+    const C f1[1] = {flux[0]};
+    block_sum0<1, C>(f1, ftot, s_red);
+    rho_w = ftot[0] * cv.winv[w];
+  }
+  const C crw = (C)rho_w;
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
     if (cls[k] != 0) {
       const C g0 = crw * Mw[k];
       st1(fb + k, g0);
       if (NC == 2) st1(fb + NVp + k, cT * g0);
-      int kk = k;
-      C v2 = (C)0;
-      part[0] += g0;
+      if (PH == 0) {
+        int kk = k;
+        C v2 = (C)0;
+        part[0] += g0;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const C va = s_v[kk % nv];
-        kk /= nv;
-        part[1 + a] += va * g0;
-        v2 += va * va;
+        for (int a = 0; a < DIM; ++a) {
+          const C va = s_v[kk % nv];
+          kk /= nv;
+          part[1 + a] += va * g0;
+          v2 += va * va;
+        }
+        part[DIM + 1] += v2 * g0;
+        if (NC == 2) part[DIM + 1] += cT * g0;
       }
-      part[DIM + 1] += v2 * g0;
-      if (NC == 2) part[DIM + 1] += cT * g0;
     }
   }
   double tot[DIM + 2];
-  block_sum0<DIM + 2, C>(part, tot, s_red);
+  if constexpr (PH == 2) {
+    const double* xw = cv.xs + (int64_t)w * wall_sums<DIM>();
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) tot[q] = xw[2 + q] + rho_w * xw[DIM + 4 + q];
+  } else {
+    block_sum0<DIM + 2, C>(part, tot, s_red);
+  }
   if (threadIdx.x == 0) {
     double rho, Un[3] = {0, 0, 0}, T;
     const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
@@ -573,10 +737,10 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   }
 }
 
-template <typename S, typename C, int DIM>
+template <typename S, typename C, int DIM, int PH = 0>
 __global__ void __launch_bounds__(256) k_walls(const CaseView cv) {
   extern __shared__ __align__(16) unsigned char smem[];
-  walls_point<S, C, DIM>(cv, blockIdx.x, smem);
+  walls_point<S, C, DIM, PH>(cv, blockIdx.x, smem);
 }
 
 // witems[k] = (case, wall slot): one CTA per wall point of any case
@@ -669,7 +833,7 @@ __global__ void k_wall_tables(CaseView cv) {
     int8_t cl = 0;
     double avn = 0.0;
     if (k < NV) {
-      int kk = k;
+      int kk = k + cv.vk0;
       double vn = 0.0, c2 = 0.0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
@@ -692,8 +856,11 @@ __global__ void k_wall_tables(CaseView cv) {
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) s += s_sum[q];
+    // a velocity slab of a sharded case holds part of this sum (its wall step takes
+    // the sum over all slabs instead): no check there
+    const bool slab = cv.vk0 != 0 || NV != (DIM == 2 ? nv * nv : nv * nv * nv);
     cv.winv[w] = s > 0.0 ? 1.0 / s : 0.0;
-    if (!(s > 0.0)) set_status(cv.status, ST_SINGULAR);
+    if (!(s > 0.0) && !slab) set_status(cv.status, ST_SINGULAR);
   }
 }
 
@@ -708,7 +875,7 @@ __global__ void k_mw_table(CaseView cv) {
     const double* uw = row == 0 ? zero : (row == 1 ? cv.lid_u : cv.body_u);
     double M = 0.0;
     if (k < cv.NV) {
-      int kk = k;
+      int kk = k + cv.vk0;
       double c2 = 0.0;
       for (int a = 0; a < DIM; ++a) {
         const double c = cv.vnodes[kk % cv.nv] - uw[a];
@@ -823,7 +990,7 @@ __global__ void k_set_maxwellian(CaseView cv, double rho0, double u0, double u1,
   double M = 0.0;
   if (k < cv.NV) {
     const double U[3] = {u0, u1, u2};
-    int kk = k;
+    int kk = k + cv.vk0;
     double c2 = 0.0;
     for (int a = 0; a < DIM; ++a) {
       const double c = cv.vnodes[kk % cv.nv] - U[a];
@@ -853,8 +1020,9 @@ int launch_set_maxwellian(const CaseView& cv, double rho0, const double* u0, dou
   return 1;
 }
 
-// Moments of every point of f (internal layout), one CTA per point.
-template <typename S, typename C, int DIM>
+// Moments of every point of f (internal layout), one CTA per point.  SH: the raw sums
+// of the velocity slab to the exchange buffer instead.
+template <typename S, typename C, int DIM, bool SH = false>
 __global__ void k_moments(CaseView cv, const S* f) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   __shared__ double s_red[8 * 32];
@@ -866,7 +1034,7 @@ __global__ void k_moments(CaseView cv, const S* f) {
   for (int t = 0; t < DIM + 2; ++t) part[t] = (C)0;
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
     const C g = ld1(fi + k);
-    int kk = k;
+    int kk = k + (SH ? cv.vk0 : 0);
     C v2 = (C)0;
     part[0] += g;
 #pragma unroll
@@ -881,7 +1049,10 @@ __global__ void k_moments(CaseView cv, const S* f) {
   }
   double tot[DIM + 2];
   block_sum0<DIM + 2, C>(part, tot, s_red);
-  if (threadIdx.x == 0) {
+  if (SH && threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = tot[q];
+  } else if (threadIdx.x == 0) {
     double rho, Un[3] = {0, 0, 0}, T;
     const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
@@ -894,7 +1065,7 @@ __global__ void k_moments(CaseView cv, const S* f) {
 // (16-byte loads, velocity nodes staged in shared memory as FP32), the lanes'
 // Kahan-compensated FP32 sums added by warp shuffles as in the transport kernel, the
 // moments finished in FP64.
-template <typename S, int DIM, bool ROW>
+template <typename S, int DIM, bool ROW, bool SH = false>
 __global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
   constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4;
   __shared__ float s_v[64];
@@ -904,6 +1075,7 @@ __global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
   const int i = blockIdx.x * W + (threadIdx.x >> 5);
   if (i >= cv.n) return;
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const int vk0 = SH ? cv.vk0 : 0;
   const float inv_nv = 1.0f / (float)nv;
   const S* fi = f + (int64_t)i * NC * NVp;
   float msum[DIM + 2], mcmp[DIM + 2];
@@ -913,7 +1085,7 @@ __global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
     const int k0 = chunk * VPL;
     float vel[VPL][DIM];
     bool kin[VPL];
-    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    chunk_velocities<DIM, VPL, ROW>(k0 + vk0, nv, NV + vk0, inv_nv, s_v, vel, kin);
     float g[NC][VPL];
 #pragma unroll
     for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, g[c]);
@@ -941,7 +1113,10 @@ __global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
   double tot[DIM + 2];
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) tot[q] = (double)warp_sum(msum[q] - mcmp[q]);
-  if (lane == 0) {
+  if (SH && lane == 0) {
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = tot[q];
+  } else if (lane == 0) {
     double rho, Un[3] = {0, 0, 0}, T;
     const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
@@ -968,6 +1143,151 @@ int launch_moments(const CaseView& cv, const void* f, cudaStream_t s) {
     else BGK_MOM_WP(__nv_bfloat16, 3)
   }
 #undef BGK_MOM_WP
+  return 1;
+}
+
+// ---------------------------------------------------------------------------
+// velocity-sharded step: slabs of the velocity grid, each advanced by the kernels
+// above with its velocity offset; the slabs couple only through the sums in cv.xs
+// ---------------------------------------------------------------------------
+template <typename S, int DIM>
+static void launch_shard_transport_wp(const CaseView& cv, cudaStream_t s) {
+  const int W = 8, threads = 32 * W;
+  const size_t smem = wp_smem_bytes<DIM>(W, cv.cap);
+  const int grid = (cv.n_int + W - 1) / W;
+  const bool row4 = cv.nv % 4 == 0;
+#define BGK_LAUNCH_SH(ALE, ROW)                                                           \
+  {                                                                                       \
+    auto k = k_transport_wp<S, DIM, ALE, ROW, 4, true>;                                   \
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+    k<<<grid, threads, smem, s>>>(cv);                                                    \
+  }
+  if (cv.ale) {
+    if (row4) BGK_LAUNCH_SH(true, true) else BGK_LAUNCH_SH(true, false)
+  } else {
+    if (row4) BGK_LAUNCH_SH(false, true) else BGK_LAUNCH_SH(false, false)
+  }
+#undef BGK_LAUNCH_SH
+}
+
+int launch_shard_transport(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_int == 0) return 0;
+  if (cv.dim == 2) {
+    if (cv.storage == 0) launch_transport_d<double, double, 2, true>(cv, s);
+    else if (cv.storage == 1) launch_shard_transport_wp<float, 2>(cv, s);
+    else launch_shard_transport_wp<__nv_bfloat16, 2>(cv, s);
+  } else {
+    if (cv.storage == 0) launch_transport_d<double, double, 3, true>(cv, s);
+    else if (cv.storage == 1) launch_shard_transport_wp<float, 3>(cv, s);
+    else launch_shard_transport_wp<__nv_bfloat16, 3>(cv, s);
+  }
+  return 1;
+}
+
+template <typename S, int DIM>
+static void launch_shard_relax_wp(const CaseView& cv, cudaStream_t s) {
+  const int W = 8, grid = (cv.n_int + W - 1) / W;
+  if (cv.nv % 4 == 0) k_shard_relax_wp<S, DIM, true><<<grid, 32 * W, 0, s>>>(cv);
+  else k_shard_relax_wp<S, DIM, false><<<grid, 32 * W, 0, s>>>(cv);
+}
+
+int launch_shard_relax(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_int == 0) return 0;
+  if (cv.dim == 2) {
+    if (cv.storage == 0) launch_shard_relax_d<double, double, 2>(cv, s);
+    else if (cv.storage == 1) launch_shard_relax_wp<float, 2>(cv, s);
+    else launch_shard_relax_wp<__nv_bfloat16, 2>(cv, s);
+  } else {
+    if (cv.storage == 0) launch_shard_relax_d<double, double, 3>(cv, s);
+    else if (cv.storage == 1) launch_shard_relax_wp<float, 3>(cv, s);
+    else launch_shard_relax_wp<__nv_bfloat16, 3>(cv, s);
+  }
+  return 1;
+}
+
+int launch_shard_walls(const CaseView& cv, int phase, cudaStream_t s) {
+  if (cv.n_wall == 0) return 0;
+  const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)) + sizeof(double) * cv.cap;
+#define BGK_WALLS_PH(S, C, D)                                                          \
+  {                                                                                    \
+    if (phase == 1) k_walls<S, C, D, 1><<<cv.n_wall, 256, smem, s>>>(cv);              \
+    else k_walls<S, C, D, 2><<<cv.n_wall, 256, smem, s>>>(cv);                         \
+  }
+  if (cv.dim == 2) {
+    if (cv.storage == 0) BGK_WALLS_PH(double, double, 2)
+    else if (cv.storage == 1) BGK_WALLS_PH(float, float, 2)
+    else BGK_WALLS_PH(__nv_bfloat16, float, 2)
+  } else {
+    if (cv.storage == 0) BGK_WALLS_PH(double, double, 3)
+    else if (cv.storage == 1) BGK_WALLS_PH(float, float, 3)
+    else BGK_WALLS_PH(__nv_bfloat16, float, 3)
+  }
+#undef BGK_WALLS_PH
+  return 1;
+}
+
+int launch_shard_partial(const CaseView& cv, cudaStream_t s) {
+  const int W = 8, grid = (cv.n + W - 1) / W;
+  const bool row = cv.nv % 4 == 0;
+#define BGK_PART_WP(S, D)                                                                                   \
+  {                                                                                                         \
+    if (row) k_moments_wp<S, D, true, true><<<grid, 32 * W, 0, s>>>(cv, (const S*)cv.f_in);                 \
+    else k_moments_wp<S, D, false, true><<<grid, 32 * W, 0, s>>>(cv, (const S*)cv.f_in);                    \
+  }
+  if (cv.dim == 2) {
+    if (cv.storage == 0) k_moments<double, double, 2, true><<<cv.n, 256, 0, s>>>(cv, (const double*)cv.f_in);
+    else if (cv.storage == 1) BGK_PART_WP(float, 2)
+    else BGK_PART_WP(__nv_bfloat16, 2)
+  } else {
+    if (cv.storage == 0) k_moments<double, double, 3, true><<<cv.n, 256, 0, s>>>(cv, (const double*)cv.f_in);
+    else if (cv.storage == 1) BGK_PART_WP(float, 3)
+    else BGK_PART_WP(__nv_bfloat16, 3)
+  }
+#undef BGK_PART_WP
+  return 1;
+}
+
+template <int DIM>
+__global__ void k_shard_moments(CaseView cv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cv.n) return;
+  double tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = cv.xs[(int64_t)i * (DIM + 2) + q];
+  double rho, Un[3] = {0, 0, 0}, T;
+  const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+  finish_moments<DIM>(tot, wv, &rho, Un, &T);
+  double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
+  mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
+}
+
+int launch_shard_moments(const CaseView& cv, cudaStream_t s) {
+  if (cv.dim == 2) k_shard_moments<2><<<grid_for(cv.n, 256), 256, 0, s>>>(cv);
+  else k_shard_moments<3><<<grid_for(cv.n, 256), 256, 0, s>>>(cv);
+  return 1;
+}
+
+// One-device stand-in for the allreduce of the slabs' sums: every element is summed
+// over the buffers in buffer order and the sum is written to every buffer, so that
+// all slabs continue from the same bits.
+struct ShardBufs {
+  double* p[SHARD_MAX_BUFS];
+};
+
+__global__ void k_shard_allreduce(ShardBufs b, int nb, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    for (int r = 0; r < nb; ++r) sum += b.p[r][e];
+    for (int r = 0; r < nb; ++r) b.p[r][e] = sum;
+  }
+}
+
+int launch_shard_allreduce(double* const* bufs, int nbufs, int64_t count, cudaStream_t s) {
+  if (count <= 0) return 0;
+  ShardBufs b;
+  for (int r = 0; r < SHARD_MAX_BUFS; ++r) b.p[r] = r < nbufs ? bufs[r] : nullptr;
+  const int64_t blocks = (count + 255) / 256;
+  k_shard_allreduce<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(b, nbufs, count);
   return 1;
 }
 

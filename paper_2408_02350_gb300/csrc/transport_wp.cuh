@@ -162,22 +162,21 @@ __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const
   }
 }
 
-// Moments of f~_i (warp totals of the lanes' compensated sums; every lane gets them),
+// Moments of f~_i from the raw sums tot = (sum g, sum v g, sum |v|^2 g (+ sum h)),
 // tau and the Maxwellian, then the relaxation pass over the output row:
-// f^{n+1} = (tau f~ + dt M)/(tau + dt).  All 32 lanes of the warp take part.
-template <typename S, int DIM, bool ROW, int VPL>
-__device__ __forceinline__ void finish_point(const CaseView& cv, const int i, const float* s_v,
-                                             const float (&msum)[DIM + 2], const float (&mcmp)[DIM + 2]) {
+// f^{n+1} = (tau f~ + dt M)/(tau + dt).  All 32 lanes of the warp take part, each
+// with the same tot.  SH: the row holds the velocity slab that starts at cv.vk0.
+template <typename S, int DIM, bool ROW, int VPL, bool SH = false>
+__device__ __forceinline__ void relax_point(const CaseView& cv, const int i, const float* s_v,
+                                            const float (&tot)[DIM + 2]) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   const int lane = threadIdx.x & 31;
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const int vk0 = SH ? cv.vk0 : 0;
   const float inv_nv = 1.0f / (float)nv;
   const int nchunk = NVp / VPL;
   const int nslice = (nchunk + 31) >> 5;
   S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * NC * NVp;
-  float tot[DIM + 2];
-#pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
   const float R = tot[0];
   float Un[DIM], u2 = 0.0f;
 #pragma unroll
@@ -209,7 +208,7 @@ __device__ __forceinline__ void finish_point(const CaseView& cv, const int i, co
     const int k0 = VPL * chunk;
     float vel[VPL][DIM];
     bool kin[VPL];
-    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    chunk_velocities<DIM, VPL, ROW>(k0 + vk0, nv, NV + vk0, inv_nv, s_v, vel, kin);
     float ft[NC][VPL], out[NC][VPL];
 #pragma unroll
     for (int c = 0; c < NC; ++c) ldv<S, VPL>(fo + (int64_t)c * NVp + k0, ft[c]);
@@ -230,6 +229,31 @@ __device__ __forceinline__ void finish_point(const CaseView& cv, const int i, co
   }
 }
 
+// Moments of f~_i (warp totals of the lanes' compensated sums; every lane gets them)
+// and the relaxation of the output row.
+template <typename S, int DIM, bool ROW, int VPL>
+__device__ __forceinline__ void finish_point(const CaseView& cv, const int i, const float* s_v,
+                                             const float (&msum)[DIM + 2], const float (&mcmp)[DIM + 2]) {
+  float tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
+  relax_point<S, DIM, ROW, VPL>(cv, i, s_v, tot);
+}
+
+// Sharded step: the raw moment sums of f~_i over the slab (warp totals of the lanes'
+// compensated sums) to row i of the exchange buffer, in double.
+template <int DIM>
+__device__ __forceinline__ void partial_out(const CaseView& cv, const int i, const float (&msum)[DIM + 2],
+                                            const float (&mcmp)[DIM + 2]) {
+  float tot[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = (double)tot[q];
+  }
+}
+
 // The per-point body, shared by the single-case kernel and the batched kernel:
 // one warp, point i of case cv; s_v, s_col, s_P, s_k are this warp's shared buffers
 // (nv, cap, cap * dim^2 and kahan_floats(DIM) entries).  Each lane owns VPL
@@ -238,11 +262,13 @@ __device__ __forceinline__ void finish_point(const CaseView& cv, const int i, co
 // recomputed after the neighbour loop, which keeps the 4-velocity body within 64
 // registers (4 CTAs of 8 warps per SM: 0.432 against 0.465 ms at 3 CTAs on the
 // 201^2 x 32^2 ALE cavity); without KS they stay in registers (the 8-velocity 3D
-// body and the batched kernel, which lose with KS).
+// body and the batched kernel, which lose with KS).  SH (sharded step): the row holds
+// the velocity slab that starts at cv.vk0, and the slab's moment sums of f~ go to the
+// exchange buffer instead of the relaxation.
 template <int DIM>
 __host__ __device__ constexpr int kahan_floats() { return 2 * (DIM + 2) * 32; }
 
-template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool KS>
+template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool KS, bool SH = false>
 __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
                                                    float* s_P, float* s_k) {
   constexpr int NC = DIM == 2 ? 2 : 1;
@@ -250,6 +276,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
   constexpr int NP = VPL / 2;  // velocity pairs per lane
   const int lane = threadIdx.x & 31;
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const int vk0 = SH ? cv.vk0 : 0;
   const float inv_nv = 1.0f / (float)nv;
   const int m = cv.cnt[i];
   for (int q = lane; q < nv; q += 32) s_v[q] = (float)cv.vnodes[q];
@@ -288,7 +315,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
     float acc[NC][VPL], sk[VPL];
     float vel[VPL][DIM];
     bool kin[VPL];
-    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    chunk_velocities<DIM, VPL, ROW>(k0 + vk0, nv, NV + vk0, inv_nv, s_v, vel, kin);
     {
     const S* fj0 = fbase + k0;
     if (ROW) {
@@ -381,7 +408,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
     }
     if (KS) {
       // the velocities again (not held in registers across the neighbour loop)
-      chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+      chunk_velocities<DIM, VPL, ROW>(k0 + vk0, nv, NV + vk0, inv_nv, s_v, vel, kin);
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
     }
@@ -395,7 +422,8 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
 #pragma unroll
     for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
   }
-  finish_point<S, DIM, ROW, VPL>(cv, i, s_v, rsum, rcmp);
+  if constexpr (SH) partial_out<DIM>(cv, i, rsum, rcmp);
+  else finish_point<S, DIM, ROW, VPL>(cv, i, s_v, rsum, rcmp);
 }
 
 // Fixed points (the transport uses c = v): a velocity v and its mirror -v, which the

@@ -1,0 +1,202 @@
+"""Rank logic of the velocity-sharded step on CPU: the slab split, and two gloo ranks
+driving ``ShardedSolver`` through ``TorchExchange`` (a real allreduce) with a CPU slab
+built from the oracle's pieces.  The assembled slabs must reproduce the oracle's
+unsharded run: the decomposition (sums over each slab's velocities, summed over the
+ranks, then the relaxation, the wall density rho_w and the wall moments from the
+totals) is the method's step with its velocity sums regrouped.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_velocity_slabs_cover_the_grid_with_aligned_starts():
+    from paper_2408_02350_gb300.sharded import velocity_slabs
+    for NV in (4, 16, 36, 125, 1024, 8000):
+        for parts in range(1, min(9, -(-NV // 4)) + 1):
+            sl = velocity_slabs(NV, parts)
+            assert len(sl) == parts and sl[0][0] == 0 and sl[-1][1] == NV
+            sizes = [hi - lo for lo, hi in sl]
+            assert all(lo % 4 == 0 for lo, _ in sl) and min(sizes) > 0
+            assert all(sl[r][1] == sl[r + 1][0] for r in range(parts - 1))
+            assert max(sizes[:-1] or [0]) - min(sizes[:-1] or [0]) <= 4
+    with pytest.raises(ValueError):
+        velocity_slabs(16, 5)
+
+
+class OracleSlab:
+    """One rank's slab of the sharded step in FP64 on the CPU, from the oracle's pieces
+    (neighbours, stencils, transport, Maxwellian, tau, motion) and plain sums over the
+    slab's velocities; it has the methods and buffers ``ShardedSolver`` drives."""
+
+    def __init__(self, p, cl, lo, hi):
+        import torch
+        import oracle
+        self.o = oracle
+        self.p = dict(p)
+        self.lo, self.hi = lo, hi
+        self.x = np.array(cl["x"], dtype=np.float64, order="C")
+        self.kind = np.array(cl["kind"], dtype=np.int32)
+        self.normal = np.array(cl["normal"], dtype=np.float64)
+        self.dim = dim = p["dim"]
+        self.nc = 2 if dim == 2 else 1
+        self.NV = p["nv"] ** dim
+        self.vel = oracle.velocity_grid(dim, p["nv"], p["vmax"])[lo:hi]
+        self.wv = oracle.dv(p["nv"], p["vmax"]) ** dim
+        self.n = len(self.kind)
+        self.wall = np.where(self.kind != 0)[0]
+        self.inner = np.where(self.kind == 0)[0]
+        self.xm = torch.zeros(self.n * (dim + 2), dtype=torch.float64)
+        self.xw = torch.zeros(len(self.wall) * (2 * dim + 6), dtype=torch.float64)
+        self.rho, self.U, self.T = np.zeros(self.n), np.zeros((self.n, dim)), np.zeros(self.n)
+        self.lists = None
+
+    def _sums(self, g):
+        """Raw sums (sum g1, sum v g1, sum |v|^2 g1 (+ sum g2)) over the slab, rows of g."""
+        v2 = (self.vel ** 2).sum(1)
+        E = g[:, 0] @ v2 + (g[:, 1].sum(1) if self.nc == 2 else 0.0)
+        return np.column_stack([g[:, 0].sum(1), g[:, 0] @ self.vel, E])
+
+    def _finish(self, t):
+        d = self.dim
+        R = t[:, 0]
+        U = t[:, 1:1 + d] / R[:, None]
+        T = (t[:, d + 1] - R * (U * U).sum(1)) / (3.0 * R)
+        return R * self.wv, U, T
+
+    def _uw(self, b):
+        u = np.zeros(self.dim)
+        if self.kind[b] == self.p.get("lid_wall", 0):
+            u[:] = self.p["lid_u"][: self.dim]
+        if self.p.get("body_wall", 0) > 0 and self.kind[b] == self.p["body_wall"]:
+            u[:] = self.p["body_u"][: self.dim]
+        return u
+
+    def set_maxwellian(self, rho0, u0, T0, stream=None):
+        M = self.o.maxwellian(self.p, rho0, u0, T0)[:, self.lo:self.hi]
+        self.f = np.broadcast_to(M, (self.n,) + M.shape).copy()
+
+    def partial(self, stream=None):
+        self.xm.numpy()[:] = self._sums(self.f).ravel()
+
+    def set_moments(self, stream=None):
+        self.rho, self.U, self.T = self._finish(self.xm.numpy().reshape(self.n, -1))
+
+    def transport(self, stream=None):
+        if self.lists is None or self.p["ale"]:
+            cnt, col = self.o.neighbours(self.x, self.p["h"], False, self.p["max_nbrs"])
+            self.lists = (cnt, col, self.o.stencils(self.p, self.x, self.kind, cnt, col))
+        cnt, col, st = self.lists
+        full = np.zeros((self.n, self.nc, self.NV))
+        full[:, :, self.lo:self.hi] = self.f
+        self.ft = self.o.transport(self.p, self.kind, cnt, col, st, self.U, full)[:, :, self.lo:self.hi]
+        xm = self.xm.numpy().reshape(self.n, -1)
+        xm[self.inner] = self._sums(self.ft[self.inner])
+
+    def relax(self, stream=None):
+        d, dt = self.dim, self.p["dt"]
+        rho, U, T = self._finish(self.xm.numpy().reshape(self.n, -1)[self.inner])
+        fn = self.f.copy()
+        for a, i in enumerate(self.inner):
+            tau = self.o.tau(self.p, rho[a], T[a])
+            M = self.o.maxwellian(self.p, rho[a], U[a], T[a])[:, self.lo:self.hi]
+            fn[i] = (tau * self.ft[i] + dt * M) / (tau + dt)
+        self.rho[self.inner], self.U[self.inner], self.T[self.inner] = rho, U, T
+        cnt, col, st = self.lists
+        xw = self.xw.numpy().reshape(len(self.wall), -1)
+        self.parts = []
+        for w, b in enumerate(self.wall):
+            uw = self._uw(b)
+            # c_n = (v - u_w).n term by term without a fused multiply-add (a BLAS dot
+            # may fuse), as the oracle does: at a 45-degree corner c_n is exactly 0 for
+            # v_x = v_y, and a fused sum would move those velocities to the leaving half
+            cn = np.zeros(len(self.vel))
+            for a in range(self.dim):
+                cn = cn + (self.vel[:, a] - uw[a]) * self.normal[b, a]
+            arr = cn <= 0.0
+            Mw = self.o.maxwellian(self.p, 1.0, uw, self.p["wall_T"])[:, self.lo:self.hi]
+            g = np.zeros((self.nc, self.hi - self.lo))
+            for s in range(cnt[b]):
+                j = col[b, s]
+                if self.kind[j] == 0:
+                    g += st["recon"][b, s] * fn[j]
+            g[:, ~arr] = 0.0
+            fn[b][:, arr] = g[:, arr]
+            Ml = np.where(arr, 0.0, Mw)
+            xw[w, 0] = (-cn[arr] * g[0, arr]).sum()
+            xw[w, 1] = (cn[~arr] * Mw[0, ~arr]).sum()
+            xw[w, 2:d + 4] = self._sums(g[None])[0]
+            xw[w, d + 4:] = self._sums(Ml[None])[0]
+            self.parts.append((arr, Mw))
+        self.fn = fn
+
+    def walls(self, stream=None):
+        d = self.dim
+        xw = self.xw.numpy().reshape(len(self.wall), -1)
+        for w, b in enumerate(self.wall):
+            arr, Mw = self.parts[w]
+            rho_w = xw[w, 0] / xw[w, 1]
+            self.fn[b][:, ~arr] = rho_w * Mw[:, ~arr]
+            rho, U, T = self._finish((xw[w, 2:d + 4] + rho_w * xw[w, d + 4:])[None])
+            self.rho[b], self.U[b], self.T[b] = rho[0], U[0], T[0]
+        self.f = self.fn
+        if self.p["ale"]:
+            self.o.move(self.p, self.kind, self.U, self.x)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, name, over, steps, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bgk_inputs as bi
+    from paper_2408_02350_gb300.sharded import ShardedSolver, TorchExchange, velocity_slabs
+    from test_sharded_ranks import OracleSlab
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p = bi.config(name, **over)
+    cl = bi.cloud_for(p)
+    lo, hi = velocity_slabs(p["nv"] ** p["dim"], world)[rank]
+    s = ShardedSolver([OracleSlab(p, cl, lo, hi)], TorchExchange())
+    s.set_maxwellian()
+    s.step(steps)
+    sl = s.slabs[0]
+    out[rank] = (lo, hi, sl.f.copy(), sl.rho.copy(), sl.U.copy(), sl.T.copy(), sl.x.copy())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name,over,steps", [
+    ("cavity2d_n41_v16_f64", dict(n=9, nv=6, vmax=3.0), 3),
+    ("cavity2d_ale_n201_v32_f32", dict(n=9, nv=6, vmax=3.0, storage="f64"), 3),
+    ("body2d_ale_n201_v32_f32", dict(n=13, nv=4, vmax=3.0, storage="f64", body_radius=0.12,
+                                     body_centre=[0.45, 0.5, 0.0]), 2),
+    ("cavity3d_n41_v16_f32", dict(n=5, nv=4, vmax=3.0, storage="f64"), 2)])
+def test_two_gloo_ranks_reproduce_the_unsharded_oracle(name, over, steps):
+    sys.path.insert(0, ROOT)
+    import bgk_inputs as bi
+    import oracle
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_worker, args=(world, port, name, over, steps, out), nprocs=world, join=True)
+    p = bi.config(name, **over)
+    sim = oracle.Simulation(p, bi.cloud_for(p))
+    sim.run(steps)
+    f = np.concatenate([out[r][2] for r in range(world)], axis=2)
+    assert out[0][1] == out[1][0] and out[1][1] == sim.f.shape[2]
+    assert np.abs(f - sim.f).max() <= 1e-12 * np.abs(sim.f).max()
+    for r in range(world):
+        _, _, _, rho, U, T, x = out[r]
+        assert np.abs(rho - sim.rho).max() <= 1e-12 and np.abs(T - sim.T).max() <= 1e-12
+        assert np.abs(U - sim.U).max() <= 1e-12 and np.abs(x - sim.x).max() <= 1e-14
