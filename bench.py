@@ -403,6 +403,87 @@ def run_reference(args, p: dict) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_sharded(args, p: dict, rank: int, world: int, local_rank: int) -> None:
+    """One cavity split over the ranks by velocity slabs, the sums exchanged by an NCCL
+    allreduce twice a step (strong scaling: the same cavity for every rank count)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2408_02350_gb300 as g
+    from paper_2408_02350_gb300.sharded import ShardedSolver
+
+    torch.cuda.set_device(local_rank)
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ.setdefault("MASTER_PORT", "29517")
+    dist.init_process_group("nccl", rank=rank, world_size=world)
+    stream = torch.cuda.current_stream()
+    cl = bi.cloud_for(p)
+    n = cl["x"].shape[0]
+    dim, NV = p["dim"], p["nv"] ** p["dim"]
+    s = ShardedSolver.distributed(p, cl)
+    sl = s.slabs[0]
+    s.set_maxwellian(stream=stream)
+    s.step(args.warmup, stream=stream)
+    s.sync(stream)
+
+    def barrier():
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = g.bgk_get_stats(sl.ctx)["launches"]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps, stream=stream)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    s.sync(stream)
+    launches = g.bgk_get_stats(sl.ctx)["launches"] - launches0
+    value = n * NV * args.steps / (ms * 1e-3)
+
+    # end to end: this rank's slab of f from pinned host memory, the moments refreshed
+    # (partial sums, allreduce), one step, the moments read back
+    ncomp = 2 if dim == 2 else 1
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[p["storage"]]
+    code = {"f64": 0, "f32": 1, "bf16": 2}[p["storage"]]
+    f_host = torch.empty((n, ncomp, sl.hi - sl.lo), dtype=tdt, pin_memory=True)
+    g.bgk_get_f(sl.ctx, 0, f_host, code, stream)
+    mom = [torch.empty(n, dtype=torch.float64, pin_memory=True),
+           torch.empty((n, dim), dtype=torch.float64, pin_memory=True),
+           torch.empty(n, dtype=torch.float64, pin_memory=True)]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.bgk_set_f(sl.ctx, 0, f_host, code, stream)
+        s.refresh_moments(stream)
+        s.step(1, stream=stream)
+        g.bgk_moments(sl.ctx, 0, *mom, stream)
+    barrier()
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    s.sync(stream)
+    if rank == 0:
+        xbytes = 8 * (sl.xm.numel() + sl.xw.numel())
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": p["storage"], "data": "synthetic",
+                "config": {"workload": args.workload, "points": n, "velocities": NV, "dim": dim,
+                           "kn": p["kn"], "ale": bool(p["ale"]), "storage": p["storage"],
+                           "parallelism": "velocity slabs, one per rank; NCCL allreduce of %d bytes twice a step"
+                                          % xbytes,
+                           "l2": "inputs larger than L2 (f %.0f MB per buffer over all ranks)"
+                                 % (f_host.numel() * f_host.element_size() * world / 1e6)},
+                "clocks": clk, "gpu_launches": launches,
+                "e2e": {"value": n * NV * args.e2e_steps / e2e_s, "unit": UNIT,
+                        "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
+                        "d2h_bytes_per_step": n * (dim + 2) * 8, "steps": args.e2e_steps}}
+        print(json.dumps(line), flush=True)
+    s.close()
+    dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,8 +500,16 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-cavity batched measurement")
     ap.add_argument("--no-manage", action="store_true", help="skip the point-management measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the Kn sweep and the FP64 41^2 cavity")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one cavity split over the ranks by velocity slabs (strong scaling)")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
+    if args.sharded and args.impl == "ours":
+        q = bi.config(args.workload, **({"n": args.n} if args.n else {}))
+        if args.storage:
+            q["storage"] = args.storage
+        run_sharded(args, q, rank, world, local_rank)
+        return
     p = rank_config(bi.config(args.workload, **({"n": args.n} if args.n else {})), rank, world)
     if args.storage:
         p["storage"] = args.storage
