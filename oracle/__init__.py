@@ -56,7 +56,7 @@ class Params(C.Structure):
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
         ("guard", C.c_double), ("lid_u", C.c_double * 3),
         ("body_wall", C.c_int32), ("wls_order", C.c_int32), ("body_u", C.c_double * 3),
-        ("body_c", C.c_double * 3), ("body_r", C.c_double),
+        ("body_c", C.c_double * 3), ("body_r", C.c_double), ("time_order", C.c_int32), ("pad2_", C.c_int32),
     ]
 
 
@@ -79,6 +79,7 @@ def params(p: dict) -> Params:
         q.body_c[a] = float(bc[a])
     q.body_r = float(p.get("body_radius", 0.0))
     q.wls_order = int(p.get("wls_order", 1))
+    q.time_order = int(p.get("time_order", 1))
     return q
 
 
@@ -109,6 +110,7 @@ def lib():
                 "or_transport": (None, [_PP, C.c_int64, _PI, _PI, _PI, _PD, _PD, _PD, _PD, _PD]),
                 "or_moments": (None, [_PP, C.c_int64, _PD, _PD, _PD, _PD]),
                 "or_relax": (None, [_PP, C.c_int64, _PI, _PD, _PD, _PD, _PD, _PD]),
+                "or_relax_exact": (None, [_PP, C.c_int64, _PI, _PD, C.c_double]),
                 "or_transport_relax_points": (None, [_PP, C.c_int64, _PL, _PI, _PI, _PD, _PD, _PD, _PD, _PD, _PD]),
                 "or_boundary": (C.c_int, [_PP, C.c_int64, _PI, _PD, _PI, _PI, _PD, _PD, _PD, _PD, _PD]),
                 "or_move": (C.c_int64, [_PP, C.c_int64, _PI, _PD, _PD]),
@@ -288,6 +290,14 @@ def transport_relax_points(p: dict, idx, cnt, col, st: dict, U, f):
     lib().or_transport_relax_points(C.byref(q), len(idx), idx.ctypes.data_as(_PL), _i(_i32(cnt)), _i(_i32(col)),
                                     _d(_f64(st["abar"])), _d(_f64(st["frame"])), _d(_f64(U)), _d(f), _d(out), _d(mom))
     return out, mom[:, 0], mom[:, 1:1 + dim], mom[:, 1 + dim]
+
+
+def relax_exact(p: dict, kind, f, h: float) -> None:
+    """In place on f: the exact relaxation over a time h at every interior point,
+    f = M + (f - M) exp(-h / tau) with M, tau from the moments of f."""
+    q = params(p)
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    lib().or_relax_exact(C.byref(q), f.shape[0], _i(_i32(kind)), _d(f), float(h))
 
 
 def boundary(p: dict, kind, normal, cnt, col, st: dict, f, rho, U, T) -> int:

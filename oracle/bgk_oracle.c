@@ -70,6 +70,12 @@ typedef struct {
   double body_u[3];
   double body_c[3];
   double body_r;
+  /* time discretisation: 0 or 1 the paper's first-order splitting (Sec. 3.2: explicit
+   * transport, implicit relaxation); 2 a second-order variant the paper leaves to future
+   * work: Strang splitting R(dt/2) T(dt) R(dt/2) with the exact relaxation solve and the
+   * transport advanced by two explicit stages (SSP-RK2, Heun); fixed points only */
+  int32_t time_order;
+  int32_t pad2_;
 } or_params;
 
 enum { OR_OK = 0, OR_E_OVERFLOW = 1, OR_E_SINGULAR = 2, OR_E_INVAL = 3, OR_E_NOMEM = 4 };
@@ -824,6 +830,33 @@ void or_transport_relax_points(const or_params* p, int64_t nidx, const int64_t* 
   free(vel); free(ft); free(M);
 }
 
+/* ---- second-order time discretisation (time_order = 2) ---- */
+
+/* Exact solution of the relaxation df/dt = (M - f)/tau over a time h at one point.  The
+ * relaxation keeps rho, U and T (and so M and tau), hence f(h) = M + (f - M) e^{-h/tau}
+ * with M and tau from the moments of f.  The moments of f go to rho, U[dim], T. */
+static void relax_exact_point(const or_params* p, double* fi, double h, double* M, double* rho, double* U,
+                              double* T) {
+  int64_t row = ncomp_of(p->dim) * nvel_of(p->dim, p->nv);
+  or_moments_point(p, fi, rho, U, T);
+  if (p->tau_mode == 2) return;
+  double tau = or_tau(p, *rho, *T);
+  double e = exp(-h / tau);
+  or_maxwellian(p, *rho, U, *T, M);
+  for (int64_t q = 0; q < row; ++q) fi[q] = M[q] + (fi[q] - M[q]) * e;
+}
+
+/* The exact relaxation over h at every interior point, in place. */
+void or_relax_exact(const or_params* p, int64_t n, const int32_t* kind, double* f, double h) {
+  int dim = p->dim;
+  int64_t row = ncomp_of(dim) * nvel_of(dim, p->nv);
+  double* M = (double*)malloc(sizeof(double) * row);
+  double rho, U[3], T;
+  for (int64_t i = 0; i < n; ++i)
+    if (kind[i] == 0) relax_exact_point(p, f + i * row, h, M, &rho, U, &T);
+  free(M);
+}
+
 /* ---- diffuse-reflection walls (Sec. 5.1, 5.2; Table 3) ---- */
 
 /* At every wall point, with c_n = (v - u_w).n the normal velocity relative to the
@@ -1165,15 +1198,42 @@ int or_run(or_params* p, int64_t n, double* x, const int32_t* kind, const double
   double* frame = (double*)malloc(sizeof(double) * n * cap * dim * dim);
   double* recon = (double*)malloc(sizeof(double) * n * cap);
   double* ft = (double*)malloc(sizeof(double) * n * row);
+  const int second = p->time_order == 2;
+  double* f2 = second ? (double*)malloc(sizeof(double) * n * row) : NULL;
+  double* mom2 = second ? (double*)malloc(sizeof(double) * n * (dim + 2)) : NULL;
   int status = OR_OK;
-  if (!cnt || !col || !coef || !abar || !frame || !recon || !ft) { status = OR_E_NOMEM; goto done; }
+  if (!cnt || !col || !coef || !abar || !frame || !recon || !ft || (second && (!f2 || !mom2))) {
+    status = OR_E_NOMEM;
+    goto done;
+  }
+  if (second && p->ale) { status = OR_E_INVAL; goto done; }
   for (int32_t s = 0; s < nsteps; ++s) {
     if (s == 0 || p->ale) {
       if (or_neighbours_cells(dim, n, x, p->h, p->periodic, cap, cnt, col) < 0) { status = OR_E_OVERFLOW; goto done; }
       if ((status = or_stencils(p, n, x, kind, cnt, col, coef, abar, frame, recon)) != OR_OK) goto done;
     }
-    or_transport(p, n, kind, cnt, col, abar, frame, U, f, ft);
-    or_relax(p, n, kind, ft, f, rho, U, T);
+    if (second) {
+      /* f^{n+1} = R(dt/2) T(dt) R(dt/2) f^n; T by two explicit stages with the walls applied
+       * to each stage, f^T = (f + T1(T1 f))/2 with T1 the first-order transport */
+      or_relax_exact(p, n, kind, f, 0.5 * p->dt);
+      or_transport(p, n, kind, cnt, col, abar, frame, U, f, ft);
+      if (!p->periodic)
+        if ((status = or_boundary(p, n, kind, normal, cnt, col, recon, ft, mom2, mom2 + n, mom2 + n * (1 + dim))) !=
+            OR_OK)
+          goto done;
+      or_transport(p, n, kind, cnt, col, abar, frame, U, ft, f2);
+      double* M = (double*)malloc(sizeof(double) * row);
+      for (int64_t i = 0; i < n; ++i) {
+        if (kind[i] != 0) continue;
+        double* fi = f + i * row;
+        for (int64_t q = 0; q < row; ++q) fi[q] = 0.5 * (fi[q] + f2[i * row + q]);
+        relax_exact_point(p, fi, 0.5 * p->dt, M, rho + i, U + i * dim, T + i);
+      }
+      free(M);
+    } else {
+      or_transport(p, n, kind, cnt, col, abar, frame, U, f, ft);
+      or_relax(p, n, kind, ft, f, rho, U, T);
+    }
     if (!p->periodic)
       if ((status = or_boundary(p, n, kind, normal, cnt, col, recon, f, rho, U, T)) != OR_OK) goto done;
     if (p->ale) {
@@ -1182,6 +1242,6 @@ int or_run(or_params* p, int64_t n, double* x, const int32_t* kind, const double
     }
   }
 done:
-  free(cnt); free(col); free(coef); free(abar); free(frame); free(recon); free(ft);
+  free(cnt); free(col); free(coef); free(abar); free(frame); free(recon); free(ft); free(f2); free(mom2);
   return status;
 }
