@@ -327,7 +327,8 @@ def sharded_rate(torch, stream, p: dict, parts: int, steps: int) -> dict:
 def extra_configs(g, torch, stream, workload: str) -> dict:
     """The ALE workload over its Kn sweep and with the second-order WLS stencils, the same
     cavity with a moving disc (plain and with point management), the plain FP64 41^2 x
-    16^2 cavity, the 3D 41^3 x 16^3 cavity (FP32) and the workload in velocity slabs."""
+    16^2 cavity, the 3D 41^3 x 16^3 cavity (FP32), the workload with fixed points (first- and
+    second-order steps) and the workload in velocity slabs."""
     out = {}
     p = bi.config(workload)
     if p.get("ale"):
@@ -340,6 +341,10 @@ def extra_configs(g, torch, stream, workload: str) -> dict:
     out["body2d_ale_n201_v32_f32_managed"] = body_managed(g, torch, stream)
     out["cavity2d_n41_v16_f64"] = _rate(g, torch, stream, bi.config("cavity2d_n41_v16_f64"), 100)
     out["cavity3d_n41_v16_f32"] = _rate(g, torch, stream, bi.config("cavity3d_n41_v16_f32"), 10)
+    # the same cavity with fixed points, with the paper's first-order step and with the
+    # second-order time discretisation (time_order = 2)
+    out[workload + "_fixed"] = _rate(g, torch, stream, bi.config(workload, ale=0), 100)
+    out[workload + "_fixed_time_order2"] = _rate(g, torch, stream, bi.config(workload, ale=0, time_order=2), 50)
     # the workload through the velocity-sharded step: one slab (the split's own cost
     # against the fused step) and 4 slabs sharing this GPU
     out[workload + "_sharded"] = {str(k): sharded_rate(torch, stream, p, k, 100) for k in (1, 4)}

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 6
+#define BGK_ABI_VERSION 7
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -112,6 +112,16 @@ typedef struct bgk_params {
    * the whole grid.  vk_lo must be a multiple of 4.  Fixed at bgk_init. */
   int32_t vk_lo;
   int32_t vk_hi;
+  /* Time discretisation.  0 or 1: the paper's first-order splitting (Sec. 3.2: explicit
+   * upwind transport, implicit relaxation).  2: a second-order variant, which the paper
+   * leaves to future work (Sec. 6): Strang splitting f^{n+1} = R(dt/2) T(dt) R(dt/2) f^n
+   * with the relaxation solved exactly (it keeps rho, U and T, so R(h) f = M + (f - M)
+   * exp(-h / tau)) and T two explicit transport stages (Heun):
+   * f^T = (f + T1(T1 f)) / 2 with T1 the first-order transport and the walls applied to
+   * each stage.  Needs ale = 0; not with bgk_shard_*, the batched modes or the adjoint.
+   * Fixed at bgk_init. */
+  int32_t time_order;
+  int32_t pad3_;
 } bgk_params;
 
 typedef struct bgk_stats {

@@ -44,7 +44,7 @@ class bgk_params(C.Structure):
         ("spare_points", C.c_int32), ("pad2_", C.c_int32),
         ("body_wall", C.c_int32), ("wls_order", C.c_int32), ("body_u", C.c_double * 3),
         ("body_centre", C.c_double * 3), ("body_radius", C.c_double),
-        ("vk_lo", C.c_int32), ("vk_hi", C.c_int32),
+        ("vk_lo", C.c_int32), ("vk_hi", C.c_int32), ("time_order", C.c_int32), ("pad3_", C.c_int32),
     ]
 
 
@@ -388,6 +388,7 @@ def params_from(p: dict) -> bgk_params:
     q.body_radius = float(p.get("body_radius", 0.0))
     q.wls_order = int(p.get("wls_order", 1))
     q.vk_lo, q.vk_hi = int(p.get("vk_lo", 0)), int(p.get("vk_hi", 0))
+    q.time_order = int(p.get("time_order", 1))
     return q
 
 

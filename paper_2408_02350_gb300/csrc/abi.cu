@@ -174,6 +174,8 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
   if (p.nv < 2 || p.nv > 64) { *why = "nv must be in [2, 64]"; return 0; }
   int64_t NV = p.dim == 2 ? (int64_t)p.nv * p.nv : (int64_t)p.nv * p.nv * p.nv;
   if (NV > 8192) { *why = "nv^dim must be <= 8192"; return 0; }
+  if (p.time_order < 0 || p.time_order > 2) { *why = "time_order must be 0, 1 or 2"; return 0; }
+  if (p.time_order == 2 && p.ale) { *why = "time_order 2 needs fixed points (ale = 0)"; return 0; }
   if (p.vk_hi == 0 ? p.vk_lo != 0 : (p.vk_lo < 0 || p.vk_lo >= p.vk_hi || p.vk_hi > NV || p.vk_lo % 4 != 0)) {
     *why = "velocity slab must satisfy 0 <= vk_lo < vk_hi <= nv^dim, vk_lo % 4 == 0 (or vk_lo = vk_hi = 0)";
     return 0;
@@ -366,7 +368,7 @@ bool batch_eligible(const bgk_ctx* ctx) {
   const CaseHost& c0 = ctx->cases[0];
   if (c0.cv.dim != 2) return false;  // the batched kernels are the 2D ones
   for (const CaseHost& c : ctx->cases) {
-    if (c.slab || c.cv.ale || c.p.storage == 0 || c.p.storage != c0.p.storage || c.cv.dim != c0.cv.dim || c.cur != c0.cur)
+    if (c.slab || c.p.time_order == 2 || c.cv.ale || c.p.storage == 0 || c.p.storage != c0.p.storage || c.cv.dim != c0.cv.dim || c.cur != c0.cur)
       return false;
   }
   return true;
@@ -782,6 +784,41 @@ int bgk_get_stencils(bgk_ctx* ctx, int32_t ci, double* P, double* recon, int64_t
   return BGK_OK;
 }
 
+// One second-order step of a fixed-point case, f^{n+1} = R(dt/2) T(dt) R(dt/2) f^n, with
+// A = f[cur] and B = f[1 - cur]: R(dt/2) on A in place; T1: A -> B (no relaxation) and
+// the walls of B; T1 from B averaged with A and R(dt/2), into A; the walls of A.  The
+// result stays in A.
+static int step_second_order(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+  int st;
+  EvPair* e;
+  CaseView a = c.cv;  // f_in = A, f_out = B
+  CaseView pre = a;
+  pre.f_out = a.f_in;
+  CaseView s1 = a;
+  s1.tau_mode = 2;
+  CaseView s2 = a;
+  s2.f_in = a.f_out;
+  s2.f_out = a.f_in;
+  s2.f_avg = a.f_in;
+  if ((st = timed_begin(ctx, K_TRANSPORT, s, &e))) return st;
+  ctx->launches += launch_relax_half(pre, s);
+  ctx->launches += launch_transport(s1, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  if ((st = timed_begin(ctx, K_WALLS, s, &e))) return st;
+  ctx->launches += launch_walls(s1, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  if ((st = timed_begin(ctx, K_TRANSPORT, s, &e))) return st;
+  ctx->launches += launch_transport_avg(s2, s);
+  CKL(ctx);
+  if ((st = timed_end(ctx, e, s))) return st;
+  if ((st = timed_begin(ctx, K_WALLS, s, &e))) return st;
+  ctx->launches += launch_walls(s2, s);
+  CKL(ctx);
+  return timed_end(ctx, e, s);
+}
+
 int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
   if (!ctx || nsteps < 0) return ctx ? fail(ctx, BGK_E_INVAL, "bgk_step: nsteps < 0") : BGK_E_INVAL;
   for (const CaseHost& c : ctx->cases)
@@ -821,6 +858,10 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
         recon_chain = c.chain - 1;
       } else if (c.cv.ale || !c.stencils_valid) {
         if ((st = build_lists(ctx, c, s))) return st;
+      }
+      if (c.p.time_order == 2) {
+        if ((st = step_second_order(ctx, c, s))) return st;
+        continue;
       }
       if ((st = timed_begin(ctx, K_TRANSPORT, s, &e))) return st;
       ctx->launches += launch_transport(c.cv, s);
@@ -869,6 +910,7 @@ int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
   if ((st = shard_case(ctx, ci, xm, "bgk_shard_transport", &cp))) return st;
   CaseHost& c = *cp;
   if (c.shard_phase != 0) return fail(ctx, BGK_E_STATE, "bgk_shard_transport: the previous sharded step is not finished");
+  if (c.p.time_order == 2) return fail(ctx, BGK_E_STATE, "bgk_shard_transport: not available with time_order 2");
   cudaStream_t s = (cudaStream_t)stream;
   invalidate_batch(ctx);
   // the lists of this step, as in bgk_step
@@ -1118,7 +1160,7 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
       p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin ||
       p->spare_points != o.spare_points || p->wls_order != o.wls_order || p->body_wall != o.body_wall ||
-      p->vk_lo != o.vk_lo || p->vk_hi != o.vk_hi ||
+      p->vk_lo != o.vk_lo || p->vk_hi != o.vk_hi || p->time_order != o.time_order ||
       p->body_radius != o.body_radius ||
       p->body_centre[0] != o.body_centre[0] || p->body_centre[1] != o.body_centre[1] ||
       p->body_centre[2] != o.body_centre[2])
@@ -1240,6 +1282,7 @@ int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out
   CaseHost& c = ctx->cases[ci];
   if (c.cv.ale) return fail(ctx, BGK_E_STATE, "bgk_adjoint_step: the adjoint is for fixed points (ale = 0)");
   if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_adjoint_step: not available for a velocity slab");
+  if (c.p.time_order == 2) return fail(ctx, BGK_E_STATE, "bgk_adjoint_step: the adjoint is of the first-order step");
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   refresh_view(c);

@@ -107,6 +107,9 @@ struct CaseView {
   int32_t vk0;
   int32_t pad_vk;
   double* xs;  // exchange buffer of the current sharded phase (device, caller-owned), else null
+  // second-order step: the state at the start of the step, averaged into the second
+  // transport stage (null otherwise)
+  void* f_avg;
 };
 
 // Launchers (stream-ordered; each returns the number of kernels launched).
@@ -151,6 +154,11 @@ constexpr int SHARD_MAX_BUFS = 16;
 // reconstruction weights (nothing for FP64 storage).
 int launch_stencils(const CaseView& cv, cudaStream_t s, int part = 0);
 int launch_transport(const CaseView& cv, cudaStream_t s);
+// Second-order step (fixed points): the second transport stage, f~ averaged with the row of
+// cv.f_avg and relaxed exactly over dt/2 into f_out; and the exact relaxation over dt/2 of
+// f_out in place with the moments of its own rows (interior points).
+int launch_transport_avg(const CaseView& cv, cudaStream_t s);
+int launch_relax_half(const CaseView& cv, cudaStream_t s);
 // FP32 warp-per-point transport + relaxation (used by the adjoint's forward recomputation)
 int launch_transport_fp32(const CaseView& cv, cudaStream_t s);
 int launch_walls(const CaseView& cv, cudaStream_t s);

@@ -87,9 +87,10 @@ __device__ __forceinline__ void block_sum0(const T (&v)[NVAL], double (&out)[NVA
 // transport + moments + relaxation
 // ---------------------------------------------------------------------------
 // Moments of f~_i from the raw sums tot, tau and the Maxwellian (one thread, FP64,
-// broadcast through shared memory), then f^{n+1} = (tau f~ + dt M)/(tau + dt) for the
-// thread's chunks, written to the output row.  vk0: first grid velocity of the row.
-template <typename S, typename C, int DIM, int NCH>
+// broadcast through shared memory), then f^{n+1} = (tau f~ + dt M)/(tau + dt) (RK = 1:
+// the exact relaxation over dt/2) for the thread's chunks, written to the output row.
+// vk0: first grid velocity of the row.
+template <typename S, typename C, int DIM, int NCH, int RK = 0>
 __device__ __forceinline__ void relax_cta(const CaseView& cv, const int i, const double (&tot)[DIM + 2],
                                           const C (&ft)[NCH][DIM == 2 ? 2 : 1][4], const C* s_v, double* s_red,
                                           const int vk0) {
@@ -111,8 +112,13 @@ __device__ __forceinline__ void relax_cta(const CaseView& cv, const int i, const
     } else if (cv.tau_mode != 2) {
       const double pi = 3.14159265358979323846;
       const double tau = cv.tau_mode == 1 ? sqrt(2.0 / pi) * cv.kn : sqrt(2.0 / pi) * cv.kn / (rho * sqrt(T));
-      a = tau / (tau + cv.dt);
-      b = cv.dt / (tau + cv.dt);
+      if (RK == 1) {
+        a = exp(-0.5 * cv.dt / tau);
+        b = -expm1(-0.5 * cv.dt / tau);
+      } else {
+        a = tau / (tau + cv.dt);
+        b = cv.dt / (tau + cv.dt);
+      }
       pref = DIM == 2 ? rho / (2.0 * pi * T) : rho / pow(2.0 * pi * T, 1.5);
       inv2T = 1.0 / (2.0 * T);
     }
@@ -158,7 +164,7 @@ __device__ __forceinline__ void relax_cta(const CaseView& cv, const int i, const
   }
 }
 
-template <typename S, typename C, int DIM, int NCH, bool ALE, bool SH = false>
+template <typename S, typename C, int DIM, int NCH, bool ALE, bool SH = false, bool AVG = false>
 __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   constexpr int DD = DIM * DIM;
@@ -257,13 +263,22 @@ __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
   for (int q = 0; q < NCH; ++q) {
     const int chunk = threadIdx.x + q * blockDim.x;
     if (chunk < nchunk) {
-      C fiv[NC][4];
+      C fiv[NC][4], fav[NC][4];
 #pragma unroll
       for (int c = 0; c < NC; ++c) ld4(fi + (int64_t)c * NVp + 4 * chunk, fiv[c]);
+      if (AVG) {
+        const S* fa = reinterpret_cast<const S*>(cv.f_avg) + (int64_t)i * rowlen;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ld4(fa + (int64_t)c * NVp + 4 * chunk, fav[c]);
+      }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) ft[q][c][e] = fiv[c][e] - two_dt * (acc[q][c][e] - sk[q][e] * fiv[c][e]);
+        if (AVG) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ft[q][c][e] = (C)0.5 * (ft[q][c][e] + fav[c][e]);
+        }
         const int k = 4 * chunk + e;
         if (k < NV) {
           int kk = k + vk0;
@@ -307,13 +322,18 @@ __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
       }
     }
   } else {
-    relax_cta<S, C, DIM, NCH>(cv, i, tot, ft, s_v, s_red, 0);
+    relax_cta<S, C, DIM, NCH, AVG ? 1 : 0>(cv, i, tot, ft, s_v, s_red, 0);
   }
 }
 
-template <typename S, typename C, int DIM, int NCH, bool SH = false>
+template <typename S, typename C, int DIM, int NCH, bool SH = false, bool AVG = false>
 static void launch_transport_t(const CaseView& cv, int threads, size_t smem, cudaStream_t s) {
-  if (cv.ale) {
+  if (AVG) {
+    // the second-order step is for fixed points
+    auto k = k_transport<S, C, DIM, NCH, false, false, true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<cv.n_int, threads, smem, s>>>(cv);
+  } else if (cv.ale) {
     auto k = k_transport<S, C, DIM, NCH, true, SH>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<cv.n_int, threads, smem, s>>>(cv);
@@ -365,17 +385,70 @@ static inline void cta_shape(int NVp, int* nch, int* threads) {
   *threads = (((nchunk + q - 1) / q) + 31) / 32 * 32;
 }
 
-template <typename S, typename C, int DIM, bool SH = false>
+template <typename S, typename C, int DIM, bool SH = false, bool AVG = false>
 static void launch_transport_d(const CaseView& cv, cudaStream_t s) {
   int nch, threads;
   cta_shape(cv.NVp, &nch, &threads);
   const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * cv.cap) + sizeof(C) * cv.cap * DIM * DIM;
   switch (nch) {
-    case 1: launch_transport_t<S, C, DIM, 1, SH>(cv, threads, smem, s); break;
-    case 2: launch_transport_t<S, C, DIM, 2, SH>(cv, threads, smem, s); break;
-    case 4: launch_transport_t<S, C, DIM, 4, SH>(cv, threads, smem, s); break;
-    default: launch_transport_t<S, C, DIM, 8, SH>(cv, threads, smem, s); break;
+    case 1: launch_transport_t<S, C, DIM, 1, SH, AVG>(cv, threads, smem, s); break;
+    case 2: launch_transport_t<S, C, DIM, 2, SH, AVG>(cv, threads, smem, s); break;
+    case 4: launch_transport_t<S, C, DIM, 4, SH, AVG>(cv, threads, smem, s); break;
+    default: launch_transport_t<S, C, DIM, 8, SH, AVG>(cv, threads, smem, s); break;
   }
+}
+
+// Second-order step, FP64 storage: the exact relaxation over dt/2 of the output row of
+// each interior point in place, with the moments of that row (one CTA per point).
+template <typename S, typename C, int DIM, int NCH>
+__global__ void __launch_bounds__(256) k_relax_half_cta(const CaseView cv) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  __shared__ double s_red[8 * 32];
+  __shared__ C s_v[64];
+  const int i = cv.int_idx[blockIdx.x];
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp, nchunk = NVp >> 2;
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (C)cv.vnodes[t];
+  __syncthreads();
+  const S* fo = reinterpret_cast<const S*>(cv.f_out) + (int64_t)i * NC * NVp;
+  C ft[NCH][NC][4];
+  C part[DIM + 2];
+#pragma unroll
+  for (int t = 0; t < DIM + 2; ++t) part[t] = (C)0;
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int chunk = threadIdx.x + q * blockDim.x;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (chunk < nchunk) {
+        ld4(fo + (int64_t)c * NVp + 4 * chunk, ft[q][c]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ft[q][c][e] = (C)0;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k = 4 * chunk + e;
+      if (chunk < nchunk && k < NV) {
+        int kk = k;
+        C v2 = (C)0;
+        const C g = ft[q][0][e];
+        part[0] += g;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const C va = s_v[kk % nv];
+          kk /= nv;
+          part[1 + a] += va * g;
+          v2 += va * va;
+        }
+        part[DIM + 1] += v2 * g;
+        if (NC == 2) part[DIM + 1] += ft[q][NC - 1][e];
+      }
+    }
+  }
+  double tot[DIM + 2];
+  block_sum0<DIM + 2, C>(part, tot, s_red);
+  relax_cta<S, C, DIM, NCH, 1>(cv, i, tot, ft, s_v, s_red, 0);
 }
 
 template <typename S, typename C, int DIM>
@@ -398,7 +471,7 @@ __host__ __device__ inline size_t wp_smem_bytes(int W, int cap) {
          sizeof(float) * kahan_floats<DIM>() * W;
 }
 
-template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool SH = false>
+template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool SH = false, bool AVG = false>
 __global__ void __launch_bounds__(256, VPL == 4 ? 4 : 2) k_transport_wp(const CaseView cv) {
   constexpr int DD = DIM * DIM;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -411,7 +484,58 @@ __global__ void __launch_bounds__(256, VPL == 4 ? 4 : 2) k_transport_wp(const Ca
   float* s_k = s_P0 + (size_t)W * cap * DD + warp * kahan_floats<DIM>();
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
-  transport_point_wp<S, DIM, ALE, ROW, VPL, VPL == 4, SH>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
+  transport_point_wp<S, DIM, ALE, ROW, VPL, VPL == 4, SH, AVG>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
+}
+
+// Second-order step, FP32/BF16 storage: one warp per interior point relaxes its output
+// row exactly over dt/2 in place, with the moments of that row (compensated lane sums).
+template <typename S, int DIM, bool ROW>
+__global__ void __launch_bounds__(256) k_relax_half_wp(const CaseView cv) {
+  constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4;
+  __shared__ float s_vall[8 * 64];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* s_v = s_vall + warp * 64;
+  const int t = blockIdx.x * W + warp;
+  if (t >= cv.n_int) return;
+  for (int q = lane; q < cv.nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  __syncwarp();
+  const int i = cv.int_idx[t];
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  const float inv_nv = 1.0f / (float)nv;
+  const S* fi = reinterpret_cast<const S*>(cv.f_out) + (int64_t)i * NC * NVp;
+  float msum[DIM + 2], mcmp[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) { msum[q] = 0.0f; mcmp[q] = 0.0f; }
+  for (int chunk = lane; chunk * VPL < NVp; chunk += 32) {
+    const int k0 = chunk * VPL;
+    float vel[VPL][DIM];
+    bool kin[VPL];
+    chunk_velocities<DIM, VPL, ROW>(k0, nv, NV, inv_nv, s_v, vel, kin);
+    float g[NC][VPL];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, g[c]);
+    float ps[DIM + 2];
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < VPL; ++e) {
+      const float g0 = kin[e] ? g[0][e] : 0.0f;
+      float v2 = 0.0f;
+      ps[0] += g0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g0, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
+      ps[DIM + 1] = fmaf(v2, g0, ps[DIM + 1]);
+      if (NC == 2) ps[DIM + 1] += kin[e] ? g[NC - 1][e] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) {
+      const float y = ps[q] - mcmp[q];
+      const float tt = msum[q] + y;
+      mcmp[q] = (tt - msum[q]) - y;
+      msum[q] = tt;
+    }
+  }
+  finish_point<S, DIM, ROW, VPL, 1>(cv, i, s_v, msum, mcmp);
 }
 
 // Sharded step, FP32/BF16 storage: one warp per interior point relaxes f~ in the
@@ -544,6 +668,69 @@ int launch_transport_fp32(const CaseView& cv, cudaStream_t s) {
   } else {
     if (cv.storage == 1) launch_transport_wp<float, 3>(cv, s);
     else launch_transport_wp<__nv_bfloat16, 3>(cv, s);
+  }
+  return 1;
+}
+
+template <typename S, int DIM>
+static void launch_transport_avg_wp(const CaseView& cv, cudaStream_t s) {
+  const int W = 8, threads = 32 * W;
+  const size_t smem = wp_smem_bytes<DIM>(W, cv.cap);
+  const int grid = (cv.n_int + W - 1) / W;
+  if (cv.nv % 4 == 0) {
+    auto k = k_transport_wp<S, DIM, false, true, 4, false, true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, threads, smem, s>>>(cv);
+  } else {
+    auto k = k_transport_wp<S, DIM, false, false, 4, false, true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, threads, smem, s>>>(cv);
+  }
+}
+
+int launch_transport_avg(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_int == 0) return 0;
+  if (cv.dim == 2) {
+    if (cv.storage == 0) launch_transport_d<double, double, 2, false, true>(cv, s);
+    else if (cv.storage == 1) launch_transport_avg_wp<float, 2>(cv, s);
+    else launch_transport_avg_wp<__nv_bfloat16, 2>(cv, s);
+  } else {
+    if (cv.storage == 0) launch_transport_d<double, double, 3, false, true>(cv, s);
+    else if (cv.storage == 1) launch_transport_avg_wp<float, 3>(cv, s);
+    else launch_transport_avg_wp<__nv_bfloat16, 3>(cv, s);
+  }
+  return 1;
+}
+
+template <typename S, typename C, int DIM>
+static void launch_relax_half_d(const CaseView& cv, cudaStream_t s) {
+  int nch, threads;
+  cta_shape(cv.NVp, &nch, &threads);
+  switch (nch) {
+    case 1: k_relax_half_cta<S, C, DIM, 1><<<cv.n_int, threads, 0, s>>>(cv); break;
+    case 2: k_relax_half_cta<S, C, DIM, 2><<<cv.n_int, threads, 0, s>>>(cv); break;
+    case 4: k_relax_half_cta<S, C, DIM, 4><<<cv.n_int, threads, 0, s>>>(cv); break;
+    default: k_relax_half_cta<S, C, DIM, 8><<<cv.n_int, threads, 0, s>>>(cv); break;
+  }
+}
+
+template <typename S, int DIM>
+static void launch_relax_half_wp(const CaseView& cv, cudaStream_t s) {
+  const int W = 8, grid = (cv.n_int + W - 1) / W;
+  if (cv.nv % 4 == 0) k_relax_half_wp<S, DIM, true><<<grid, 32 * W, 0, s>>>(cv);
+  else k_relax_half_wp<S, DIM, false><<<grid, 32 * W, 0, s>>>(cv);
+}
+
+int launch_relax_half(const CaseView& cv, cudaStream_t s) {
+  if (cv.n_int == 0 || cv.tau_mode == 2) return 0;
+  if (cv.dim == 2) {
+    if (cv.storage == 0) launch_relax_half_d<double, double, 2>(cv, s);
+    else if (cv.storage == 1) launch_relax_half_wp<float, 2>(cv, s);
+    else launch_relax_half_wp<__nv_bfloat16, 2>(cv, s);
+  } else {
+    if (cv.storage == 0) launch_relax_half_d<double, double, 3>(cv, s);
+    else if (cv.storage == 1) launch_relax_half_wp<float, 3>(cv, s);
+    else launch_relax_half_wp<__nv_bfloat16, 3>(cv, s);
   }
   return 1;
 }

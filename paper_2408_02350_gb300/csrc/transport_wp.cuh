@@ -119,7 +119,9 @@ __device__ __forceinline__ void row_upwind(const float2 (&cx)[NP], const float (
 // End of a velocity slice: f~ = f_i - 2 dt (acc - sk f_i) for the lane's VPL
 // velocities, written to the output row (and to the adjoint's tape when one is
 // attached); the slice's moment sums are Kahan-added to the lane's running sums.
-template <typename S, int DIM, int NC, int VPL>
+// AVG (second stage of the two-stage transport): f~ = (f_avg,i + f~) / 2, f_avg the
+// state at the start of the step, whose row i is read before the output overwrites it.
+template <typename S, int DIM, int NC, int VPL, bool AVG = false>
 __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const int k0, const float (&vel)[VPL][DIM],
                                           const bool (&kin)[VPL], const float (&acc)[NC][VPL],
                                           const float (&sk)[VPL], const float two_dt, float (&msum)[DIM + 2],
@@ -128,9 +130,14 @@ __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const
   const int64_t rowlen = (int64_t)NC * NVp;
   const S* fi = reinterpret_cast<const S*>(cv.f_in) + (int64_t)i * rowlen;
   S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * rowlen;
-  float fiv[NC][VPL], ft[NC][VPL];
+  float fiv[NC][VPL], ft[NC][VPL], fav[NC][AVG ? VPL : 1];
 #pragma unroll
   for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, fiv[c]);
+  if constexpr (AVG) {
+    const S* fa = reinterpret_cast<const S*>(cv.f_avg) + (int64_t)i * rowlen;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ldv<S, VPL>(fa + (int64_t)c * NVp + k0, fav[c]);
+  }
   float ps[DIM + 2];
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
@@ -138,6 +145,10 @@ __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const
   for (int e = 0; e < VPL; ++e) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? fiv[c][e] - two_dt * (acc[c][e] - sk[e] * fiv[c][e]) : 0.0f;
+    if (AVG) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ft[c][e] = 0.5f * (ft[c][e] + fav[c][e]);
+    }
     const float g = ft[0][e];
     float v2 = 0.0f;
     ps[0] += g;
@@ -164,9 +175,10 @@ __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const
 
 // Moments of f~_i from the raw sums tot = (sum g, sum v g, sum |v|^2 g (+ sum h)),
 // tau and the Maxwellian, then the relaxation pass over the output row:
-// f^{n+1} = (tau f~ + dt M)/(tau + dt).  All 32 lanes of the warp take part, each
-// with the same tot.  SH: the row holds the velocity slab that starts at cv.vk0.
-template <typename S, int DIM, bool ROW, int VPL, bool SH = false>
+// f^{n+1} = (tau f~ + dt M)/(tau + dt) (RK = 1: the exact relaxation over dt/2).  All 32
+// lanes of the warp take part, each with the same tot.  SH: the row holds the velocity
+// slab that starts at cv.vk0.
+template <typename S, int DIM, bool ROW, int VPL, bool SH = false, int RK = 0>
 __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, const float* s_v,
                                             const float (&tot)[DIM + 2]) {
   constexpr int NC = DIM == 2 ? 2 : 1;
@@ -196,8 +208,14 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
   if (cv.tau_mode != 2 && rho > 0.0f && Tn > 0.0f) {
     const float kn = (float)cv.kn, dtf = (float)cv.dt;
     const float tau = cv.tau_mode == 1 ? 0.7978845608f * kn : 0.7978845608f * kn / (rho * sqrtf(Tn));
-    ca = tau / (tau + dtf);
-    cb = dtf / (tau + dtf);
+    if (RK == 1) {
+      // exact relaxation over dt/2 (the second-order step): f = e f + (1 - e) M, e = exp(-dt/(2 tau))
+      ca = expf(-0.5f * dtf / tau);
+      cb = -expm1f(-0.5f * dtf / tau);
+    } else {
+      ca = tau / (tau + dtf);
+      cb = dtf / (tau + dtf);
+    }
     const float twopiT = 6.283185307f * Tn;
     pref = cb * (DIM == 2 ? rho / twopiT : rho / (twopiT * sqrtf(twopiT)));
     nl2 = -0.5f / Tn;
@@ -231,13 +249,13 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
 
 // Moments of f~_i (warp totals of the lanes' compensated sums; every lane gets them)
 // and the relaxation of the output row.
-template <typename S, int DIM, bool ROW, int VPL>
+template <typename S, int DIM, bool ROW, int VPL, int RK = 0>
 __device__ __forceinline__ void finish_point(const CaseView& cv, const int i, const float* s_v,
                                              const float (&msum)[DIM + 2], const float (&mcmp)[DIM + 2]) {
   float tot[DIM + 2];
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
-  relax_point<S, DIM, ROW, VPL>(cv, i, s_v, tot);
+  relax_point<S, DIM, ROW, VPL, false, RK>(cv, i, s_v, tot);
 }
 
 // Sharded step: the raw moment sums of f~_i over the slab (warp totals of the lanes'
@@ -264,11 +282,12 @@ __device__ __forceinline__ void partial_out(const CaseView& cv, const int i, con
 // 201^2 x 32^2 ALE cavity); without KS they stay in registers (the 8-velocity 3D
 // body and the batched kernel, which lose with KS).  SH (sharded step): the row holds
 // the velocity slab that starts at cv.vk0, and the slab's moment sums of f~ go to the
-// exchange buffer instead of the relaxation.
+// exchange buffer instead of the relaxation.  AVG (second stage of the second-order
+// step): f~ is averaged with the row of cv.f_avg and relaxed exactly over dt/2.
 template <int DIM>
 __host__ __device__ constexpr int kahan_floats() { return 2 * (DIM + 2) * 32; }
 
-template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool KS, bool SH = false>
+template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool KS, bool SH = false, bool AVG = false>
 __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
                                                    float* s_P, float* s_k) {
   constexpr int NC = DIM == 2 ? 2 : 1;
@@ -412,7 +431,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
     }
-    slice_out<S, DIM, NC, VPL>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
+    slice_out<S, DIM, NC, VPL, AVG>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
     if (KS) {
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
@@ -423,7 +442,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
     for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
   }
   if constexpr (SH) partial_out<DIM>(cv, i, rsum, rcmp);
-  else finish_point<S, DIM, ROW, VPL>(cv, i, s_v, rsum, rcmp);
+  else finish_point<S, DIM, ROW, VPL, AVG ? 1 : 0>(cv, i, s_v, rsum, rcmp);
 }
 
 // Fixed points (the transport uses c = v): a velocity v and its mirror -v, which the

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in _declared() if not hasattr(h, n)]
     assert not missing, missing
     assert set(_declared()) <= set(lib.exported_symbols()) | {"bgk_version"}
-    assert lib.bgk_version() == 6
+    assert lib.bgk_version() == 7
 
 
 @pytest.mark.parametrize("struct", ["bgk_params", "bgk_stats"])
@@ -89,6 +89,16 @@ def test_init_rejects_bad_body_parameters(lib, change):
         lib.bgk_init([q], [len(cl["kind"])], cl["x"], cl["kind"], cl["normal"])
     assert e.value.code == lib.BGK_E_INVAL
     assert "body" in lib.bgk_last_error(None)
+
+
+@pytest.mark.parametrize("order,ale", [(3, 0), (-1, 0), (2, 1)])
+def test_init_rejects_bad_time_orders(lib, order, ale):
+    p = bi.config("cavity2d_n41_v16_f64", n=5, time_order=order, ale=ale)
+    cl = bi.cloud_for(p)
+    with pytest.raises(lib.BGKError) as e:
+        lib.bgk_init([lib.params_from(p)], [len(cl["kind"])], cl["x"], cl["kind"], cl["normal"])
+    assert e.value.code == lib.BGK_E_INVAL
+    assert "time_order" in lib.bgk_last_error(None)
 
 
 @pytest.mark.parametrize("lo,hi", [(2, 8), (8, 8), (12, 8), (0, 300), (-4, 8), (4, 0)])
