@@ -235,9 +235,10 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream);
  *   xw  [n_wall][2 dim + 6], wall points in ascending index order: sum over the
  *       arriving velocities of |c_n| g, sum over the leaving ones of c_n M_w, the
  *       moment sums of the arriving half, those of M_w over the leaving half
- * (bgk_shard_sizes gives the two lengths).  The buffers must stay valid until the
- * stream has run the call's kernels; the summed buffer must hold identical bits in
- * every slab (NCCL's allreduce and bgk_shard_allreduce both do).  Calls out of this
+ * (bgk_shard_sizes gives the two lengths; xw may be NULL when the case has no wall
+ * points).  The buffers must stay valid until the stream has run the call's kernels;
+ * the summed buffer must hold identical bits in every slab (NCCL's allreduce and
+ * bgk_shard_allreduce both do).  Calls out of this
  * order return BGK_E_STATE.  Stream-ordered.  With ale = 1 the motion and the next
  * lists run on the internal stream after bgk_shard_relax, as in bgk_step.
  * bgk_stats.steps counts the bgk_shard_walls calls of case 0. */

@@ -887,8 +887,10 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
 
 // ---- velocity-sharded step ----
 
-static int shard_case(bgk_ctx* ctx, int32_t ci, const void* buf, const char* fn, CaseHost** out) {
-  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !buf)
+// Case ci of a sharded call; buf (an exchange buffer) may be null only where the case
+// has no wall points and the buffer is the wall sums.
+static int shard_case(bgk_ctx* ctx, int32_t ci, const void* buf, bool wall_buf, const char* fn, CaseHost** out) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || (!buf && !(wall_buf && ctx->cases[ci].cv.n_wall == 0)))
     return ctx ? fail(ctx, BGK_E_INVAL, "%s: bad argument", fn) : BGK_E_INVAL;
   *out = &ctx->cases[ci];
   refresh_view(**out);
@@ -907,7 +909,7 @@ int bgk_shard_sizes(bgk_ctx* ctx, int32_t ci, int64_t* n_xm, int64_t* n_xw) {
 int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
   CaseHost* cp;
   int st;
-  if ((st = shard_case(ctx, ci, xm, "bgk_shard_transport", &cp))) return st;
+  if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_transport", &cp))) return st;
   CaseHost& c = *cp;
   if (c.shard_phase != 0) return fail(ctx, BGK_E_STATE, "bgk_shard_transport: the previous sharded step is not finished");
   if (c.p.time_order == 2) return fail(ctx, BGK_E_STATE, "bgk_shard_transport: not available with time_order 2");
@@ -936,7 +938,7 @@ int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
 int bgk_shard_relax(bgk_ctx* ctx, int32_t ci, const double* xm, double* xw, void* stream) {
   CaseHost* cp;
   int st;
-  if ((st = shard_case(ctx, ci, xm, "bgk_shard_relax", &cp))) return st;
+  if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_relax", &cp))) return st;
   CaseHost& c = *cp;
   if (!xw && c.cv.n_wall > 0) return fail(ctx, BGK_E_INVAL, "bgk_shard_relax: bad argument");
   if (c.shard_phase != 1) return fail(ctx, BGK_E_STATE, "bgk_shard_relax: call bgk_shard_transport first");
@@ -963,11 +965,7 @@ int bgk_shard_relax(bgk_ctx* ctx, int32_t ci, const double* xm, double* xw, void
 int bgk_shard_walls(bgk_ctx* ctx, int32_t ci, const double* xw, void* stream) {
   CaseHost* cp;
   int st;
-  if (ctx && ci >= 0 && ci < (int)ctx->cases.size() && !xw && ctx->cases[ci].cv.n_wall == 0) {
-    static const double none = 0.0;
-    xw = &none;  // no wall points: nothing is read
-  }
-  if ((st = shard_case(ctx, ci, xw, "bgk_shard_walls", &cp))) return st;
+  if ((st = shard_case(ctx, ci, xw, true, "bgk_shard_walls", &cp))) return st;
   CaseHost& c = *cp;
   if (c.shard_phase != 2) return fail(ctx, BGK_E_STATE, "bgk_shard_walls: call bgk_shard_relax first");
   cudaStream_t s = (cudaStream_t)stream;
@@ -989,7 +987,7 @@ int bgk_shard_walls(bgk_ctx* ctx, int32_t ci, const double* xw, void* stream) {
 int bgk_shard_partial(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
   CaseHost* cp;
   int st;
-  if ((st = shard_case(ctx, ci, xm, "bgk_shard_partial", &cp))) return st;
+  if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_partial", &cp))) return st;
   CaseView v = cp->cv;
   v.xs = xm;
   ctx->launches += launch_shard_partial(v, (cudaStream_t)stream);
@@ -1000,7 +998,7 @@ int bgk_shard_partial(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
 int bgk_shard_set_moments(bgk_ctx* ctx, int32_t ci, const double* xm, void* stream) {
   CaseHost* cp;
   int st;
-  if ((st = shard_case(ctx, ci, xm, "bgk_shard_set_moments", &cp))) return st;
+  if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_set_moments", &cp))) return st;
   CaseView v = cp->cv;
   v.xs = const_cast<double*>(xm);
   ctx->launches += launch_shard_moments(v, (cudaStream_t)stream);

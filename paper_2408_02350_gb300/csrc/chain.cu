@@ -143,6 +143,14 @@ void bounds(int dim, double r, float* lo, float* hi) {
 
 bool chain_eligible(const CaseView& cv) { return cv.ale && cv.sk && cv.storage != 0 && cv.wls_order != 2; }
 
+// CTAs per SM of the cooperative launch (0: as many as fit, 5 at 48 registers).  The
+// kernel runs beside the wall kernel; with fewer CTAs the two share the SMs instead of
+// running one after the other.  201^2 x 32^2 ALE workload, ms per step (two runs each):
+// all that fit 0.4932, 4 per SM 0.4929, 3 per SM 0.4900, 2 per SM 0.4895.
+#ifndef BGK_CHAIN_PER_SM
+#define BGK_CHAIN_PER_SM 2
+#endif
+
 int launch_chain(const CaseView& cv, int* grid_cache, long long max_spins, cudaStream_t s) {
   const size_t smem = sizeof(int32_t) * (size_t)cv.ccap * CHAIN_WARPS;
   const void* fn = cv.dim == 2 ? (const void*)k_chain<2> : (const void*)k_chain<3>;
@@ -156,6 +164,7 @@ int launch_chain(const CaseView& cv, int* grid_cache, long long max_spins, cudaS
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CHAIN_THREADS, smem) != cudaSuccess || per_sm < 1)
       return -1;
+    if (BGK_CHAIN_PER_SM > 0 && per_sm > BGK_CHAIN_PER_SM) per_sm = BGK_CHAIN_PER_SM;
     *grid_cache = nsm * per_sm;
   }
   const double half = 0.5 * cv.h * cv.skin;

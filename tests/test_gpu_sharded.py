@@ -70,6 +70,35 @@ def test_sharded_step_matches_oracle(g, dim, n, nv, ale, storage, parts, steps, 
     s.close()
 
 
+@pytest.mark.parametrize("ale", [0, 1])
+def test_sharded_periodic_box_without_walls(g, ale):
+    # no wall points: the wall exchange is empty and its buffer is passed as NULL
+    n, nv, vmax = 9, 6, 3.0
+    dx = 1.0 / n
+    p = {"dim": 2, "nv": nv, "vmax": vmax, "kn": 0.1, "tau_mode": 0, "dt": bi.cfl_dt(dx, vmax, 2), "h": 2.5 * dx,
+         "alpha": 6.25, "max_nbrs": 48, "periodic": 1, "ale": ale, "guard": 0.0, "storage": "f64"}
+    cl = bi.periodic_box(2, n, seed=4, jitter=0.1)
+    rng = np.random.default_rng(3)
+    M = oracle.maxwellian(p, 1.0, (0.1, -0.05), 1.0)
+    f0 = np.ascontiguousarray(M[None] * rng.uniform(0.9, 1.1, (n * n, 1, 1)))
+    sim = oracle.Simulation(p, cl, f0=f0)
+    sim.run(5)
+    from paper_2408_02350_gb300.sharded import ShardedSolver
+    s = ShardedSolver.on_one_device(p, cl, 3)
+    for sl in s.slabs:
+        sl.set_f(np.ascontiguousarray(f0[:, :, sl.lo:sl.hi]))
+    s.refresh_moments()
+    assert s.slabs[0].xw.numel() == 0
+    s.step(5)
+    s.sync()
+    rho, u, T = s.moments()
+    assert _rel(rho, sim.rho) < 1e-10 and _rel(T, sim.T) < 1e-10 and _rel(u, sim.U) < 1e-10
+    assert np.abs(s.get_f() - sim.f).max() < 1e-9 * np.abs(sim.f).max()
+    if ale:
+        assert np.abs(s.positions() - sim.x).max() < 1e-13
+    s.close()
+
+
 def test_sharded_moving_body_matches_oracle(g):
     # the body's rows of the wall tables with the slab's velocity offset
     p = bi.config("body2d_ale_n201_v32_f32", n=25, nv=8, vmax=3.0, storage="f64")
