@@ -23,6 +23,7 @@
  *   f          [n][ncomp][NV] with ncomp = 2 (Chu g1, g2) in 2D, 1 in 3D,
  *              NV = nv^dim, velocity index k = kx + nv*(ky + nv*kz)
  *   velocity nodes v_j = -vmax + j*dv, dv = 2 vmax / (nv - 1), j = 0..nv-1
+ *              (vgrid = 1: v_j = -vmax + (j + 1/2) dv, dv = 2 vmax / nv)
  */
 #ifndef BGK_H
 #define BGK_H
@@ -34,7 +35,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 7
+#define BGK_ABI_VERSION 8
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -121,7 +122,10 @@ typedef struct bgk_params {
    * each stage.  Needs ale = 0; not with bgk_shard_*, the batched modes or the adjoint.
    * Fixed at bgk_init. */
   int32_t time_order;
-  int32_t pad3_;
+  /* Velocity grid (Sec. 3.3): 0 the paper's nv nodes from -vmax to vmax, dv = 2 vmax /
+   * (nv - 1); 1 the midpoint grid, nv cells of width dv = 2 vmax / nv with a node at each
+   * cell centre (no node at +-vmax).  Both are symmetric about zero.  Fixed at bgk_init. */
+  int32_t vgrid;
 } bgk_params;
 
 typedef struct bgk_stats {
@@ -187,6 +191,21 @@ int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, v
  * and converted on the device); device copies are stream-ordered. */
 int bgk_set_f(bgk_ctx* ctx, int32_t c, const void* f, int32_t dtype, int32_t on_device, void* stream);
 int bgk_get_f(bgk_ctx* ctx, int32_t c, void* f, int32_t dtype, int32_t on_device, void* stream);
+
+/* Caller-owned storage for case c's distribution (no copies per step): f_dev is
+ * device memory of at least (n + spare_points) ncomp NV elements of the storage type,
+ * 16-byte aligned, layout [n][ncomp][NV]; NV must be a multiple of 4 (then the
+ * internal layout is this one).  The call copies the current state into f_dev, and
+ * from then on every call leaves the case's state in f_dev when it returns: the
+ * context's own second buffer still serves the double buffering, and a call that ends
+ * with the state there copies it into f_dev (one device copy; bgk_step with an even
+ * step count needs none).  The context never frees f_dev.  After writing into f_dev,
+ * call bgk_set_f with f_dev itself (on_device = 1, the storage type) to recompute the
+ * stored moments; nothing is copied then.  f_dev = NULL unbinds: the state goes back
+ * into the context's own buffer, and the call waits for the stream, after which the
+ * caller may free the memory.  Rebinding unbinds first.  BGK_E_INVAL for a buffer that
+ * is too small, misaligned or not device memory.  Stream-ordered except the unbinding. */
+int bgk_bind_f(bgk_ctx* ctx, int32_t c, void* f_dev, size_t bytes, void* stream);
 
 /* Rebuild cell lists, neighbour lists N(i) = {j != i : |x_j - x_i|^2 <= h^2}
  * (ascending j, FP64 without fused multiply-add) and the WLS stencils of

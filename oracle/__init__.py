@@ -56,7 +56,7 @@ class Params(C.Structure):
         ("dt", C.c_double), ("h", C.c_double), ("alpha", C.c_double), ("wall_T", C.c_double),
         ("guard", C.c_double), ("lid_u", C.c_double * 3),
         ("body_wall", C.c_int32), ("wls_order", C.c_int32), ("body_u", C.c_double * 3),
-        ("body_c", C.c_double * 3), ("body_r", C.c_double), ("time_order", C.c_int32), ("pad2_", C.c_int32),
+        ("body_c", C.c_double * 3), ("body_r", C.c_double), ("time_order", C.c_int32), ("vgrid", C.c_int32),
     ]
 
 
@@ -80,6 +80,7 @@ def params(p: dict) -> Params:
     q.body_r = float(p.get("body_radius", 0.0))
     q.wls_order = int(p.get("wls_order", 1))
     q.time_order = int(p.get("time_order", 1))
+    q.vgrid = int(p.get("vgrid", 0))
     return q
 
 
@@ -98,6 +99,9 @@ def lib():
                 "or_dv": (C.c_double, [C.c_int32, C.c_double]),
                 "or_velocity_nodes": (None, [C.c_int32, C.c_double, _PD]),
                 "or_velocity_grid": (None, [C.c_int32, C.c_int32, C.c_double, _PD]),
+                "or_dv_g": (C.c_double, [C.c_int32, C.c_double, C.c_int32]),
+                "or_velocity_nodes_g": (None, [C.c_int32, C.c_double, C.c_int32, _PD]),
+                "or_velocity_grid_g": (None, [C.c_int32, C.c_int32, C.c_double, C.c_int32, _PD]),
                 "or_tau_si": (C.c_double, [C.c_double] * 5),
                 "or_lambda_si": (C.c_double, [C.c_double] * 4),
                 "or_tau": (C.c_double, [_PP, C.c_double, C.c_double]),
@@ -157,19 +161,21 @@ def nvel(dim: int, nv: int) -> int:
 
 # ---- velocity grid (Sec. 3.3) ----
 
-def dv(nv: int, vmax: float) -> float:
-    return lib().or_dv(nv, vmax)
+def dv(nv: int, vmax: float, vgrid: int = 0) -> float:
+    """Node spacing: 2 vmax / (nv - 1) on the paper's endpoint grid, 2 vmax / nv on the
+    midpoint grid (vgrid 1)."""
+    return lib().or_dv_g(nv, vmax, vgrid)
 
 
-def velocity_nodes(nv: int, vmax: float) -> np.ndarray:
+def velocity_nodes(nv: int, vmax: float, vgrid: int = 0) -> np.ndarray:
     out = np.empty(nv)
-    lib().or_velocity_nodes(nv, vmax, _d(out))
+    lib().or_velocity_nodes_g(nv, vmax, vgrid, _d(out))
     return out
 
 
-def velocity_grid(dim: int, nv: int, vmax: float) -> np.ndarray:
+def velocity_grid(dim: int, nv: int, vmax: float, vgrid: int = 0) -> np.ndarray:
     out = np.empty((nv ** dim, dim))
-    lib().or_velocity_grid(dim, nv, vmax, _d(out))
+    lib().or_velocity_grid_g(dim, nv, vmax, vgrid, _d(out))
     return out
 
 

@@ -75,7 +75,9 @@ typedef struct {
    * work: Strang splitting R(dt/2) T(dt) R(dt/2) with the exact relaxation solve and the
    * transport advanced by two explicit stages (SSP-RK2, Heun); fixed points only */
   int32_t time_order;
-  int32_t pad2_;
+  /* velocity grid: 0 the paper's nv nodes with both ends at -vmax and vmax (Sec. 3.3),
+   * 1 the midpoint grid, nv cells of width 2 vmax / nv with a node at each centre */
+  int32_t vgrid;
 } or_params;
 
 enum { OR_OK = 0, OR_E_OVERFLOW = 1, OR_E_SINGULAR = 2, OR_E_INVAL = 3, OR_E_NOMEM = 4 };
@@ -85,21 +87,27 @@ static int64_t nvel_of(int dim, int nv) { return dim == 2 ? (int64_t)nv * nv : (
 
 /* ---- velocity grid (Sec. 3.3) ---- */
 
-double or_dv(int32_t nv, double vmax) { return 2.0 * vmax / (double)(nv - 1); }
+/* node spacing of the endpoint grid (vgrid 0) or the midpoint grid (vgrid 1) */
+double or_dv_g(int32_t nv, double vmax, int32_t vgrid) {
+  return vgrid == 1 ? 2.0 * vmax / (double)nv : 2.0 * vmax / (double)(nv - 1);
+}
+double or_dv(int32_t nv, double vmax) { return or_dv_g(nv, vmax, 0); }
 
-/* v_j = -vmax + j dv, written in the centred form (j - (nv-1)/2) dv, which is the
- * same number in exact arithmetic and makes the grid exactly symmetric in floating
- * point (v_{nv-1-j} = -v_j), so that a grazing velocity has v.n = 0 exactly on
- * axis-aligned and diagonal walls. */
-void or_velocity_nodes(int32_t nv, double vmax, double* v) {
-  double dv = or_dv(nv, vmax);
+/* Endpoint grid v_j = -vmax + j dv, midpoint grid v_j = -vmax + (j + 1/2) dv, both
+ * written in the centred form (j - (nv-1)/2) dv, which is the same number in exact
+ * arithmetic and makes the grid exactly symmetric in floating point (v_{nv-1-j} =
+ * -v_j), so that a grazing velocity has v.n = 0 exactly on axis-aligned and diagonal
+ * walls. */
+void or_velocity_nodes_g(int32_t nv, double vmax, int32_t vgrid, double* v) {
+  double dv = or_dv_g(nv, vmax, vgrid);
   for (int j = 0; j < nv; ++j) v[j] = ((double)j - 0.5 * (double)(nv - 1)) * dv;
 }
+void or_velocity_nodes(int32_t nv, double vmax, double* v) { or_velocity_nodes_g(nv, vmax, 0, v); }
 
 /* vel[k][a] for the tensor-product grid, kx fastest. */
-void or_velocity_grid(int32_t dim, int32_t nv, double vmax, double* vel) {
+void or_velocity_grid_g(int32_t dim, int32_t nv, double vmax, int32_t vgrid, double* vel) {
   double* nodes = (double*)malloc(sizeof(double) * nv);
-  or_velocity_nodes(nv, vmax, nodes);
+  or_velocity_nodes_g(nv, vmax, vgrid, nodes);
   int64_t NV = nvel_of(dim, nv);
   for (int64_t k = 0; k < NV; ++k) {
     int64_t r = k;
@@ -110,9 +118,10 @@ void or_velocity_grid(int32_t dim, int32_t nv, double vmax, double* vel) {
   }
   free(nodes);
 }
+void or_velocity_grid(int32_t dim, int32_t nv, double vmax, double* vel) { or_velocity_grid_g(dim, nv, vmax, 0, vel); }
 
 static double quad_weight(const or_params* p) {
-  double dv = or_dv(p->nv, p->vmax);
+  double dv = or_dv_g(p->nv, p->vmax, p->vgrid);
   return p->dim == 2 ? dv * dv : dv * dv * dv;
 }
 
@@ -146,7 +155,7 @@ void or_maxwellian(const or_params* p, double rho, const double* U, double T, do
   int dim = p->dim;
   int64_t NV = nvel_of(dim, p->nv);
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
-  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
   for (int64_t k = 0; k < NV; ++k) {
     double c2 = 0.0;
     for (int a = 0; a < dim; ++a) {
@@ -171,7 +180,7 @@ void or_moments_point(const or_params* p, const double* fi, double* rho, double*
   int64_t NV = nvel_of(dim, p->nv);
   double wv = quad_weight(p);
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
-  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
   double r = 0.0, mom[3] = {0.0, 0.0, 0.0};
   for (int64_t k = 0; k < NV; ++k) {
     r += fi[k] * wv;
@@ -770,7 +779,7 @@ void or_transport(const or_params* p, int64_t n, const int32_t* kind, const int3
   int dim = p->dim;
   int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
-  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
   for (int64_t i = 0; i < n; ++i) {
     if (kind[i] != 0) { memcpy(ft + i * row, f + i * row, sizeof(double) * row); continue; }
     transport_point(p, i, cnt, col, abar, frame, U, f, vel, ft + i * row);
@@ -821,7 +830,7 @@ void or_transport_relax_points(const or_params* p, int64_t nidx, const int64_t* 
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
   double* ft = (double*)malloc(sizeof(double) * row);
   double* M = (double*)malloc(sizeof(double) * row);
-  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
   for (int64_t q = 0; q < nidx; ++q) {
     double* mo = mom_out + q * (dim + 2);
     transport_point(p, idx[q], cnt, col, abar, frame, U, f, vel, ft);
@@ -874,7 +883,7 @@ int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double
   int status = OR_OK;
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
   double* Mw = (double*)malloc(sizeof(double) * row);
-  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
   for (int64_t b = 0; b < n; ++b) {
     if (kind[b] == 0) continue;
     double* fb = f + b * row;
@@ -1014,7 +1023,7 @@ int or_adjoint_step(const or_params* p, int64_t n, const int32_t* kind, const do
   double* Mw = (double*)malloc(sizeof(double) * row);
   double* M = (double*)malloc(sizeof(double) * row);
   double rho_, U_[3], T_;
-  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
 
   /* forward recomputation of the step's intermediates */
   double zero3[3] = {0.0, 0.0, 0.0};
@@ -1164,7 +1173,7 @@ double or_objective(const or_params* p, int64_t n, const int32_t* kind, const do
   int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
   double wv = quad_weight(p);
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
-  or_velocity_grid(dim, p->nv, p->vmax, vel);
+  or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
   int64_t nlid = 0;
   for (int64_t b = 0; b < n; ++b) nlid += kind[b] == p->lid_wall;
   double J = 0.0;

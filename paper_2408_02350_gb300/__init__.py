@@ -44,7 +44,7 @@ class bgk_params(C.Structure):
         ("spare_points", C.c_int32), ("pad2_", C.c_int32),
         ("body_wall", C.c_int32), ("wls_order", C.c_int32), ("body_u", C.c_double * 3),
         ("body_centre", C.c_double * 3), ("body_radius", C.c_double),
-        ("vk_lo", C.c_int32), ("vk_hi", C.c_int32), ("time_order", C.c_int32), ("pad3_", C.c_int32),
+        ("vk_lo", C.c_int32), ("vk_hi", C.c_int32), ("time_order", C.c_int32), ("vgrid", C.c_int32),
     ]
 
 
@@ -67,6 +67,7 @@ _SIGS = {
     "bgk_set_maxwellian": (C.c_int, [_P, C.c_double, _PD, C.c_double, _P]),
     "bgk_set_f": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
     "bgk_get_f": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
+    "bgk_bind_f": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, _P]),
     "bgk_neighbours": (C.c_int, [_P, _P]),
     "bgk_get_neighbours": (C.c_int, [_P, C.c_int32, _PL, _PI, C.c_int64, _PL]),
     "bgk_get_stencils": (C.c_int, [_P, C.c_int32, _PD, _PD, C.c_int64]),
@@ -196,6 +197,15 @@ def bgk_set_f(ctx, case: int, f, dtype: int, stream=None) -> None:
 
 def bgk_get_f(ctx, case: int, f, dtype: int, stream=None) -> None:
     _check(lib().bgk_get_f(ctx, case, _ptr(f), dtype, _on_device(f), _stream_ptr(stream)), ctx)
+
+
+def bgk_bind_f(ctx, case: int, f, stream=None) -> None:
+    """Use the device tensor f (contiguous, the storage dtype) as case's distribution
+    storage; None unbinds."""
+    if f is None:
+        _check(lib().bgk_bind_f(ctx, case, None, 0, _stream_ptr(stream)), ctx)
+    else:
+        _check(lib().bgk_bind_f(ctx, case, _ptr(f), f.numel() * f.element_size(), _stream_ptr(stream)), ctx)
 
 
 def bgk_neighbours(ctx, stream=None) -> None:
@@ -389,6 +399,7 @@ def params_from(p: dict) -> bgk_params:
     q.wls_order = int(p.get("wls_order", 1))
     q.vk_lo, q.vk_hi = int(p.get("vk_lo", 0)), int(p.get("vk_hi", 0))
     q.time_order = int(p.get("time_order", 1))
+    q.vgrid = int(p.get("vgrid", 0))
     return q
 
 
@@ -432,6 +443,18 @@ class Solver:
             import torch
             dt = {torch.float64: BGK_F64, torch.float32: BGK_F32, torch.bfloat16: BGK_BF16}[f.dtype]
         bgk_set_f(self.ctx, case, f, dt, stream)
+
+    def bind_f(self, f, case: int = 0, stream=None):
+        """Keep case's distribution in the device tensor f ([n + spare_points][ncomp][NV],
+        the storage dtype) from now on; f[:n] holds the state after every call.  None
+        unbinds.  The solver keeps a reference to f while it is bound."""
+        if not hasattr(self, "_bound"):
+            self._bound = {}
+        bgk_bind_f(self.ctx, case, f, stream)
+        if f is None:
+            self._bound.pop(case, None)
+        else:
+            self._bound[case] = f
 
     def get_f(self, case: int = 0, dtype=np.float64):
         d, nc, NV = self.dims(case)

@@ -56,6 +56,11 @@ struct CaseHost {
   bool slab = false;
   int shard_phase = 0;
   int64_t shard_recon = -1;
+  // caller-owned distribution storage (bgk_bind_f): it takes the place of f[bound_slot],
+  // whose own buffer is kept in own_buf for the unbinding
+  void* bound = nullptr;
+  int bound_slot = -1;
+  void* own_buf = nullptr;
   // ALE: the lists of the next step (second set of cnt, col, P, recon) are built on
   // the side stream right after the motion, while the wall kernel runs; they are
   // swapped in at the next step.  ev_fork orders the side work after the transport,
@@ -175,6 +180,7 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
   int64_t NV = p.dim == 2 ? (int64_t)p.nv * p.nv : (int64_t)p.nv * p.nv * p.nv;
   if (NV > 8192) { *why = "nv^dim must be <= 8192"; return 0; }
   if (p.time_order < 0 || p.time_order > 2) { *why = "time_order must be 0, 1 or 2"; return 0; }
+  if (p.vgrid < 0 || p.vgrid > 1) { *why = "vgrid must be 0 or 1"; return 0; }
   if (p.time_order == 2 && p.ale) { *why = "time_order 2 needs fixed points (ale = 0)"; return 0; }
   if (p.vk_hi == 0 ? p.vk_lo != 0 : (p.vk_lo < 0 || p.vk_lo >= p.vk_hi || p.vk_hi > NV || p.vk_lo % 4 != 0)) {
     *why = "velocity slab must satisfy 0 <= vk_lo < vk_hi <= nv^dim, vk_lo % 4 == 0 (or vk_lo = vk_hi = 0)";
@@ -214,6 +220,17 @@ int check_params(const bgk_params& p, int64_t n, const char** why) {
 void refresh_view(CaseHost& c) {
   c.cv.f_in = c.f[c.cur];
   c.cv.f_out = c.f[1 - c.cur];
+}
+
+// With caller-owned storage bound, a call that ends with the state in the context's own
+// buffer copies it into the caller's (one device copy of the n current rows).
+int settle_bound(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+  if (!c.bound || c.cur == c.bound_slot) return BGK_OK;
+  const size_t b = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
+  CK(ctx, cudaMemcpyAsync(c.f[c.bound_slot], c.f[c.cur], b, cudaMemcpyDeviceToDevice, s));
+  c.cur = c.bound_slot;
+  refresh_view(c);
+  return BGK_OK;
 }
 
 int timed_begin(bgk_ctx* ctx, int kid, cudaStream_t s, EvPair** out) {
@@ -527,7 +544,7 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.kn = q.kn;
     v.wall_T = q.wall_T;
     v.guard = q.guard;
-    v.dv = 2.0 * q.vmax / (double)(q.nv - 1);
+    v.dv = q.vgrid == 1 ? 2.0 * q.vmax / (double)q.nv : 2.0 * q.vmax / (double)(q.nv - 1);
     for (int a = 0; a < 3; ++a) v.lid_u[a] = q.lid_u[a];
     v.skin = q.skin;
     v.body_wall = q.body_wall;
@@ -680,7 +697,9 @@ int bgk_set_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype, int32_t on
   const size_t bytes = (size_t)c.cv.n * c.cv.ncomp * c.cv.NV * esz;
   const void* src = f;
   const bool direct = dtype == c.cv.storage && c.cv.NV == c.cv.NVp;  // same element type, no padding
-  if (!on_device && direct) {
+  if (on_device && direct && f == c.f[c.cur]) {
+    // the bound storage itself, written by the caller: only the moments are recomputed
+  } else if (!on_device && direct) {
     CK(ctx, cudaMemcpyAsync(c.f[c.cur], f, bytes, cudaMemcpyHostToDevice, s));
   } else {
     if (!on_device) {
@@ -846,6 +865,8 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
       }
       ctx->steps += 1;
     }
+    for (auto& c : ctx->cases)
+      if ((st = settle_bound(ctx, c, s))) return st;
     return BGK_OK;
   }
   for (int step = 0; step < nsteps; ++step) {
@@ -880,8 +901,10 @@ int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
     }
     ctx->steps += 1;
   }
-  for (auto& c : ctx->cases)
+  for (auto& c : ctx->cases) {
     if (c.next_ready && (st = join_side(ctx, c, s))) return st;
+    if ((st = settle_bound(ctx, c, s))) return st;
+  }
   return BGK_OK;
 }
 
@@ -979,6 +1002,7 @@ int bgk_shard_walls(bgk_ctx* ctx, int32_t ci, const double* xw, void* stream) {
   c.cur = 1 - c.cur;
   refresh_view(c);
   if (c.next_ready && (st = join_side(ctx, c, s))) return st;
+  if ((st = settle_bound(ctx, c, s))) return st;
   c.shard_phase = 0;
   if (ci == 0) ctx->steps += 1;
   return BGK_OK;
@@ -1012,6 +1036,44 @@ int bgk_shard_allreduce(double* const* bufs, int32_t nbufs, int64_t count, void*
     if (!bufs[r]) return BGK_E_INVAL;
   launch_shard_allreduce(bufs, nbufs, count, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
+}
+
+int bgk_bind_f(bgk_ctx* ctx, int32_t ci, void* f_dev, size_t bytes, void* stream) {
+  if (!ctx || ci < 0 || ci >= (int)ctx->cases.size())
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_bind_f: bad argument") : BGK_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  CaseHost& c = ctx->cases[ci];
+  const size_t rows = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
+  if (c.bound) {
+    // back to the context's own buffer, with the current state in it
+    if (c.cur == c.bound_slot) CK(ctx, cudaMemcpyAsync(c.own_buf, c.bound, rows, cudaMemcpyDeviceToDevice, s));
+    c.f[c.bound_slot] = c.own_buf;
+    c.bound = nullptr;
+    c.bound_slot = -1;
+    c.own_buf = nullptr;
+    refresh_view(c);
+    invalidate_batch(ctx);
+    CK(ctx, cudaStreamSynchronize(s));
+  }
+  if (!f_dev) return BGK_OK;
+  if (c.cv.NV != c.cv.NVp) return fail(ctx, BGK_E_INVAL, "bgk_bind_f: NV must be a multiple of 4");
+  if (reinterpret_cast<uintptr_t>(f_dev) % 16 != 0) return fail(ctx, BGK_E_INVAL, "bgk_bind_f: f_dev must be 16-byte aligned");
+  const size_t need = (size_t)c.cap_n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
+  if (bytes < need) return fail(ctx, BGK_E_INVAL, "bgk_bind_f: %zu bytes, %zu needed", bytes, need);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, f_dev) != cudaSuccess ||
+      (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+    cudaGetLastError();
+    return fail(ctx, BGK_E_INVAL, "bgk_bind_f: f_dev is not device memory");
+  }
+  CK(ctx, cudaMemcpyAsync(f_dev, c.f[c.cur], rows, cudaMemcpyDeviceToDevice, s));
+  c.own_buf = c.f[c.cur];
+  c.f[c.cur] = f_dev;
+  c.bound = f_dev;
+  c.bound_slot = c.cur;
+  refresh_view(c);
+  invalidate_batch(ctx);
+  return BGK_OK;
 }
 
 int bgk_moments(bgk_ctx* ctx, int32_t ci, double* rho, double* u, double* T, int32_t on_device, void* stream) {
@@ -1142,7 +1204,9 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
     if (int st = reset_skin(ctx, c)) return st;  // positions changed: rebuild the candidates
     c.cur = 0;
     refresh_view(c);
+    if (int st = settle_bound(ctx, c, 0)) return st;
   }
+  CK(ctx, cudaDeviceSynchronize());
   invalidate_batch(ctx);
   ctx->steps = (int64_t)hdr[3];
   return BGK_OK;
@@ -1158,7 +1222,7 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   if (p->dim != o.dim || p->nv != o.nv || p->vmax != o.vmax || p->storage != o.storage || p->max_nbrs != o.max_nbrs ||
       p->h != o.h || p->alpha != o.alpha || p->periodic != o.periodic || p->skin != o.skin ||
       p->spare_points != o.spare_points || p->wls_order != o.wls_order || p->body_wall != o.body_wall ||
-      p->vk_lo != o.vk_lo || p->vk_hi != o.vk_hi || p->time_order != o.time_order ||
+      p->vk_lo != o.vk_lo || p->vk_hi != o.vk_hi || p->time_order != o.time_order || p->vgrid != o.vgrid ||
       p->body_radius != o.body_radius ||
       p->body_centre[0] != o.body_centre[0] || p->body_centre[1] != o.body_centre[1] ||
       p->body_centre[2] != o.body_centre[2])
@@ -1257,6 +1321,8 @@ int bgk_manage(bgk_ctx* ctx, int32_t ci, double rmin, int32_t min_nbrs, int64_t*
   c.tslot_valid = false;
   if ((st = reset_skin(ctx, c))) return st;
   invalidate_batch(ctx);
+  if ((st = settle_bound(ctx, c, s))) return st;
+  CK(ctx, cudaStreamSynchronize(s));
   counts[0] = n_new;
   counts[1] = n_old - survivors;
   counts[2] = adds;

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in _declared() if not hasattr(h, n)]
     assert not missing, missing
     assert set(_declared()) <= set(lib.exported_symbols()) | {"bgk_version"}
-    assert lib.bgk_version() == 7
+    assert lib.bgk_version() == 8
 
 
 @pytest.mark.parametrize("struct", ["bgk_params", "bgk_stats"])

@@ -89,3 +89,15 @@ def test_collinear_interior_stencil_is_singular(g):
         s.sync()
     assert e.value.code == g.BGK_E_SINGULAR
     s.close()
+
+
+@pytest.mark.parametrize("dim,nv,ale,storage,tol", [
+    (2, 8, 0, "f64", 1e-10), (2, 7, 1, "f64", 1e-10), (2, 8, 1, "f32", 1e-4), (3, 6, 0, "f32", 1e-4)])
+def test_midpoint_velocity_grid(g, dim, nv, ale, storage, tol):
+    # vgrid 1: nodes at the centres of nv cells over [-vmax, vmax]
+    n = 13 if dim == 2 else 6
+    p = bi.config(_name(dim), n=n, nv=nv, vmax=3.0, storage=storage, ale=ale, vgrid=1)
+    cl = bi.cloud_for(p)
+    sim, f, rho, u, T = _run_both(g, p, cl, 6)
+    assert _rel(rho, sim.rho) < tol and _rel(T, sim.T) < tol and _rel(u, sim.U) < max(tol, 1e-12)
+    assert np.abs(f - sim.f).max() < 10 * tol * np.abs(sim.f).max()

@@ -189,3 +189,23 @@ def test_local_tau_uses_density_and_temperature():
     assert abs(t0 - math.sqrt(2 / math.pi) * 0.3) < 1e-15
     assert abs(oracle.tau(p, 2.0, 1.0) - t0 / 2) < 1e-15
     assert abs(oracle.tau(p, 1.0, 4.0) - t0 / 2) < 1e-15
+
+
+def test_midpoint_velocity_grid():
+    # vgrid 1: nv cells of width 2 vmax / nv over [-vmax, vmax], a node at each centre,
+    # exactly symmetric; the midpoint rule integrates a Maxwellian to rounding on a wide grid
+    for nv, vmax in [(16, 5.0), (17, 5.0), (2, 1.0)]:
+        v = oracle.velocity_nodes(nv, vmax, 1)
+        d = 2 * vmax / nv
+        assert abs(oracle.dv(nv, vmax, 1) - d) < 1e-15
+        assert abs(v[0] - (-vmax + d / 2)) < 1e-14 and abs(v[-1] - (vmax - d / 2)) < 1e-14
+        assert np.allclose(np.diff(v), d, rtol=0, atol=1e-14)
+        assert np.array_equal(v, -v[::-1])
+    p = _p(2, 40, 10.0, vgrid=1)
+    M = oracle.maxwellian(p, 0.8, (0.3, -0.2), 1.2)
+    rho, U, T = oracle.moments_point(p, M)
+    assert abs(rho - 0.8) < 1e-12 and np.abs(U - [0.3, -0.2]).max() < 1e-12 and abs(T - 1.2) < 1e-12
+    # the same numbers as an explicit midpoint sum
+    g = oracle.velocity_grid(2, 40, 10.0, 1)
+    assert abs(M[0].sum() * oracle.dv(40, 10.0, 1) ** 2 - 0.8) < 1e-12
+    assert np.abs(g[:40, 0] - oracle.velocity_nodes(40, 10.0, 1)).max() == 0.0
