@@ -507,15 +507,20 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the Kn sweep and the FP64 41^2 cavity")
     ap.add_argument("--sharded", action="store_true",
                     help="one cavity split over the ranks by velocity slabs (strong scaling)")
+    ap.add_argument("--time-order", type=int, default=None,
+                    help="2: the workload with fixed points and the second-order time step (profiling runs)")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
+    over = {"n": args.n} if args.n else {}
+    if args.time_order:
+        over.update(ale=0, time_order=args.time_order)
     if args.sharded and args.impl == "ours":
-        q = bi.config(args.workload, **({"n": args.n} if args.n else {}))
+        q = bi.config(args.workload, **over)
         if args.storage:
             q["storage"] = args.storage
         run_sharded(args, q, rank, world, local_rank)
         return
-    p = rank_config(bi.config(args.workload, **({"n": args.n} if args.n else {})), rank, world)
+    p = rank_config(bi.config(args.workload, **over), rank, world)
     if args.storage:
         p["storage"] = args.storage
     if args.impl == "reference":

@@ -171,3 +171,20 @@ def test_shard_allreduce_sums_in_buffer_order(g):
         want = want + h
     for b in bufs:
         assert np.array_equal(b.cpu().numpy(), want)
+
+
+def test_sharded_bf16_matches_unsharded_bf16(g):
+    # BF16 storage: the slabs round f~ and f to BF16 exactly where the fused step does,
+    # so the two agree to the BF16 step (2^-8 relative) and the moments to FP32 sums
+    p = bi.config("cavity2d_ale_n201_v32_f32", n=41, nv=8, vmax=3.0, storage="bf16")
+    cl = bi.cloud_for(p)
+    s1 = g.Solver([p], [cl])
+    s1.set_maxwellian()
+    s1.step(10)
+    s1.sync()
+    rho1, u1, T1 = s1.moments()
+    s1.close()
+    s = _sharded(g, p, cl, 3, 10)
+    rho, u, T = s.moments()
+    assert _rel(rho, rho1) < 1e-3 and _rel(T, T1) < 1e-3 and np.abs(u - u1).max() < 1e-3
+    s.close()
