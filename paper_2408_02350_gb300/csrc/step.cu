@@ -924,13 +924,157 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   }
 }
 
+// FP32/BF16 storage, the whole wall step (PH = 0 of walls_point): each thread takes 4
+// consecutive velocities, so a neighbour row costs one 16-byte (8-byte for BF16) load
+// per channel instead of four; the leaving half of the loaded values is unused.  The
+// arithmetic per velocity is that of walls_point, with FP32 block sums finished in FP64.
+template <typename S, int DIM>
+__device__ __forceinline__ void walls_point_v4(const CaseView& cv, const int w, unsigned char* smem) {
+  constexpr int NC = DIM == 2 ? 2 : 1;
+  double* s_red = reinterpret_cast<double*>(smem);
+  float* s_v = reinterpret_cast<float*>(smem + RED_BYTES);
+  int32_t* s_j = reinterpret_cast<int32_t*>(smem + RED_BYTES + NODE_BYTES);
+  float* s_r = reinterpret_cast<float*>(smem + RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)));
+  const int b = cv.wall_idx[w];
+  const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, m = cv.cnt[b];
+    const int32_t* col = cv.col + (int64_t)b * cv.cap;
+    const float* R = reinterpret_cast<const float*>(cv.recon) + (int64_t)b * cv.cap;
+    int mi = 0;
+    for (int s0 = 0; s0 < m; s0 += 32) {
+      const int s = s0 + lane;
+      const int j = s < m ? col[s] : 0;
+      const bool in = s < m && cv.kind[j] == 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int pos = mi + __popc(bal & ((1u << lane) - 1u));
+        s_j[1 + pos] = j;
+        s_r[pos] = R[s];
+      }
+      mi += __popc(bal);
+    }
+    if (lane == 0) s_j[0] = mi;
+  }
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (float)cv.vnodes[t];
+  __syncthreads();
+  const int mi = s_j[0];
+  const int64_t rowlen = (int64_t)NC * NVp;
+  S* f = reinterpret_cast<S*>(cv.f_out);
+  S* fb = f + (int64_t)b * rowlen;
+  const int8_t* cls = cv.wcls + (int64_t)w * NVp;
+  const float* vn = reinterpret_cast<const float*>(cv.wvn) + (int64_t)w * NVp;
+  const int kb = cv.kind[b];
+  const int mrow = kb == cv.lid_wall ? 1 : (cv.body_wall > 0 && kb == cv.body_wall ? 2 : 0);
+  const float* Mw = reinterpret_cast<const float*>(cv.mw) + (int64_t)mrow * NVp;
+  const float cT = (float)cv.wall_T;
+  const int nchunk = NVp >> 2;
+
+  float flux[1] = {0.0f};
+  float part[DIM + 2];
+#pragma unroll
+  for (int t = 0; t < DIM + 2; ++t) part[t] = 0.0f;
+  for (int ch = threadIdx.x; ch < nchunk; ch += blockDim.x) {
+    const int k0 = 4 * ch;
+    const char4 c4 = *reinterpret_cast<const char4*>(cls + k0);
+    const bool arr[4] = {c4.x == 0 && k0 < NV, c4.y == 0 && k0 + 1 < NV, c4.z == 0 && k0 + 2 < NV,
+                         c4.w == 0 && k0 + 3 < NV};
+    if (!(arr[0] || arr[1] || arr[2] || arr[3])) continue;
+    float g[NC][4];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) g[c][e] = 0.0f;
+    for (int s = 0; s < mi; ++s) {
+      const S* fj = f + (int64_t)s_j[1 + s] * rowlen + k0;
+      const float r = s_r[s];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float v[4];
+        ld4(fj + (int64_t)c * NVp, v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) g[c][e] += r * v[e];
+      }
+    }
+    const float4 vn4 = *reinterpret_cast<const float4*>(vn + k0);
+    const float vnv[4] = {vn4.x, vn4.y, vn4.z, vn4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (!arr[e]) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) st1(fb + (int64_t)c * NVp + k0 + e, g[c][e]);
+      flux[0] += vnv[e] * g[0][e];
+      int kk = k0 + e;
+      float v2 = 0.0f;
+      part[0] += g[0][e];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float va = s_v[kk % nv];
+        kk /= nv;
+        part[1 + a] += va * g[0][e];
+        v2 += va * va;
+      }
+      part[DIM + 1] += v2 * g[0][e];
+      if (NC == 2) part[DIM + 1] += g[NC - 1][e];
+    }
+  }
+  double ftot[1];
+  block_sum0<1, float>(flux, ftot, s_red);
+  const double rho_w = ftot[0] * cv.winv[w];
+  const float crw = (float)rho_w;
+  for (int ch = threadIdx.x; ch < nchunk; ch += blockDim.x) {
+    const int k0 = 4 * ch;
+    const char4 c4 = *reinterpret_cast<const char4*>(cls + k0);
+    const bool lv[4] = {c4.x != 0, c4.y != 0, c4.z != 0, c4.w != 0};
+    if (!(lv[0] || lv[1] || lv[2] || lv[3])) continue;
+    const float4 m4 = *reinterpret_cast<const float4*>(Mw + k0);
+    const float mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (!lv[e]) continue;
+      const float g0 = crw * mw[e];
+      st1(fb + k0 + e, g0);
+      if (NC == 2) st1(fb + NVp + k0 + e, cT * g0);
+      int kk = k0 + e;
+      float v2 = 0.0f;
+      part[0] += g0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float va = s_v[kk % nv];
+        kk /= nv;
+        part[1 + a] += va * g0;
+        v2 += va * va;
+      }
+      part[DIM + 1] += v2 * g0;
+      if (NC == 2) part[DIM + 1] += cT * g0;
+    }
+  }
+  double tot[DIM + 2];
+  block_sum0<DIM + 2, float>(part, tot, s_red);
+  if (threadIdx.x == 0) {
+    double rho, Un[3] = {0, 0, 0}, T;
+    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    finish_moments<DIM>(tot, wv, &rho, Un, &T);
+    double* mo = cv.mom + (int64_t)b * MOM_STRIDE;
+    mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
+    if (!(rho_w >= 0.0) || !isfinite(rho_w)) set_status(cv.status, ST_NONFINITE);
+  }
+}
+
+template <typename S, int DIM>
+__global__ void __launch_bounds__(256) k_walls_v4(const CaseView cv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  walls_point_v4<S, DIM>(cv, blockIdx.x, smem);
+}
+
 template <typename S, typename C, int DIM, int PH = 0>
 __global__ void __launch_bounds__(256) k_walls(const CaseView cv) {
   extern __shared__ __align__(16) unsigned char smem[];
   walls_point<S, C, DIM, PH>(cv, blockIdx.x, smem);
 }
 
-// witems[k] = (case, wall slot): one CTA per wall point of any case
+// witems[k] = (case, wall slot): one CTA per wall point of any case (2D: the body of
+// k_walls, so that batched and per-case stepping give the same bits)
 template <typename S, typename C, int DIM>
 __global__ void __launch_bounds__(256) k_walls_batch(const CaseView* __restrict__ cases, const int2* __restrict__ witems) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -978,14 +1122,18 @@ int launch_walls(const CaseView& cv, cudaStream_t s) {
   if (cv.n_wall == 0) return 0;
   const int threads = 256;
   const size_t smem = RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * (cv.cap + 1)) + sizeof(double) * cv.cap;
+  // 2D keeps the one-velocity-per-thread body: beside the side-chain kernel of an ALE step
+  // the vector body's extra registers (43 against 32) slow the chain more than they save
+  // (201^2 x 32^2 ALE cavity: 0.4925 against 0.4857 ms per step, chain 61 against 53 us);
+  // in 3D, with no side chain, the vector body wins (41^3 x 16^3: 6.45 against 6.63 ms).
   if (cv.dim == 2) {
     if (cv.storage == 0) k_walls<double, double, 2><<<cv.n_wall, threads, smem, s>>>(cv);
     else if (cv.storage == 1) k_walls<float, float, 2><<<cv.n_wall, threads, smem, s>>>(cv);
     else k_walls<__nv_bfloat16, float, 2><<<cv.n_wall, threads, smem, s>>>(cv);
   } else {
     if (cv.storage == 0) k_walls<double, double, 3><<<cv.n_wall, threads, smem, s>>>(cv);
-    else if (cv.storage == 1) k_walls<float, float, 3><<<cv.n_wall, threads, smem, s>>>(cv);
-    else k_walls<__nv_bfloat16, float, 3><<<cv.n_wall, threads, smem, s>>>(cv);
+    else if (cv.storage == 1) k_walls_v4<float, 3><<<cv.n_wall, threads, smem, s>>>(cv);
+    else k_walls_v4<__nv_bfloat16, 3><<<cv.n_wall, threads, smem, s>>>(cv);
   }
   return 1;
 }
