@@ -232,8 +232,9 @@ int bgk_get_stencils(bgk_ctx* ctx, int32_t c, double* P, double* recon, int64_t 
  * walls, and with ale = 1 the motion x^{n+1} = x^n + dt U^{n+1}.  Asynchronous:
  * with ale = 1 the motion and the next step's lists run on an internal stream
  * concurrently with the wall kernel, and every such piece of work is ordered
- * before later work on `stream` when the call returns.  BGK_E_STATE when a case
- * holds a proper velocity slab (such cases step with bgk_shard_*). */
+ * before later work on `stream` when the call returns.  A case with time_order = 2
+ * takes the second-order step described at that field instead.  BGK_E_STATE when a
+ * case holds a proper velocity slab (such cases step with bgk_shard_*). */
 int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream);
 
 /* Velocity-sharded step, not in the paper (Sec. 5 parallelises over points on one
