@@ -192,6 +192,18 @@ int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, v
 int bgk_set_f(bgk_ctx* ctx, int32_t c, const void* f, int32_t dtype, int32_t on_device, void* stream);
 int bgk_get_f(bgk_ctx* ctx, int32_t c, void* f, int32_t dtype, int32_t on_device, void* stream);
 
+/* Upload case c's distribution for the next bgk_step without waiting: f is
+ * page-locked host memory, layout [n][ncomp][NV] of the storage type (NV a multiple of
+ * 4).  The copy goes into a third device buffer on an internal stream, so it overlaps
+ * whatever runs meanwhile (the step before, typically); the next bgk_step waits for it
+ * on its stream, takes it as the state (as bgk_set_f would, moments included) and steps
+ * from it.  A second call before that step replaces the pending input; bgk_manage and
+ * bgk_set_state drop it.  f must stay unchanged until the copy has run (any call that
+ * waits for the stream after the next bgk_step ensures it).  BGK_E_STATE with bound
+ * storage (bgk_bind_f) or for a velocity slab; BGK_E_INVAL for pageable memory or
+ * another element type.  Asynchronous. */
+int bgk_stage_f(bgk_ctx* ctx, int32_t c, const void* f, int32_t dtype);
+
 /* Caller-owned storage for case c's distribution (no copies per step): f_dev is
  * device memory of at least (n + spare_points) ncomp NV elements of the storage type,
  * 16-byte aligned, layout [n][ncomp][NV]; NV must be a multiple of 4 (then the
@@ -204,7 +216,8 @@ int bgk_get_f(bgk_ctx* ctx, int32_t c, void* f, int32_t dtype, int32_t on_device
  * stored moments; nothing is copied then.  f_dev = NULL unbinds: the state goes back
  * into the context's own buffer, and the call waits for the stream, after which the
  * caller may free the memory.  Rebinding unbinds first.  BGK_E_INVAL for a buffer that
- * is too small, misaligned or not device memory.  Stream-ordered except the unbinding. */
+ * is too small, misaligned or not device memory; BGK_E_STATE while an input staged by
+ * bgk_stage_f is pending.  Stream-ordered except the unbinding. */
 int bgk_bind_f(bgk_ctx* ctx, int32_t c, void* f_dev, size_t bytes, void* stream);
 
 /* Rebuild cell lists, neighbour lists N(i) = {j != i : |x_j - x_i|^2 <= h^2}

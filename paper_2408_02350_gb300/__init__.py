@@ -68,6 +68,7 @@ _SIGS = {
     "bgk_set_f": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
     "bgk_get_f": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
     "bgk_bind_f": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, _P]),
+    "bgk_stage_f": (C.c_int, [_P, C.c_int32, _P, C.c_int32]),
     "bgk_neighbours": (C.c_int, [_P, _P]),
     "bgk_get_neighbours": (C.c_int, [_P, C.c_int32, _PL, _PI, C.c_int64, _PL]),
     "bgk_get_stencils": (C.c_int, [_P, C.c_int32, _PD, _PD, C.c_int64]),
@@ -197,6 +198,12 @@ def bgk_set_f(ctx, case: int, f, dtype: int, stream=None) -> None:
 
 def bgk_get_f(ctx, case: int, f, dtype: int, stream=None) -> None:
     _check(lib().bgk_get_f(ctx, case, _ptr(f), dtype, _on_device(f), _stream_ptr(stream)), ctx)
+
+
+def bgk_stage_f(ctx, case: int, f, dtype: int) -> None:
+    """Asynchronous upload of case's next input from page-locked host memory (a pinned
+    torch tensor); the next bgk_step takes it."""
+    _check(lib().bgk_stage_f(ctx, case, _ptr(f), dtype), ctx)
 
 
 def bgk_bind_f(ctx, case: int, f, stream=None) -> None:

@@ -61,6 +61,13 @@ struct CaseHost {
   void* bound = nullptr;
   int bound_slot = -1;
   void* own_buf = nullptr;
+  // input staged by bgk_stage_f for the next step: a third buffer filled on the copy
+  // stream (ev_staged), swapped in by the next bgk_step, whose start (ev_free) frees the
+  // buffer it replaces for the next upload
+  void* staged = nullptr;
+  bool staged_ready = false;
+  bool free_recorded = false;
+  cudaEvent_t ev_staged = nullptr, ev_free = nullptr;
   // ALE: the lists of the next step (second set of cnt, col, P, recon) are built on
   // the side stream right after the motion, while the wall kernel runs; they are
   // swapped in at the next step.  ev_fork orders the side work after the transport,
@@ -99,6 +106,7 @@ struct bgk_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
   cudaStream_t side = nullptr;  // ALE motion and next-step lists, concurrent with the wall kernel
+  cudaStream_t copy = nullptr;  // uploads of bgk_stage_f
   std::vector<void*> allocs;
   DevStatus* status = nullptr;
   std::string err;
@@ -838,12 +846,31 @@ static int step_second_order(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
   return timed_end(ctx, e, s);
 }
 
+// The input staged by bgk_stage_f becomes the state: stream s waits for its upload, the
+// buffers are swapped, the moments are taken, and ev_free marks the point after which the
+// replaced buffer (the next staging target) is no longer used.
+static int take_staged(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
+  if (!c.staged_ready) return BGK_OK;
+  CK(ctx, cudaStreamWaitEvent(s, c.ev_staged, 0));
+  std::swap(c.f[c.cur], c.staged);
+  refresh_view(c);
+  ctx->launches += launch_moments(c.cv, c.f[c.cur], s);
+  CKL(ctx);
+  CK(ctx, cudaEventRecord(c.ev_free, s));
+  c.free_recorded = true;
+  c.staged_ready = false;
+  invalidate_batch(ctx);
+  return BGK_OK;
+}
+
 int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
   if (!ctx || nsteps < 0) return ctx ? fail(ctx, BGK_E_INVAL, "bgk_step: nsteps < 0") : BGK_E_INVAL;
   for (const CaseHost& c : ctx->cases)
     if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_step: a case holds a velocity slab (step it with bgk_shard_*)");
   cudaStream_t s = (cudaStream_t)stream;
   int st;
+  for (auto& c : ctx->cases)
+    if ((st = take_staged(ctx, c, s))) return st;
   EvPair* e;
   const int mode = effective_mode(ctx);
   if (mode >= 1 && nsteps > 0) {
@@ -1038,11 +1065,40 @@ int bgk_shard_allreduce(double* const* bufs, int32_t nbufs, int64_t count, void*
   return cudaGetLastError() == cudaSuccess ? BGK_OK : BGK_E_CUDA;
 }
 
+int bgk_stage_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype) {
+  if (!ctx || !f || ci < 0 || ci >= (int)ctx->cases.size())
+    return ctx ? fail(ctx, BGK_E_INVAL, "bgk_stage_f: bad argument") : BGK_E_INVAL;
+  CaseHost& c = ctx->cases[ci];
+  if (c.bound || c.slab) return fail(ctx, BGK_E_STATE, "bgk_stage_f: not with bound storage or a velocity slab");
+  if (dtype != c.cv.storage || c.cv.NV != c.cv.NVp)
+    return fail(ctx, BGK_E_INVAL, "bgk_stage_f: dtype must be the storage type and NV a multiple of 4");
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, f) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+    cudaGetLastError();
+    return fail(ctx, BGK_E_INVAL, "bgk_stage_f: f must be page-locked host memory");
+  }
+  int st;
+  if (!ctx->copy) CK(ctx, cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+  if (!c.staged) {
+    if ((st = dalloc_bytes(ctx, &c.staged, (size_t)c.cap_n * c.cv.ncomp * c.cv.NVp * c.s_bytes))) return st;
+    CK(ctx, cudaEventCreateWithFlags(&c.ev_staged, cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&c.ev_free, cudaEventDisableTiming));
+  }
+  // the staging buffer may be the state buffer a step replaced: wait until that step began
+  if (c.free_recorded) CK(ctx, cudaStreamWaitEvent(ctx->copy, c.ev_free, 0));
+  const size_t bytes = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
+  CK(ctx, cudaMemcpyAsync(c.staged, f, bytes, cudaMemcpyHostToDevice, ctx->copy));
+  CK(ctx, cudaEventRecord(c.ev_staged, ctx->copy));
+  c.staged_ready = true;
+  return BGK_OK;
+}
+
 int bgk_bind_f(bgk_ctx* ctx, int32_t ci, void* f_dev, size_t bytes, void* stream) {
   if (!ctx || ci < 0 || ci >= (int)ctx->cases.size())
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_bind_f: bad argument") : BGK_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CaseHost& c = ctx->cases[ci];
+  if (c.staged_ready) return fail(ctx, BGK_E_STATE, "bgk_bind_f: an input staged by bgk_stage_f is pending");
   const size_t rows = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
   if (c.bound) {
     // back to the context's own buffer, with the current state in it
@@ -1201,6 +1257,7 @@ int bgk_set_state(bgk_ctx* ctx, const void* blob, size_t size) {
     o += 3 * sizeof(double);
     c.stencils_valid = false;
     c.shard_phase = 0;
+    c.staged_ready = false;
     if (int st = reset_skin(ctx, c)) return st;  // positions changed: rebuild the candidates
     c.cur = 0;
     refresh_view(c);
@@ -1261,6 +1318,7 @@ int bgk_manage(bgk_ctx* ctx, int32_t ci, double rmin, int32_t min_nbrs, int64_t*
   cudaStream_t s = (cudaStream_t)stream;
   CaseHost& c = ctx->cases[ci];
   if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_manage: not available for a velocity slab");
+  c.staged_ready = false;  // a pending staged input has the old point count: dropped
   int st;
   if ((st = join_side(ctx, c, s))) return st;
   refresh_view(c);
@@ -1493,8 +1551,11 @@ void bgk_free(bgk_ctx* ctx) {
   drop_graphs(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->copy) cudaStreamDestroy(ctx->copy);
   for (auto& c : ctx->cases) {
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+    if (c.ev_staged) cudaEventDestroy(c.ev_staged);
+    if (c.ev_free) cudaEventDestroy(c.ev_free);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
     for (int k = 0; k < 2; ++k)
       if (c.ev_recon[k]) cudaEventDestroy(c.ev_recon[k]);

@@ -125,3 +125,36 @@ def test_bind_rejects_bad_buffers(g):
     with pytest.raises(g.BGKError):
         s.bind_f(torch.zeros((len(cl["kind"]), 2, 28), dtype=torch.float64, device="cuda"))
     s.close()
+
+
+@pytest.mark.parametrize("ale", [0, 1])
+def test_staged_inputs_equal_set_f(g, ale):
+    # bgk_stage_f uploads on another stream and the next step takes the input: the same
+    # bits as bgk_set_f followed by the step, for a new input every step
+    import torch
+    p = bi.config("cavity2d_n41_v16_f64", n=15, nv=8, vmax=3.0, storage="f32", ale=ale)
+    cl = bi.cloud_for(p)
+    n = len(cl["kind"])
+    gen = g.Solver([p], [cl])
+    gen.set_maxwellian()
+    a, b = g.Solver([p], [cl]), g.Solver([p], [cl])
+    for k in range(4):
+        gen.step(2)
+        f_in = torch.from_numpy(gen.get_f(0, np.float32)).pin_memory()
+        a.set_f(f_in)
+        a.step(1)
+        g.bgk_stage_f(b.ctx, 0, f_in, g.BGK_F32)
+        b.step(1)
+        b.sync()
+        assert np.array_equal(b.get_f(0, np.float64), a.get_f(0, np.float64)), k
+        for x, y in zip(b.moments(), a.moments()):
+            assert np.array_equal(x, y)
+    with pytest.raises(g.BGKError):  # pageable host memory
+        g.bgk_stage_f(b.ctx, 0, np.zeros((n, 2, 64), np.float32), g.BGK_F32)
+    g.bgk_stage_f(b.ctx, 0, f_in, g.BGK_F32)
+    with pytest.raises(g.BGKError):  # binding while an input is pending
+        b.bind_f(torch.zeros((n, 2, 64), dtype=torch.float32, device="cuda"))
+    b.step(1)
+    b.sync()
+    for x in (gen, a, b):
+        x.close()
