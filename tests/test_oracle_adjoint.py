@@ -76,7 +76,7 @@ def test_step_vjp_matches_central_differences(dim, tau_mode):
 
 
 def test_objective_gradient_matches_central_differences():
-    # J = (1/N) sum_n lid x-momentum flux of f^n over N steps; spec check with eps = 1e-4
+    # J = (1/N) sum_n lid x-momentum flux of f^n over N steps; central differences with eps = 1e-4
     p = bi.config("cavity2d_n41_v16_f64", n=9, nv=8, vmax=4.0, kn=0.1)
     p["lid_u"] = [0.1, 0.0, 0.0]
     cl = bi.cloud_for(p)

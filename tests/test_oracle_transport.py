@@ -116,7 +116,7 @@ def test_transport_is_positive_and_conservative_of_constants(dim, ale):
 
 @pytest.mark.parametrize("order,jitter", [(1, 0.0), (2, 0.1)])
 def test_free_transport_converges_at_first_order(order, jitter):
-    # North-star check (d): periodic box, no collisions, f0 = (1 + 0.1 sin 2 pi x) M(v);
+    # Free transport: periodic box, no collisions, f0 = (1 + 0.1 sin 2 pi x) M(v);
     # the exact solution is f0(x - v t).  Fixed CFL, dx in {1/20, 1/40, 1/80}.  The
     # second-order WLS fit (on a jittered box) keeps first order: the upwind dissipation
     # and the explicit time step are O(h).
@@ -178,8 +178,8 @@ def test_diffuse_reflection_has_wall_maxwellian_shape():
 
 @pytest.mark.parametrize("dim,n,nv,vmax,steps", [(2, 9, 40, 9.0, 100), (3, 5, 24, 8.5, 6)])
 def test_global_maxwellian_with_walls_at_rest_is_stationary(dim, n, nv, vmax, steps):
-    # North-star check (b), on a velocity grid whose discrete moments of a unit Maxwellian
-    # are exact to rounding.
+    # A global Maxwellian with walls at rest stays put, on a velocity grid whose discrete
+    # moments of a unit Maxwellian are exact to rounding.
     p, cl, sim = _run_cavity(dim, n, nv, vmax, steps, 0.0)
     f0 = sim.f.copy()
     sim.run(steps)
