@@ -177,6 +177,27 @@ def _worker(rank, world, port, name, over, steps, out):
     dist.destroy_process_group()
 
 
+def test_three_gloo_ranks_with_uneven_slabs():
+    # nv = 7: 49 velocities over 3 ranks, slabs [0, 16), [16, 32), [32, 49) that end
+    # inside grid rows, an ALE cavity whose positions must agree on every rank
+    sys.path.insert(0, ROOT)
+    import bgk_inputs as bi
+    import oracle
+    from paper_2408_02350_gb300.sharded import velocity_slabs
+    assert velocity_slabs(49, 3) == [(0, 16), (16, 32), (32, 49)]
+    name, over, steps, world = "cavity2d_ale_n201_v32_f32", dict(n=9, nv=7, vmax=3.0, storage="f64"), 3, 3
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_worker, args=(world, port, name, over, steps, out), nprocs=world, join=True)
+    p = bi.config(name, **over)
+    sim = oracle.Simulation(p, bi.cloud_for(p))
+    sim.run(steps)
+    f = np.concatenate([out[r][2] for r in range(world)], axis=2)
+    assert np.abs(f - sim.f).max() <= 1e-12 * np.abs(sim.f).max()
+    for r in range(world):
+        assert np.abs(out[r][3] - sim.rho).max() <= 1e-12 and np.abs(out[r][6] - sim.x).max() <= 1e-14
+
+
 @pytest.mark.parametrize("name,over,steps", [
     ("cavity2d_n41_v16_f64", dict(n=9, nv=6, vmax=3.0), 3),
     ("cavity2d_ale_n201_v32_f32", dict(n=9, nv=6, vmax=3.0, storage="f64"), 3),
