@@ -209,3 +209,16 @@ def test_midpoint_velocity_grid():
     g = oracle.velocity_grid(2, 40, 10.0, 1)
     assert abs(M[0].sum() * oracle.dv(40, 10.0, 1) ** 2 - 0.8) < 1e-12
     assert np.abs(g[:40, 0] - oracle.velocity_nodes(40, 10.0, 1)).max() == 0.0
+
+
+def test_global_maxwellian_stationary_on_the_midpoint_grid():
+    # the midpoint grid (vgrid 1) through the whole step with walls at rest: a global
+    # Maxwellian stays put to rounding on a grid wide and fine enough for its moments
+    import bgk_inputs as bi
+    p = bi.config("cavity2d_n41_v16_f64", n=9, nv=40, vmax=9.0, vgrid=1)
+    p["lid_u"] = [0.0, 0.0, 0.0]
+    sim = oracle.Simulation(p, bi.cavity(2, 9, 9))
+    f0 = sim.f.copy()
+    sim.run(50)
+    assert np.abs(sim.f - f0).max() < 1e-12 * f0.max()
+    assert np.abs(sim.rho - 1).max() < 1e-12 and np.abs(sim.T - 1).max() < 1e-12
