@@ -736,8 +736,12 @@ int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t*
 
 static double sgn(double a) { return a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0); }
 
-/* Upwind coefficient of neighbour slot s for convective velocity c:
- * abar_n [(c.n) - |c.n|] + abar_t [(c.t) - sign(abar_t)|c.t|] + abar_b [(c.b) - sign(abar_b)|c.b|]. */
+/* Upwind coefficient of neighbour slot s for convective velocity c (Sec. 3.4.2):
+ * abar_n [(c.n) - sign(abar_n)|c.n|] + abar_t [(c.t) - sign(abar_t)|c.t|] + abar_b [(c.b) - sign(abar_b)|c.b|],
+ * i.e. sum_d (abar_d c_d - |abar_d||c_d|) with every direction treated alike.  The printed
+ * normal term abar_n [(c.n) - |c.n|] is this form for abar_n > 0, which the linear fit
+ * guarantees (abar_n = w r n^T S n with S positive definite); the second-order fit can give
+ * abar_n < 0, where only the sign-aware form keeps every term non-positive. */
 static double upwind_coef(int dim, const double* ab, const double* fr, const double* c) {
   double cn = 0.0, ct = 0.0, cb = 0.0;
   for (int a = 0; a < dim; ++a) {
@@ -745,7 +749,7 @@ static double upwind_coef(int dim, const double* ab, const double* fr, const dou
     ct += c[a] * fr[dim + a];
     if (dim == 3) cb += c[a] * fr[2 * dim + a];
   }
-  double K = ab[0] * (cn - fabs(cn)) + ab[1] * (ct - sgn(ab[1]) * fabs(ct));
+  double K = ab[0] * (cn - sgn(ab[0]) * fabs(cn)) + ab[1] * (ct - sgn(ab[1]) * fabs(ct));
   if (dim == 3) K += ab[2] * (cb - sgn(ab[2]) * fabs(cb));
   return K;
 }

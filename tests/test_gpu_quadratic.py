@@ -97,3 +97,31 @@ def test_quadratic_steps_match_oracle(g, dim, n, nv, ale, storage, steps, tol):
     if ale:
         assert np.abs(s.positions() - sim.x).max() < (1e-13 if storage == "f64" else 1e-7)
     s.close()
+
+
+@pytest.mark.parametrize("dim,n,nv,ale,storage,steps,tol", [
+    (2, 21, 8, 0, "f64", 10, 1e-10), (2, 21, 8, 1, "f64", 10, 1e-10), (3, 7, 6, 0, "f64", 10, 1e-10),
+    (2, 21, 8, 0, "f32", 10, 1e-4), (2, 21, 8, 1, "f32", 10, 1e-4), (3, 7, 6, 0, "f32", 10, 1e-4)])
+def test_negative_normal_coefficients_match_oracle(g, dim, n, nv, ale, storage, steps, tol):
+    # Sec. 3.4.1 / 3.4.2 on a cloud jittered by 0.45 dx, where the second-order fit gives
+    # negative projected normal coefficients abar_n (asserted on the oracle's stencils):
+    # both sides use abar_d c_d - |abar_d||c_d| for every direction.
+    p = bi.config(_name(dim), n=n, nv=nv, vmax=4.0, storage=storage, ale=ale, wls_order=2)
+    cl = bi.cavity(dim, n, 2408011, 0.45)
+    cnt, col = oracle.neighbours(cl["x"], p["h"], False, p["max_nbrs"])
+    st = oracle.stencils(p, cl["x"], cl["kind"], cnt, col)
+    interior = cl["kind"] == 0
+    assert sum((st["abar"][i, :cnt[i], 0] < 0).sum() for i in np.where(interior)[0]) > 0
+    sim = oracle.Simulation(p, cl)
+    sim.run(steps)
+    s = g.Solver([p], [cl])
+    s.set_maxwellian()
+    s.step(steps)
+    s.sync()
+    rho, u, T = s.moments()
+    assert _rel(rho, sim.rho) < tol and _rel(T, sim.T) < tol and _rel(u, sim.U) < tol
+    f = s.get_f()
+    assert np.abs(f - sim.f).max() < tol * np.abs(sim.f).max()
+    if ale:
+        assert np.abs(s.positions() - sim.x).max() < (1e-13 if storage == "f64" else 1e-7)
+    s.close()

@@ -114,6 +114,38 @@ def test_transport_is_positive_and_conservative_of_constants(dim, ale):
         assert np.all(Li[np.arange(len(interior)), interior] >= -1e-15)
 
 
+@pytest.mark.parametrize("dim,n,seed,ale", [(2, 11, 5, 0), (2, 11, 5, 1), (3, 5, 7, 0)])
+def test_quadratic_fit_with_negative_normal_coefficient_stays_positive(dim, n, seed, ale):
+    # Sec. 3.4.2 with the second-order fit of Sec. 3.4.1 on a strongly jittered cloud
+    # (0.45 dx): some projected normal coefficients abar_n are negative, which the linear
+    # fit never gives.  Every term abar_d c_d - |abar_d||c_d| is <= 0 whatever the sign of
+    # abar_d, so the assembled operator keeps off-diagonal entries >= 0 and unit row sums.
+    # The printed normal term abar_n (c_n - |c_n|) would make some entries negative here.
+    p, c, cnt, col, st = _case(dim, n, 4, 1.0, seed=seed, jitter=0.45, ale=ale, wls_order=2)
+    interior = np.where(c["kind"] == 0)[0]
+    neg = [(i, s) for i in interior for s in range(cnt[i]) if st["abar"][i, s, 0] < 0.0]
+    assert len(neg) > 0
+    U = np.random.default_rng(4).normal(size=(c["x"].shape[0], dim)) * 0.2 if ale else np.zeros((len(c["x"]), dim))
+    vel = oracle.velocity_grid(dim, 4, 1.0)
+    # the printed form gives a positive K (a negative off-diagonal entry) for some of
+    # these slots and velocities; the reading must not
+    printed_positive = 0
+    for i, s in neg:
+        ab, fr = st["abar"][i, s], st["frame"][i, s]
+        for v in vel:
+            cd = fr @ (v - U[i])
+            k = ab[0] * (cd[0] - abs(cd[0])) + sum(ab[d] * cd[d] - abs(ab[d]) * abs(cd[d]) for d in range(1, dim))
+            printed_positive += k > 1e-12
+    assert printed_positive > 0
+    L = _dense_transport(p, c, cnt, col, st, U)
+    for k in range(L.shape[0]):
+        Li = L[k][interior]
+        off = Li.copy()
+        off[np.arange(len(interior)), interior] = 0.0
+        assert off.min() >= 0.0
+        assert np.allclose(Li.sum(1), 1.0, atol=1e-13)
+
+
 @pytest.mark.parametrize("order,jitter", [(1, 0.0), (2, 0.1)])
 def test_free_transport_converges_at_first_order(order, jitter):
     # Free transport: periodic box, no collisions, f0 = (1 + 0.1 sin 2 pi x) M(v);
