@@ -684,6 +684,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": p["storage"], "data": "synthetic",
                 "config": {"workload": args.workload, "points": n, "velocities": NV, "dim": dim,
                            "kn": p["kn"], "ale": bool(p["ale"]), "storage": p["storage"],
+                           "stencil_solve": "f64", "moment_combine": "f64",
                            "l2": "inputs larger than L2 (f %.0f MB per buffer, two buffers)"
                                  % (n * ncomp * NV * elem / 1e6)},
                 "clocks": clk, "gpu_launches": launches,

@@ -148,10 +148,12 @@ int bgk_version(void);
  * device wait gives up (the grid barriers of the fused ALE list-build kernel); 0
  * restores the default of about one second.  A wait that gives up records
  * BGK_E_TIMEOUT for the next bgk_sync and its CTAs leave the kernel, so no later phase
- * runs on incomplete data; the lists of that step are then partly stale (every index
- * still valid) until positions or lists are reset (bgk_set_state, bgk_manage,
- * bgk_set_params).  A limit of 1 makes the waits give up at once, which tests that
- * path without a hang. */
+ * runs on incomplete data.  The motion before the first wait is complete; the lists
+ * of the new positions are partly stale (every index still valid), and a step taken
+ * before the bgk_sync that reports the timeout runs on them.  That bgk_sync resets the
+ * waits' state and discards those lists, so the step after it builds its lists from
+ * the positions and the run continues as one without a timeout.  A limit of 1 makes
+ * the waits give up at once, which tests that path without a hang. */
 int bgk_set_watchdog(bgk_ctx* ctx, int64_t max_polls);
 
 /* Measurement support, not part of the method: the FP32 fused-multiply-add rate of

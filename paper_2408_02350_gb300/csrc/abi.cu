@@ -1175,6 +1175,17 @@ int bgk_sync(bgk_ctx* ctx, void* stream) {
   CK(ctx, cudaMemcpy(&hs, ctx->status, sizeof(hs), cudaMemcpyDeviceToHost));
   if (hs.flags) {
     CK(ctx, cudaMemset(&ctx->status->flags, 0, sizeof(int32_t)));
+    if (hs.flags & ST_TIMEOUT) {
+      // a grid barrier of the side chain gave up: the CTAs that waited left the kernel,
+      // so its barrier counter and the lists it was building are incomplete.  Reset the
+      // barrier state (and force a candidate rebuild) and discard those lists: the next
+      // step builds its lists from the current positions, which the motion phase (before
+      // the first barrier) finished.
+      for (auto& c : ctx->cases) {
+        if (int st = reset_skin(ctx, c)) return st;
+        c.next_ready = false;
+      }
+    }
     if (hs.flags & ST_OVERFLOW) return fail(ctx, BGK_E_NBR_OVERFLOW, "a point has more than max_nbrs neighbours");
     if (hs.flags & ST_SINGULAR) return fail(ctx, BGK_E_SINGULAR, "singular WLS system (too few or degenerate neighbours)");
     if (hs.flags & ST_NONFINITE) return fail(ctx, BGK_E_NONFINITE, "non-finite or non-positive density or temperature");

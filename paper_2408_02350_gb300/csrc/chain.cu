@@ -32,7 +32,10 @@ constexpr long long BARRIER_SPIN_LIMIT = 20000000;  // x 64 ns sleep: about a se
 // Grid-wide barrier over the co-resident CTAs: the last CTA to arrive resets the
 // counter and advances the generation; the others wait, at most max_spins polls, for
 // the new one.  Returns false (in every thread of the CTA) when the wait gave up.
-__device__ __forceinline__ bool grid_barrier(SkinState* sk, DevStatus* status, long long max_spins) {
+// With body non-null the last CTA to arrive also stores the body's new centre cn: it
+// never waits, so the centre advances exactly once even when other CTAs give up.
+__device__ __forceinline__ bool grid_barrier(SkinState* sk, DevStatus* status, long long max_spins,
+                                             BodyState* body = nullptr, const double* cn = nullptr, int dim = 0) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -41,6 +44,9 @@ __device__ __forceinline__ bool grid_barrier(SkinState* sk, DevStatus* status, l
     const uint32_t g = *vgen;
     __threadfence();
     if (atomicAdd(&sk->blocks, 1u) == gridDim.x - 1) {
+      // every CTA has arrived, so every thread has read the old centre
+      if (body)
+        for (int a = 0; a < dim; ++a) body->c[a] = cn[a];
       sk->blocks = 0u;
       __threadfence();
       atomicAdd(&sk->gen, 1u);
@@ -92,10 +98,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_chain(CaseView cv, double thr
     for (int k = 0; k < CHAIN_WARPS; ++k) b = max(b, s_max[k]);
     atomicMax(&sk->disp2, b);
   }
-  if (!grid_barrier(sk, cv.status, max_spins)) return;
-  // every thread has read the old centre
-  if (gtid == 0 && cv.body)
-    for (int a = 0; a < cv.dim; ++a) cv.body->c[a] = cn[a];
+  if (!grid_barrier(sk, cv.status, max_spins, cv.body, cn, cv.dim)) return;
   const uint32_t d = *reinterpret_cast<volatile uint32_t*>(&sk->disp2);
   const bool rebuild = forced || (double)__uint_as_float(d) > thr2;
 

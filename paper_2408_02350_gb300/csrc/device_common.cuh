@@ -90,6 +90,37 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Warp totals of N per-lane compensated FP32 sums (running sum s, compensation c: the
+// lane's value is s - c), combined in FP64: each lane's s - c is exact in double and the
+// additions are in double.  Every lane gets the totals.  For N = 4 the sums are reduced
+// transposed, so that a lane adds 6 doubles instead of 20 (FP64 runs at a small
+// fraction of the FP32 rate): at the step across 16 lanes a lane keeps two of the four
+// sums and passes the other two, across 8 lanes one of its two, then the three last
+// steps add one value; lane 8 q then holds the total of sum q, which is broadcast.
+template <int N>
+__device__ __forceinline__ void warp_total_f64(const float (&s)[N], const float (&c)[N], double (&out)[N]) {
+  double d[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) d[q] = (double)s[q] - (double)c[q];
+  if constexpr (N == 4) {
+    const int lane = threadIdx.x & 31;
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    double k0 = hi16 ? d[2] : d[0], k1 = hi16 ? d[3] : d[1];
+    const double p0 = hi16 ? d[0] : d[2], p1 = hi16 ? d[1] : d[3];
+    k0 += __shfl_xor_sync(0xffffffffu, p0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, p1, 16);
+    double k = hi8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = __shfl_sync(0xffffffffu, k, 8 * q);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = warp_sum(d[q]);
+  }
+}
+
 // Sum NVAL per-thread values over the block.  Each warp reduces in T, the
 // per-warp totals are combined in double.  Result valid in every thread.
 // scratch: at least 32 * NVAL doubles of shared memory.

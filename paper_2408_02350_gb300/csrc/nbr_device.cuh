@@ -309,30 +309,6 @@ __device__ __forceinline__ void filter_group_point(const CaseView& cv, const int
   }
 }
 
-// a d - b c in FP32 by Kahan's method: w = b c rounded, e = its rounding error (exact
-// by a fused multiply-add), a d - w by one fused multiply-add, plus e.
-__device__ __forceinline__ float kahan_det2(float a, float b, float c, float d) {
-  const float w = b * c;
-  const float e = fmaf(-b, c, w);
-  return fmaf(a, d, -w) + e;
-}
-
-// a0 b0 + a1 b1 + a2 b2 in FP32 with the products' rounding errors (fused
-// multiply-add) and the sums' (two-sum) carried along and added at the end.
-__device__ __forceinline__ float dot3_compensated(float a0, float b0, float a1, float b1, float a2, float b2) {
-  float s = a0 * b0, err = fmaf(a0, b0, -s);
-  const float p[2] = {a1 * b1, a2 * b2};
-  const float pe[2] = {fmaf(a1, b1, -p[0]), fmaf(a2, b2, -p[1])};
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float t = s + p[k];
-    const float bb = t - s;
-    err += (s - (t - bb)) + (p[k] - bb) + pe[k];
-    s = t;
-  }
-  return s + err;
-}
-
 // Separation x_j - x_i from the FP32 hi/lo split of the positions: the
 // difference of the high parts is exact or rounded once, the low parts add the
 // remainder, so the result carries about 1e-7 relative error without any FP64
@@ -348,11 +324,13 @@ __device__ __forceinline__ void sep_hilo(const CaseView& cv, int i, int j, float
 }
 
 // FP32/BF16 path, interior points: a group of LPP lanes per point.  Each lane
-// accumulates its share of the neighbours into the normal matrix
-// A = sum w dr dr^T (FP32), the group reduces A with shuffles, and the group's
-// first lane inverts it (FP32 cofactors with compensated products); all lanes then
-// write the FP32 coefficients of their neighbours.  Every lane of the warp calls it (shuffles over the full
-// warp); lanes with valid = false only take part in the shuffles.
+// accumulates its share of the neighbours into the normal matrix A = sum w dr dr^T in
+// FP64 (separations and weights in FP32; w dr_a is exact in FP64 and each entry takes one
+// rounding per term), the group reduces A in FP64 with shuffles, and the group's first
+// lane solves the normal equations in FP64 (inverse by cofactors, Sec. 3.4.1: S = A^-1).
+// S is then rounded to FP32, and all lanes write the FP32 coefficients of their
+// neighbours.  Every lane of the warp calls it (shuffles over the full warp); lanes with
+// valid = false only take part in the shuffles.
 template <int DIM, int LPP>
 __device__ __forceinline__ void stencil_grp_point(const CaseView& cv, const int i, const bool valid, const int sub) {
   constexpr int NA = DIM == 2 ? 3 : 6;  // unique entries of the symmetric A
@@ -360,21 +338,24 @@ __device__ __forceinline__ void stencil_grp_point(const CaseView& cv, const int 
   const int cap = cv.cap;
   const int32_t* row = cv.col + (int64_t)i * cap;
   const float nah2 = (float)(-cv.alpha / (cv.h * cv.h));
-  float A[NA];
+  double A[NA];
 #pragma unroll
-  for (int q = 0; q < NA; ++q) A[q] = 0.0f;
+  for (int q = 0; q < NA; ++q) A[q] = 0.0;
   for (int s = sub; s < m; s += LPP) {
     float dr[DIM];
     sep_hilo<DIM>(cv, i, row[s], dr);
     float r2 = 0.0f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) r2 = fmaf(dr[a], dr[a], r2);
-    const float w = expf(nah2 * r2);
+    const double w = (double)expf(nah2 * r2);
+    double dd[DIM], wd[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { dd[a] = (double)dr[a]; wd[a] = w * dd[a]; }
     int q = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int b = a; b < DIM; ++b) { A[q] = fmaf(w * dr[a], dr[b], A[q]); ++q; }
+      for (int b = a; b < DIM; ++b) { A[q] = fma(wd[a], dd[b], A[q]); ++q; }
   }
 #pragma unroll
   for (int o = LPP / 2; o >= 1; o >>= 1)
@@ -383,30 +364,27 @@ __device__ __forceinline__ void stencil_grp_point(const CaseView& cv, const int 
   float Sf[NA];
   int ok = 1;
   if (sub == 0) {
-    // inverse by cofactors in FP32: each 2x2 cofactor by Kahan's fused-multiply-add
-    // method (error within a few ulps however much the products cancel), the 3D
-    // determinant by a compensated dot product, one IEEE division per entry
-    float det, S[NA], scale;
+    double det, S[NA], scale;
     if constexpr (DIM == 2) {
-      scale = fmaxf(fabsf(A[0]), fabsf(A[2]));
-      det = kahan_det2(A[0], A[1], A[1], A[2]);
-      S[0] = A[2] / det; S[1] = -A[1] / det; S[2] = A[0] / det;
+      scale = fmax(fabs(A[0]), fabs(A[2]));
+      det = A[0] * A[2] - A[1] * A[1];
+      S[0] = A[2]; S[1] = -A[1]; S[2] = A[0];
     } else {
       // A = [a0 a1 a2; a1 a3 a4; a2 a4 a5]
-      scale = fmaxf(fabsf(A[0]), fmaxf(fabsf(A[3]), fabsf(A[5])));
-      const float c00 = kahan_det2(A[3], A[4], A[4], A[5]);
-      const float c01 = kahan_det2(A[4], A[1], A[5], A[2]);
-      const float c02 = kahan_det2(A[1], A[3], A[2], A[4]);
-      det = dot3_compensated(A[0], c00, A[1], c01, A[2], c02);
-      S[0] = c00 / det; S[1] = c01 / det; S[2] = c02 / det;
-      S[3] = kahan_det2(A[0], A[2], A[2], A[5]) / det;
-      S[4] = kahan_det2(A[1], A[0], A[4], A[2]) / det;
-      S[5] = kahan_det2(A[0], A[1], A[1], A[3]) / det;
+      scale = fmax(fabs(A[0]), fmax(fabs(A[3]), fabs(A[5])));
+      S[0] = A[3] * A[5] - A[4] * A[4];
+      S[1] = A[4] * A[2] - A[1] * A[5];
+      S[2] = A[1] * A[4] - A[3] * A[2];
+      det = A[0] * S[0] + A[1] * S[1] + A[2] * S[2];
+      S[3] = A[0] * A[5] - A[2] * A[2];
+      S[4] = A[1] * A[2] - A[0] * A[4];
+      S[5] = A[0] * A[3] - A[1] * A[1];
     }
-    const float sc = DIM == 2 ? scale * scale : scale * scale * scale;
-    ok = valid && m >= DIM && fabsf(det) > 1e-12f * sc && isfinite(det);
+    const double sc = DIM == 2 ? scale * scale : scale * scale * scale;
+    ok = valid && m >= DIM && fabs(det) > 1e-12 * sc && isfinite(det);
+    const double rdet = 1.0 / det;
 #pragma unroll
-    for (int q = 0; q < NA; ++q) Sf[q] = S[q];
+    for (int q = 0; q < NA; ++q) Sf[q] = (float)(S[q] * rdet);
   }
   const int src = (threadIdx.x & 31) & ~(LPP - 1);
 #pragma unroll

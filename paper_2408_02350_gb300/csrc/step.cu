@@ -550,9 +550,9 @@ __global__ void __launch_bounds__(256) k_shard_relax_wp(const CaseView cv) {
   for (int q = lane; q < cv.nv; q += 32) s_v[q] = (float)cv.vnodes[q];
   __syncwarp();
   const int i = cv.int_idx[t];
-  float tot[DIM + 2];
+  double tot[DIM + 2];
 #pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) tot[q] = (float)cv.xs[(int64_t)i * (DIM + 2) + q];
+  for (int q = 0; q < DIM + 2; ++q) tot[q] = cv.xs[(int64_t)i * (DIM + 2) + q];
   relax_point<S, DIM, ROW, 4, true>(cv, i, s_v, tot);
 }
 
@@ -1446,8 +1446,7 @@ __global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
     }
   }
   double tot[DIM + 2];
-#pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) tot[q] = (double)warp_sum(msum[q] - mcmp[q]);
+  warp_total_f64<DIM + 2>(msum, mcmp, tot);
   if (SH && lane == 0) {
 #pragma unroll
     for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = tot[q];

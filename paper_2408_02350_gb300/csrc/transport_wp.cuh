@@ -173,14 +173,15 @@ __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const
   }
 }
 
-// Moments of f~_i from the raw sums tot = (sum g, sum v g, sum |v|^2 g (+ sum h)),
-// tau and the Maxwellian, then the relaxation pass over the output row:
-// f^{n+1} = (tau f~ + dt M)/(tau + dt) (RK = 1: the exact relaxation over dt/2).  All 32
-// lanes of the warp take part, each with the same tot.  SH: the row holds the velocity
-// slab that starts at cv.vk0.
+// Moments of f~_i from the raw sums tot = (sum g, sum v g, sum |v|^2 g (+ sum h)) in
+// FP64 (U = sum v g / R and T = (sum |v|^2 g - R |U|^2) / (3 R), where the difference
+// cancels), tau and the Maxwellian in FP32 from them, then the relaxation pass over the
+// output row: f^{n+1} = (tau f~ + dt M)/(tau + dt) (RK = 1: the exact relaxation over
+// dt/2).  All 32 lanes of the warp take part, each with the same tot.  SH: the row holds
+// the velocity slab that starts at cv.vk0.
 template <typename S, int DIM, bool ROW, int VPL, bool SH = false, int RK = 0>
 __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, const float* s_v,
-                                            const float (&tot)[DIM + 2]) {
+                                            const double (&tot)[DIM + 2]) {
   constexpr int NC = DIM == 2 ? 2 : 1;
   const int lane = threadIdx.x & 31;
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
@@ -189,20 +190,23 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
   const int nchunk = NVp / VPL;
   const int nslice = (nchunk + 31) >> 5;
   S* fo = reinterpret_cast<S*>(cv.f_out) + (int64_t)i * NC * NVp;
-  const float R = tot[0];
-  float Un[DIM], u2 = 0.0f;
+  const double R = tot[0], rR = 1.0 / R;
+  double Ud[DIM], u2d = 0.0;
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) { Un[a] = tot[1 + a] / R; u2 = fmaf(Un[a], Un[a], u2); }
-  const float Tn = (tot[DIM + 1] - R * u2) / (3.0f * R);
-  const float wv = (float)(DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
-  const float rho = R * wv;
+  for (int a = 0; a < DIM; ++a) { Ud[a] = tot[1 + a] * rR; u2d = fma(Ud[a], Ud[a], u2d); }
+  const double Td = (tot[DIM + 1] - R * u2d) * rR * (1.0 / 3.0);
+  const double rhod = R * (DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
+  float Un[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) Un[a] = (float)Ud[a];
+  const float Tn = (float)Td, rho = (float)rhod;
   if (lane == 0) {
     double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
-    mo[0] = rho;
+    mo[0] = rhod;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) mo[1 + a] = a < DIM ? (double)Un[a < DIM ? a : 0] : 0.0;
-    mo[4] = Tn;
-    if (!(rho > 0.0f) || !(Tn > 0.0f) || !isfinite(rho) || !isfinite(Tn)) set_status(cv.status, ST_NONFINITE);
+    for (int a = 0; a < 3; ++a) mo[1 + a] = a < DIM ? Ud[a < DIM ? a : 0] : 0.0;
+    mo[4] = Td;
+    if (!(rhod > 0.0) || !(Td > 0.0) || !isfinite(rhod) || !isfinite(Td)) set_status(cv.status, ST_NONFINITE);
   }
   float ca = 1.0f, cb = 0.0f, pref = 0.0f, nl2 = 0.0f;
   if (cv.tau_mode != 2 && rho > 0.0f && Tn > 0.0f) {
@@ -247,28 +251,26 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
   }
 }
 
-// Moments of f~_i (warp totals of the lanes' compensated sums; every lane gets them)
-// and the relaxation of the output row.
+// Moments of f~_i (warp totals of the lanes' compensated sums, combined in FP64; every
+// lane gets them) and the relaxation of the output row.
 template <typename S, int DIM, bool ROW, int VPL, int RK = 0>
 __device__ __forceinline__ void finish_point(const CaseView& cv, const int i, const float* s_v,
                                              const float (&msum)[DIM + 2], const float (&mcmp)[DIM + 2]) {
-  float tot[DIM + 2];
-#pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
+  double tot[DIM + 2];
+  warp_total_f64<DIM + 2>(msum, mcmp, tot);
   relax_point<S, DIM, ROW, VPL, false, RK>(cv, i, s_v, tot);
 }
 
 // Sharded step: the raw moment sums of f~_i over the slab (warp totals of the lanes'
-// compensated sums) to row i of the exchange buffer, in double.
+// compensated sums, combined in FP64) to row i of the exchange buffer.
 template <int DIM>
 __device__ __forceinline__ void partial_out(const CaseView& cv, const int i, const float (&msum)[DIM + 2],
                                             const float (&mcmp)[DIM + 2]) {
-  float tot[DIM + 2];
-#pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) tot[q] = warp_sum(msum[q] - mcmp[q]);
+  double tot[DIM + 2];
+  warp_total_f64<DIM + 2>(msum, mcmp, tot);
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = (double)tot[q];
+    for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = tot[q];
   }
 }
 
