@@ -156,7 +156,8 @@ def _traffic_record(kernel: str, workload: str):
 
 
 def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
-    """The FP64 CPU oracle, single-threaded, on a bounded sample of the workload."""
+    """The FP64 CPU oracle on a bounded sample of the workload: single-threaded, and its
+    OpenMP build (loops over points split among all host cores) beside it."""
     import oracle
     cl = bi.cloud_for(p)
     sim = oracle.Simulation(p, cl)
@@ -165,10 +166,25 @@ def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
     dt = time.perf_counter() - t0
     n = cl["x"].shape[0]
     upd = n * p["nv"] ** p["dim"] * nsteps
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d full time step(s) of the %d^%d x %d^%d cavity (%d points), FP64, one thread, %.1f s"
-                      % (nsteps, p["n"], p["dim"], p["nv"], p["dim"], n, dt),
-            "host": _host_cpu()}
+    out = {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d full time step(s) of the %d^%d x %d^%d cavity (%d points), FP64, one thread, %.1f s"
+                     % (nsteps, p["n"], p["dim"], p["nv"], p["dim"], n, dt),
+           "host": _host_cpu()}
+    try:
+        somp = oracle.Simulation(p, cl, omp=True)
+        somp.run(1)  # warm-up: thread pool start
+        k = max(2, nsteps)
+        t0 = time.perf_counter()
+        somp.run(k)
+        dto = time.perf_counter() - t0
+        thr = oracle.threads(True)
+        out["omp"] = {"value": n * p["nv"] ** p["dim"] * k / dto, "unit": UNIT, "cores": thr,
+                      "kind": "oracle_omp",
+                      "sample": "%d full time steps of the same cavity after one warm-up step, FP64, OpenMP "
+                                "over points on %d threads, %.1f s" % (k, thr, dto)}
+    except (OSError, subprocess.CalledProcessError) as e:
+        out["omp"] = {"unavailable": "OpenMP build of the oracle failed: %s" % e}
+    return out
 
 
 def _host_cpu() -> dict:
@@ -380,29 +396,49 @@ def batched_cost(g, torch, stream, steps: int = 20) -> dict:
 
 
 def run_reference(args, p: dict) -> None:
-    """Reference arm: the FP64 CPU oracle timed on host cores, each step a bounded sample."""
+    """Reference arm: the FP64 CPU oracle (its OpenMP build, all host cores) on the bench
+    workload itself, W warm-up and K timed full steps; when those would take longer than
+    about four minutes, each step is instead one full step of a smaller cavity with the
+    same velocity grid and parameters, sized to fit, and the line says so."""
     rank, world, _ = _dist_env()
     if rank != 0:
         return
     import oracle
-    sample_n = 25
-    q = bi.config(WORKLOAD, n=sample_n)
-    cl = bi.cloud_for(q)
-    sim = oracle.Simulation(q, cl)
-    sim.run(args.warmup)
+    budget_s = 240.0
+    cl = bi.cloud_for(p)
+    sim = oracle.Simulation(p, cl, omp=True)
+    t0 = time.perf_counter()
+    sim.run(1)  # first warm-up step, also the estimate of one step
+    t1 = time.perf_counter() - t0
+    q, sample_n = p, p["n"]
+    if (args.warmup + args.steps) * t1 > budget_s:
+        # a smaller cavity: the step cost is about linear in the point count
+        scale = budget_s / ((args.warmup + args.steps) * t1)
+        sample_n = max(11, int((p["n"] - 1) * scale ** (1.0 / p["dim"])) + 1)
+        q = bi.config(WORKLOAD, n=sample_n, kn=p["kn"], storage=p["storage"])
+        cl = bi.cloud_for(q)
+        sim = oracle.Simulation(q, cl, omp=True)
+        sim.run(1)
+    sim.run(max(0, args.warmup - 1))
     t0 = time.perf_counter()
     sim.run(args.steps)
     dt = time.perf_counter() - t0
     n = cl["x"].shape[0]
-    value = n * q["nv"] ** 2 * args.steps / dt
+    value = n * q["nv"] ** q["dim"] * args.steps / dt
+    thr = oracle.threads(True)
+    same = sample_n == p["n"]
+    what = ("one full FP64 time step of the bench workload itself (%d^%d points, %d^%d velocities, ALE, Kn %.2g)"
+            % (p["n"], p["dim"], p["nv"], p["dim"], p["kn"]) if same else
+            "one full FP64 time step of a %d^%d-point cavity with the bench's %d^%d velocity grid, ALE, Kn %.2g "
+            "(%d points; the full workload would not fit the time budget)"
+            % (sample_n, q["dim"], q["nv"], q["dim"], q["kn"], n))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "points": p["n"] ** 2, "velocities": p["nv"] ** 2, "kn": p["kn"],
-                       "ale": True, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: one full FP64 time step of a %d^2-point cavity with the same "
-                                       "32^2 velocity grid, ALE, Kn %.2g (%d points)" % (sample_n, q["kn"], n),
+            "config": {"workload": WORKLOAD, "points": n, "velocities": q["nv"] ** q["dim"], "kn": q["kn"],
+                       "ale": True, "l2": "n/a (CPU)", "same_workload": same},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle_omp",
+                             "sample": "each step: " + what + ", OpenMP over points on %d threads" % thr,
                              "host": _host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

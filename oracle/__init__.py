@@ -23,29 +23,35 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bgk_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
 _handle = None
+_handle_omp = None
 
 OK, E_OVERFLOW, E_SINGULAR, E_INVAL, E_NOMEM = 0, 1, 2, 3, 4
 
 
-def build(force: bool = False) -> str:
-    """Compile bgk_oracle.c into oracle/_build/liboracle.so (gcc -O2, no FMA contraction)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile bgk_oracle.c into oracle/_build/liboracle.so (gcc -O2, no FMA contraction);
+    with omp=True into liboracle_omp.so with -fopenmp (the loops over points split among
+    threads, every point computed as in the plain build; used to time the oracle on all
+    host cores)."""
+    out = _OUT_OMP if omp else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
     import hashlib
     import platform
     stamp = hashlib.sha256(open(_SRC, "rb").read() + platform.machine().encode()).hexdigest()
-    stamp_path = _OUT + ".stamp"
+    stamp_path = out + ".stamp"
     old = open(stamp_path).read() if os.path.exists(stamp_path) else ""
-    if force or old != stamp or not os.path.exists(_OUT):
-        tmp = _OUT + ".%d.tmp" % os.getpid()
+    if force or old != stamp or not os.path.exists(out):
+        tmp = out + ".%d.tmp" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+               "-fno-fast-math"] + (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _OUT)
+        os.replace(tmp, out)
         with open(stamp_path, "w") as fh:
             fh.write(stamp)
-    return _OUT
+    return out
 
 
 class Params(C.Structure):
@@ -90,11 +96,12 @@ _PL = C.POINTER(C.c_int64)
 _PP = C.POINTER(Params)
 
 
-def lib():
-    global _handle
+def lib(omp: bool = False):
+    """The plain oracle library, or with omp=True its OpenMP build."""
+    global _handle, _handle_omp
     with _lock:
-        if _handle is None:
-            h = C.CDLL(build())
+        if (_handle_omp if omp else _handle) is None:
+            h = C.CDLL(build(omp=omp))
             sig = {
                 "or_dv": (C.c_double, [C.c_int32, C.c_double]),
                 "or_velocity_nodes": (None, [C.c_int32, C.c_double, _PD]),
@@ -124,13 +131,22 @@ def lib():
                 "or_objective": (C.c_double, [_PP, C.c_int64, _PI, _PD, _PD, C.c_double]),
                 "or_manage": (C.c_int64, [_PP, C.c_int64, _PD, _PI, _PD, _PD, _PI, _PI, C.c_double, C.c_int32,
                                           C.c_int64, _PD, _PI, _PD, _PD, _PL, _PL]),
+                "or_threads": (C.c_int, []),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(h, name)
                 fn.restype = res
                 fn.argtypes = args
-            _handle = h
-    return _handle
+            if omp:
+                _handle_omp = h
+            else:
+                _handle = h
+    return _handle_omp if omp else _handle
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the oracle's loops over points use (1 for the plain build)."""
+    return int(lib(omp).or_threads())
 
 
 def _d(a):
@@ -371,7 +387,9 @@ def objective(p: dict, kind, f, lam=None, scale: float = 1.0) -> float:
 class Simulation:
     """State (x, f, rho, U, T) of one point cloud advanced by ``or_run``."""
 
-    def __init__(self, p: dict, cloud: dict, rho0: float = 1.0, U0=(0.0, 0.0, 0.0), T0: float = 1.0, f0=None):
+    def __init__(self, p: dict, cloud: dict, rho0: float = 1.0, U0=(0.0, 0.0, 0.0), T0: float = 1.0, f0=None,
+                 omp: bool = False):
+        self.omp = omp  # run() through the OpenMP build (timing on all host cores)
         self.p = dict(p)
         self.q = params(p)
         self.x = _f64(cloud["x"]).copy()
@@ -416,7 +434,7 @@ class Simulation:
 
     def run(self, nsteps: int) -> None:
         cl = np.zeros(1, dtype=np.int64)
-        st = lib().or_run(C.byref(self.q), self.n, _d(self.x), _i(self.kind), _d(self.normal), _d(self.f),
+        st = lib(self.omp).or_run(C.byref(self.q), self.n, _d(self.x), _i(self.kind), _d(self.normal), _d(self.f),
                           _d(self.rho), _d(self.U), _d(self.T), nsteps, cl.ctypes.data_as(_PL))
         if st != OK:
             raise RuntimeError("oracle or_run failed with status %d" % st)

@@ -5,7 +5,10 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline leg of the benchmark may load this library.  The CUDA library never
- * links it, and the two share no code: this file includes nothing but libc.
+ * links it, and the two share no code: this file includes nothing but libc (and,
+ * in the second build made with -fopenmp to time the oracle on all host cores,
+ * the OpenMP runtime; that build splits the loops over points among threads and
+ * computes every point exactly as the plain build does).
  *
  * Plain, slow loops in IEEE double, written to be checked against the paper by
  * eye.  Built with -ffp-contract=off so that no multiply-add is fused.
@@ -44,6 +47,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int32_t dim;       /* 2: Chu-reduced g1, g2 ; 3: full f */
@@ -412,6 +418,9 @@ int or_stencils(const or_params* p, int64_t n, const double* x, const int32_t* k
   memset(abar, 0, sizeof(double) * n * cap * dim);
   memset(frame, 0, sizeof(double) * n * cap * dim * dim);
   memset(recon, 0, sizeof(double) * n * cap);
+  /* every point's stencil is independent (the OpenMP build splits the points over threads;
+   * the arithmetic of each point is the same in either build) */
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : status)
   for (int64_t i = 0; i < n; ++i) {
     const double* xi = x + i * dim;
     if (kind[i] == 0 && p->wls_order == 2) {
@@ -732,6 +741,16 @@ int64_t or_manage(const or_params* p, int64_t n, const double* x, const int32_t*
   return k;
 }
 
+/* Threads the loops over points use: 1 in the plain build, the OpenMP thread count in
+ * the build with -fopenmp (used only to time the oracle on all host cores). */
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* ---- explicit transport with the positive upwind flux (Eq. explicit, Sec. 3.4.2) ---- */
 
 static double sgn(double a) { return a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0); }
@@ -784,6 +803,7 @@ void or_transport(const or_params* p, int64_t n, const int32_t* kind, const int3
   int64_t NV = nvel_of(dim, p->nv), row = ncomp_of(dim) * NV;
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
   or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
+#pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < n; ++i) {
     if (kind[i] != 0) { memcpy(ft + i * row, f + i * row, sizeof(double) * row); continue; }
     transport_point(p, i, cnt, col, abar, frame, U, f, vel, ft + i * row);
@@ -816,12 +836,16 @@ void or_relax(const or_params* p, int64_t n, const int32_t* kind, const double* 
               double* rho, double* U, double* T) {
   int dim = p->dim;
   int64_t row = ncomp_of(dim) * nvel_of(dim, p->nv);
-  double* M = (double*)malloc(sizeof(double) * row);
-  for (int64_t i = 0; i < n; ++i) {
-    if (kind[i] != 0) continue;
-    relax_point(p, ft + i * row, f + i * row, M, rho + i, U + i * dim, T + i);
+#pragma omp parallel
+  {
+    double* M = (double*)malloc(sizeof(double) * row);  /* scratch of one thread */
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      if (kind[i] != 0) continue;
+      relax_point(p, ft + i * row, f + i * row, M, rho + i, U + i * dim, T + i);
+    }
+    free(M);
   }
-  free(M);
 }
 
 /* Transport and relaxation of the listed interior points only (for spot checks of
@@ -886,8 +910,12 @@ int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double
   int64_t NV = nvel_of(dim, p->nv), row = nc * NV;
   int status = OR_OK;
   double* vel = (double*)malloc(sizeof(double) * NV * dim);
-  double* Mw = (double*)malloc(sizeof(double) * row);
   or_velocity_grid_g(dim, p->nv, p->vmax, p->vgrid, vel);
+  /* wall points are independent: each reads interior rows only and writes its own row */
+#pragma omp parallel reduction(max : status)
+  {
+  double* Mw = (double*)malloc(sizeof(double) * row);  /* scratch of one thread */
+#pragma omp for schedule(dynamic, 4)
   for (int64_t b = 0; b < n; ++b) {
     if (kind[b] == 0) continue;
     double* fb = f + b * row;
@@ -927,8 +955,9 @@ int or_boundary(const or_params* p, int64_t n, const int32_t* kind, const double
     }
     or_moments_point(p, fb, rho + b, U + b * dim, T + b);
   }
-  free(vel);
   free(Mw);
+  }
+  free(vel);
   return status;
 }
 

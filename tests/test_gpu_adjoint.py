@@ -134,3 +134,49 @@ def test_adjoint_cavity_1000_steps_against_finite_differences(g):
     assert abs(du32[0] - fd_u) <= 1e-3 * abs(fd_u), (du32, fd_u)
     assert abs(dkn32 - fd_k) <= 1e-3 * abs(fd_k), (dkn32, fd_k)
     assert abs(du32[0] - du64[0]) <= 1e-3 * abs(du64[0])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_autograd_function_gives_the_adjoint_gradient(g, storage):
+    # torch.autograd through LidFluxObjective: the gradients equal adjoint.gradient's
+    # exactly (the same kernels in the same order), and (FP64) match central differences
+    # in u_lid and Kn and a directional difference in f0 to 1e-3
+    import torch
+    from paper_2408_02350_gb300 import adjoint
+    p = bi.config("cavity2d_n41_v16_f64", n=21, nv=8, vmax=4.0, kn=0.1, storage=storage)
+    p["lid_u"] = [0.1, 0.0, 0.0]
+    cl = bi.cloud_for(p)
+    N, K = 12, 5
+    sdt = torch.float64 if storage == "f64" else torch.float32
+    M = oracle.maxwellian(p, 1.0, (0.0, 0.0, 0.0), 1.0)
+    n = len(cl["kind"])
+    rng = np.random.default_rng(21)
+    f0 = torch.tensor(M[None] * (1.0 + 0.05 * rng.uniform(-1, 1, size=(n,) + M.shape)), dtype=sdt, device="cuda")
+    s = g.Solver([p], [cl])
+    f0r = f0.clone().requires_grad_(True)
+    lid = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    kn = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    J = adjoint.LidFluxObjective.apply(f0r, lid, kn, s, N, K)
+    gf, gl, gk = torch.autograd.grad(J, (f0r, lid, kn))
+    # the same gradient through adjoint.gradient on a fresh context
+    s2 = g.Solver([p], [cl])
+    J2, du, dkn, lam0 = adjoint.gradient(s2, N, checkpoint_every=K, f0=f0)
+    assert J.item() == J2
+    assert gl.item() == du[0] and gk.item() == dkn
+    assert torch.equal(gf, lam0.to(gf.dtype))
+    if storage == "f64":
+        def J_of(lid_u, knv, f):
+            with torch.no_grad():
+                return adjoint.LidFluxObjective.apply(f, torch.tensor(lid_u, dtype=torch.float64),
+                                                      torch.tensor(knv, dtype=torch.float64), s, N, K).item()
+        eps = 1e-4
+        fd_u = (J_of(0.1 + eps, 0.1, f0) - J_of(0.1 - eps, 0.1, f0)) / (2 * eps)
+        fd_k = (J_of(0.1, 0.1 + eps, f0) - J_of(0.1, 0.1 - eps, f0)) / (2 * eps)
+        d = torch.tensor(M[None] * rng.uniform(-1, 1, size=(n,) + M.shape), dtype=sdt, device="cuda")
+        fd_f = (J_of(0.1, 0.1, f0 + eps * d) - J_of(0.1, 0.1, f0 - eps * d)) / (2 * eps)
+        assert abs(gl.item() - fd_u) <= 1e-3 * abs(fd_u), (gl.item(), fd_u)
+        assert abs(gk.item() - fd_k) <= 1e-3 * abs(fd_k), (gk.item(), fd_k)
+        gd = float((gf * d).sum())
+        assert abs(gd - fd_f) <= 1e-3 * abs(fd_f), (gd, fd_f)
+    s.close()
+    s2.close()
