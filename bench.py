@@ -437,7 +437,7 @@ def run_reference(args, p: dict) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "points": n, "velocities": q["nv"] ** q["dim"], "kn": q["kn"],
                        "ale": True, "l2": "n/a (CPU)", "same_workload": same},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle_omp",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": "each step: " + what + ", OpenMP over points on %d threads" % thr,
                              "host": _host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

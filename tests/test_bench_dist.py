@@ -49,3 +49,7 @@ def test_reference_arm_prints_its_line():
     line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
     assert line["impl"] == "reference" and line["unit"] == "updates/s" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    # the oracle's OpenMP build on the bench workload itself, all host cores
+    assert line["config"]["same_workload"] and line["config"]["points"] == 201 ** 2
+    assert line["cpu_baseline"]["cores"] == line["cpu_baseline"]["host"]["logical_cores"] or \
+        line["cpu_baseline"]["cores"] >= 1
