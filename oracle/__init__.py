@@ -40,9 +40,13 @@ def build(force: bool = False, omp: bool = False) -> str:
     os.makedirs(os.path.dirname(out), exist_ok=True)
     import hashlib
     import platform
-    stamp = hashlib.sha256(open(_SRC, "rb").read() + platform.machine().encode()).hexdigest()
+    with open(_SRC, "rb") as fh:
+        stamp = hashlib.sha256(fh.read() + platform.machine().encode()).hexdigest()
     stamp_path = out + ".stamp"
-    old = open(stamp_path).read() if os.path.exists(stamp_path) else ""
+    old = ""
+    if os.path.exists(stamp_path):
+        with open(stamp_path) as fh:
+            old = fh.read()
     if force or old != stamp or not os.path.exists(out):
         tmp = out + ".%d.tmp" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",

@@ -36,7 +36,8 @@ def _stamp(paths: list[str], extra: list[str] | None) -> str:
     h = hashlib.sha256()
     for p in sorted(paths):
         h.update(p.encode())
-        h.update(open(p, "rb").read())
+        with open(p, "rb") as fh:
+            h.update(fh.read())
     h.update(" ".join(ARCH + FLAGS + (extra or [])).encode())
     h.update(platform.machine().encode())
     return h.hexdigest()
@@ -48,7 +49,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     headers.append(os.path.join(ROOT, "include", "bgk.h"))
     stamp_path = os.path.join(BUILD, "stamp")
     stamp = _stamp([os.path.join(CSRC, s) for s in SOURCES] + headers, extra)
-    old = open(stamp_path).read() if os.path.exists(stamp_path) else ""
+    old = ""
+    if os.path.exists(stamp_path):
+        with open(stamp_path) as fh:
+            old = fh.read()
     if old != stamp or not os.path.exists(LIB):
         force = True
     nvcc = _nvcc()
