@@ -444,19 +444,28 @@ def run_reference(args, p: dict) -> None:
     print(json.dumps(line), flush=True)
 
 
-def run_sharded(args, p: dict, rank: int, world: int, local_rank: int) -> None:
-    """One cavity split over the ranks by velocity slabs, the sums exchanged by an NCCL
-    allreduce twice a step (strong scaling: the same cavity for every rank count)."""
+def sharded_plan(p: dict, rank: int, world: int) -> dict:
+    """The slab of one rank in the velocity-sharded step and the bytes of its two
+    exchanges per step (the allreduce buffers: (dim + 2) n and (2 dim + 6) n_wall doubles)."""
+    from paper_2408_02350_gb300.sharded import velocity_slabs
+    cl = bi.cloud_for(p)
+    n = cl["x"].shape[0]
+    dim = p["dim"]
+    n_wall = int((cl["kind"] != 0).sum())
+    lo, hi = velocity_slabs(p["nv"] ** dim, world)[rank]
+    return {"lo": lo, "hi": hi, "points": n, "exchange_bytes": 8 * ((dim + 2) * n + (2 * dim + 6) * n_wall)}
+
+
+def measure_sharded(args, p: dict, dist, stream) -> dict:
+    """One cavity split over the ranks by velocity slabs, the sums exchanged by an allreduce
+    of the process group twice a step (strong scaling: the same cavity for every rank
+    count).  Device time of K steps (max over ranks) and the end-to-end rate with this
+    rank's slab of f uploaded from pinned host memory every step."""
     import torch
-    import torch.distributed as dist
     import paper_2408_02350_gb300 as g
     from paper_2408_02350_gb300.sharded import ShardedSolver
 
-    torch.cuda.set_device(local_rank)
-    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-    os.environ.setdefault("MASTER_PORT", "29517")
-    dist.init_process_group("nccl", rank=rank, world_size=world)
-    stream = torch.cuda.current_stream()
+    world = dist.get_world_size()
     cl = bi.cloud_for(p)
     n = cl["x"].shape[0]
     dim, NV = p["dim"], p["nv"] ** p["dim"]
@@ -505,23 +514,36 @@ def run_sharded(args, p: dict, rank: int, world: int, local_rank: int) -> None:
     barrier()
     e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
     s.sync(stream)
-    if rank == 0:
-        xbytes = 8 * (sl.xm.numel() + sl.xw.numel())
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "strong", "vs_baseline": None, "dtype": p["storage"], "data": "synthetic",
-                "config": {"workload": args.workload, "points": n, "velocities": NV, "dim": dim,
-                           "kn": p["kn"], "ale": bool(p["ale"]), "storage": p["storage"],
-                           "parallelism": "velocity slabs, one per rank; NCCL allreduce of %d bytes twice a step"
-                                          % xbytes,
-                           "l2": "inputs larger than L2 (f %.0f MB per buffer over all ranks)"
-                                 % (f_host.numel() * f_host.element_size() * world / 1e6)},
-                "clocks": clk, "gpu_launches": launches,
-                "e2e": {"value": n * NV * args.e2e_steps / e2e_s, "unit": UNIT,
-                        "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
-                        "d2h_bytes_per_step": n * (dim + 2) * 8, "steps": args.e2e_steps}}
-        print(json.dumps(line), flush=True)
+    xbytes = 8 * (sl.xm.numel() + sl.xw.numel())
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None, "dtype": p["storage"], "data": "synthetic",
+           "config": {"workload": args.workload, "points": n, "velocities": NV, "dim": dim,
+                      "kn": p["kn"], "ale": bool(p["ale"]), "storage": p["storage"],
+                      "stencil_solve": "f64", "moment_combine": "f64",
+                      "parallelism": "velocity slabs, one per rank; allreduce of %d bytes twice a step" % xbytes,
+                      "l2": "inputs larger than L2 (f %.0f MB per buffer over all ranks)"
+                            % (f_host.numel() * f_host.element_size() * world / 1e6)},
+           "clocks": clk, "gpu_launches": launches,
+           "e2e": {"value": n * NV * args.e2e_steps / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
+                   "d2h_bytes_per_step": n * (dim + 2) * 8, "steps": args.e2e_steps}}
     s.close()
+    return out
+
+
+def run_sharded(args, p: dict, rank: int, world: int, local_rank: int) -> None:
+    """bench.py --sharded: the velocity-sharded strong-scaling line as the headline."""
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ.setdefault("MASTER_PORT", "29517")
+    dist.init_process_group("nccl", rank=rank, world_size=world)
+    line = measure_sharded(args, p, dist, torch.cuda.current_stream())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     dist.destroy_process_group()
 
 
@@ -543,6 +565,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the Kn sweep and the FP64 41^2 cavity")
     ap.add_argument("--sharded", action="store_true",
                     help="one cavity split over the ranks by velocity slabs (strong scaling)")
+    ap.add_argument("--no-sharded", action="store_true",
+                    help="under torchrun, skip the velocity-sharded line beside the replica line")
     ap.add_argument("--time-order", type=int, default=None,
                     help="2: the workload with fixed points and the second-order time step (profiling runs)")
     args = ap.parse_args()
@@ -732,6 +756,14 @@ def main():
                 "manage": manage, "extra": extra}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, 1)
+    if dist is not None and not args.no_sharded:
+        # the multi-GPU design for one cavity: the same workload split over the ranks by
+        # velocity slabs (strong scaling), beside the weak-scaled replicas above
+        sh = measure_sharded(args, dict(bi.config(args.workload, **over), **({"storage": args.storage}
+                                                                            if args.storage else {})), dist, stream)
+        if rank == 0:
+            line["sharded"] = sh
+    if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

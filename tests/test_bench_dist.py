@@ -42,6 +42,41 @@ def test_two_ranks_take_independent_cavities_and_the_max_time():
     assert out[0][2] == out[1][2] == 201           # same cavity size on every rank
 
 
+def _plan_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    import bgk_inputs as bi
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p = bi.config(bench.WORKLOAD)
+    plan = bench.sharded_plan(p, rank, world)
+    # the allreduce the sharded step makes, on buffers of the planned size
+    xm = torch.full((plan["exchange_bytes"] // 8,), float(rank + 1), dtype=torch.float64)
+    dist.all_reduce(xm)
+    out[rank] = (plan["lo"], plan["hi"], plan["exchange_bytes"], float(xm[0]), float(xm[-1]))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_velocity_sharded_plan_splits_the_grid_and_sums_over_ranks(world):
+    # the multi-GPU line of bench.py (velocity slabs, strong scaling): the slabs of the
+    # ranks tile the 32^2 velocity grid without overlap, every rank exchanges the same
+    # (dim + 2) n + (2 dim + 6) n_wall doubles, and the allreduce sums over the ranks
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_plan_worker, args=(world, port, out), nprocs=world, join=True)
+    spans = sorted((out[r][0], out[r][1]) for r in range(world))
+    assert spans[0][0] == 0 and spans[-1][1] == 32 * 32
+    assert all(spans[k][1] == spans[k + 1][0] for k in range(world - 1))
+    n, n_wall = 201 ** 2, 4 * 200
+    assert all(out[r][2] == 8 * (4 * n + 10 * n_wall) for r in range(world))
+    total = world * (world + 1) / 2
+    assert all(out[r][3] == total and out[r][4] == total for r in range(world))
+
+
 def test_reference_arm_prints_its_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
                         "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
