@@ -357,6 +357,9 @@ def extra_configs(g, torch, stream, workload: str) -> dict:
     out["body2d_ale_n201_v32_f32_managed"] = body_managed(g, torch, stream)
     out["cavity2d_n41_v16_f64"] = _rate(g, torch, stream, bi.config("cavity2d_n41_v16_f64"), 100)
     out["cavity3d_n41_v16_f32"] = _rate(g, torch, stream, bi.config("cavity3d_n41_v16_f32"), 10)
+    # BF16 storage (FP32 arithmetic) on the 3D cavity and on the workload, beside FP32
+    out["cavity3d_n41_v16_bf16"] = _rate(g, torch, stream, bi.config("cavity3d_n41_v16_f32", storage="bf16"), 10)
+    out[workload + "_bf16"] = _rate(g, torch, stream, bi.config(workload, storage="bf16"), 100)
     # the same cavity with fixed points, with the paper's first-order step and with the
     # second-order time discretisation (time_order = 2)
     out[workload + "_fixed"] = _rate(g, torch, stream, bi.config(workload, ale=0), 100)

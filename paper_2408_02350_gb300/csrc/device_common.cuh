@@ -90,34 +90,55 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// a + b = s + e exactly (Knuth's two-sum; additions only, so nothing is contracted)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Sum of two unevaluated pairs (hi + lo): the high parts added exactly, the low parts and
+// that addition's error added in FP32.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float bhi, float blo) {
+  float s, e;
+  two_sum(hi, bhi, s, e);
+  hi = s;
+  lo = (lo + blo) + e;
+}
+
 // Warp totals of N per-lane compensated FP32 sums (running sum s, compensation c: the
-// lane's value is s - c), combined in FP64: each lane's s - c is exact in double and the
-// additions are in double.  Every lane gets the totals.  For N = 4 the sums are reduced
-// transposed, so that a lane adds 6 doubles instead of 20 (FP64 runs at a small
-// fraction of the FP32 rate): at the step across 16 lanes a lane keeps two of the four
-// sums and passes the other two, across 8 lanes one of its two, then the three last
-// steps add one value; lane 8 q then holds the total of sum q, which is broadcast.
+// lane's value is the unevaluated pair s + (-c)), combined in FP64.  Every lane gets the
+// totals.  For N = 4 the sums are reduced transposed (FP64 runs at a small fraction of the
+// FP32 rate, so the additions that involve all 32 lanes are kept few): at the step across
+// 16 lanes a lane keeps two of the four sums and passes the other two, across 8 lanes
+// one of its two, both as FP32 pairs with exact high-part additions; the pair is then
+// converted to FP64 (exactly), the three last steps add in FP64, and lane 8 q, which holds
+// the total of sum q, broadcasts it.  Otherwise each lane's pair is converted and the sums
+// are reduced in FP64 one by one.
 template <int N>
 __device__ __forceinline__ void warp_total_f64(const float (&s)[N], const float (&c)[N], double (&out)[N]) {
-  double d[N];
-#pragma unroll
-  for (int q = 0; q < N; ++q) d[q] = (double)s[q] - (double)c[q];
   if constexpr (N == 4) {
     const int lane = threadIdx.x & 31;
     const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
-    double k0 = hi16 ? d[2] : d[0], k1 = hi16 ? d[3] : d[1];
-    const double p0 = hi16 ? d[0] : d[2], p1 = hi16 ? d[1] : d[3];
-    k0 += __shfl_xor_sync(0xffffffffu, p0, 16);
-    k1 += __shfl_xor_sync(0xffffffffu, p1, 16);
-    double k = hi8 ? k1 : k0;
-    k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+    // keep sums (0, 1) below lane 16, (2, 3) from lane 16 on
+    float k0h = hi16 ? s[2] : s[0], k0l = -(hi16 ? c[2] : c[0]);
+    float k1h = hi16 ? s[3] : s[1], k1l = -(hi16 ? c[3] : c[1]);
+    const float p0h = hi16 ? s[0] : s[2], p0l = -(hi16 ? c[0] : c[2]);
+    const float p1h = hi16 ? s[1] : s[3], p1l = -(hi16 ? c[1] : c[3]);
+    pair_add(k0h, k0l, __shfl_xor_sync(0xffffffffu, p0h, 16), __shfl_xor_sync(0xffffffffu, p0l, 16));
+    pair_add(k1h, k1l, __shfl_xor_sync(0xffffffffu, p1h, 16), __shfl_xor_sync(0xffffffffu, p1l, 16));
+    // keep the first of the two below lane 8 (mod 16), the second from lane 8 on
+    float kh = hi8 ? k1h : k0h, kl = hi8 ? k1l : k0l;
+    const float qh = hi8 ? k0h : k1h, ql = hi8 ? k0l : k1l;
+    pair_add(kh, kl, __shfl_xor_sync(0xffffffffu, qh, 8), __shfl_xor_sync(0xffffffffu, ql, 8));
+    double k = (double)kh + (double)kl;
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
 #pragma unroll
     for (int q = 0; q < 4; ++q) out[q] = __shfl_sync(0xffffffffu, k, 8 * q);
   } else {
 #pragma unroll
-    for (int q = 0; q < N; ++q) out[q] = warp_sum(d[q]);
+    for (int q = 0; q < N; ++q) out[q] = warp_sum((double)s[q] - (double)c[q]);
   }
 }
 

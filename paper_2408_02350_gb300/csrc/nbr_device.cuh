@@ -325,9 +325,10 @@ __device__ __forceinline__ void sep_hilo(const CaseView& cv, int i, int j, float
 
 // FP32/BF16 path, interior points: a group of LPP lanes per point.  Each lane
 // accumulates its share of the neighbours into the normal matrix A = sum w dr dr^T in
-// FP64 (separations and weights in FP32; w dr_a is exact in FP64 and each entry takes one
-// rounding per term), the group reduces A in FP64 with shuffles, and the group's first
-// lane solves the normal equations in FP64 (inverse by cofactors, Sec. 3.4.1: S = A^-1).
+// FP64 (separations, weights and the terms w dr_a dr_b in FP32, which carry the inputs'
+// own precision; the sums in FP64), the group reduces A in FP64 with shuffles, and the
+// group's first lane solves the normal equations in FP64 (inverse by cofactors,
+// Sec. 3.4.1: S = A^-1).
 // S is then rounded to FP32, and all lanes write the FP32 coefficients of their
 // neighbours.  Every lane of the warp calls it (shuffles over the full warp); lanes with
 // valid = false only take part in the shuffles.
@@ -347,15 +348,14 @@ __device__ __forceinline__ void stencil_grp_point(const CaseView& cv, const int 
     float r2 = 0.0f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) r2 = fmaf(dr[a], dr[a], r2);
-    const double w = (double)expf(nah2 * r2);
-    double dd[DIM], wd[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) { dd[a] = (double)dr[a]; wd[a] = w * dd[a]; }
+    const float w = expf(nah2 * r2);
     int q = 0;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a)
+    for (int a = 0; a < DIM; ++a) {
+      const float wa = w * dr[a];
 #pragma unroll
-      for (int b = a; b < DIM; ++b) { A[q] = fma(wd[a], dd[b], A[q]); ++q; }
+      for (int b = a; b < DIM; ++b) { A[q] += (double)(wa * dr[b]); ++q; }
+    }
   }
 #pragma unroll
   for (int o = LPP / 2; o >= 1; o >>= 1)

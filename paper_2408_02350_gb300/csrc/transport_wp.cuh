@@ -194,7 +194,7 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
   double Ud[DIM], u2d = 0.0;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) { Ud[a] = tot[1 + a] * rR; u2d = fma(Ud[a], Ud[a], u2d); }
-  const double Td = (tot[DIM + 1] - R * u2d) * rR * (1.0 / 3.0);
+  const double Td = fma(-R, u2d, tot[DIM + 1]) * rR * (1.0 / 3.0);
   const double rhod = R * (DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
   float Un[DIM];
 #pragma unroll
@@ -206,7 +206,8 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
 #pragma unroll
     for (int a = 0; a < 3; ++a) mo[1 + a] = a < DIM ? Ud[a < DIM ? a : 0] : 0.0;
     mo[4] = Td;
-    if (!(rhod > 0.0) || !(Td > 0.0) || !isfinite(rhod) || !isfinite(Td)) set_status(cv.status, ST_NONFINITE);
+    // (non-positive or non-finite values stay so in FP32)
+    if (!(rho > 0.0f) || !(Tn > 0.0f) || !isfinite(rho) || !isfinite(Tn)) set_status(cv.status, ST_NONFINITE);
   }
   float ca = 1.0f, cb = 0.0f, pref = 0.0f, nl2 = 0.0f;
   if (cv.tau_mode != 2 && rho > 0.0f && Tn > 0.0f) {

@@ -138,9 +138,11 @@ def test_adjoint_cavity_1000_steps_against_finite_differences(g):
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_autograd_function_gives_the_adjoint_gradient(g, storage):
-    # torch.autograd through LidFluxObjective: the gradients equal adjoint.gradient's
-    # exactly (the same kernels in the same order), and (FP64) match central differences
-    # in u_lid and Kn and a directional difference in f0 to 1e-3
+    # torch.autograd through LidFluxObjective: the gradients equal adjoint.gradient's (the
+    # same kernels in the same order: lam0 bit for bit; J and the parameter gradients are
+    # sums of per-point terms added by FP64 atomics, whose order varies, so to 1e-12), and
+    # (FP64) match central differences in u_lid and Kn and a directional difference in f0
+    # to 1e-3
     import torch
     from paper_2408_02350_gb300 import adjoint
     p = bi.config("cavity2d_n41_v16_f64", n=21, nv=8, vmax=4.0, kn=0.1, storage=storage)
@@ -161,8 +163,8 @@ def test_autograd_function_gives_the_adjoint_gradient(g, storage):
     # the same gradient through adjoint.gradient on a fresh context
     s2 = g.Solver([p], [cl])
     J2, du, dkn, lam0 = adjoint.gradient(s2, N, checkpoint_every=K, f0=f0)
-    assert J.item() == J2
-    assert gl.item() == du[0] and gk.item() == dkn
+    assert abs(J.item() - J2) <= 1e-12 * abs(J2)
+    assert abs(gl.item() - du[0]) <= 1e-12 * abs(du[0]) and abs(gk.item() - dkn) <= 1e-12 * abs(dkn)
     assert torch.equal(gf, lam0.to(gf.dtype))
     if storage == "f64":
         def J_of(lid_u, knv, f):

@@ -141,20 +141,28 @@ def test_cavity2d_fp32_100_steps(g):
     _cmp_moments(sim, s, 1e-4, "fp32 100 steps")
 
 
-def test_cavity2d_bf16_error_is_bounded(g):
-    # BF16 storage with FP32 arithmetic: 8-bit mantissa per stored value.  The velocity of a
-    # low-Mach flow is a small difference of O(1) terms, so its error is large; the bounds
-    # here are the measured errors with margin (regression guard), not the FP32 bar.
-    p = bi.config("cavity2d_n41_v16_f64")
+# BF16 storage with FP32 arithmetic does not meet the 1e-4 bar: every stored value is
+# rounded to an 8-bit mantissa each step, and round-to-nearest of a smooth Maxwellian is
+# not random across velocities, so the moment errors add up step after step; the low-Mach
+# velocity, a small difference of O(1) terms, carries the largest relative error.  The
+# bounds are twice the measured errors (41^2 x 16^2 after 100 steps: rho 4.76e-2, u 0.438,
+# T 4.89e-3; ALE 31^2 x 12^2 after 30 steps: 2.23e-2, 0.255, 1.63e-3; 3D 9^3 x 8^3 after
+# 10 steps: 5.50e-3, 5.50e-2, 2.32e-3), a regression guard on the measured floor.
+@pytest.mark.parametrize("name,over,steps,bounds", [
+    ("cavity2d_n41_v16_f64", {}, 100, (0.095, 0.88, 9.8e-3)),
+    ("cavity2d_ale_n201_v32_f32", {"n": 31, "nv": 12}, 30, (4.5e-2, 0.51, 3.3e-3)),
+    ("cavity3d_n41_v16_f32", {"n": 9, "nv": 8}, 10, (1.1e-2, 0.11, 4.7e-3))])
+def test_bf16_error_is_at_its_measured_floor(g, name, over, steps, bounds):
+    p = bi.config(name, **over)
     cl = bi.cloud_for(p)
     sim = oracle.Simulation(p, cl)
-    sim.run(100)
-    s = _gpu_run(g, p, cl, 100, storage="bf16")
+    sim.run(steps)
+    s = _gpu_run(g, p, cl, steps, storage="bf16")
     rho, u, T = s.moments()
     er = np.abs(rho - sim.rho).max() / np.abs(sim.rho).max()
     eT = np.abs(T - sim.T).max() / np.abs(sim.T).max()
     eu = np.abs(u - sim.U).max() / np.abs(sim.U).max()
-    assert er < 0.1 and eT < 0.02 and eu < 1.0, (er, eu, eT)
+    assert er < bounds[0] and eu < bounds[1] and eT < bounds[2], (er, eu, eT)
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-4)])
