@@ -675,6 +675,18 @@ def main():
     e2e_s = reduce_max(e2e_s, dist, "cuda")
     s.sync(stream)
     e2e_value = upd_per_step * args.e2e_steps * world / e2e_s
+    # host-to-device rate of the upload alone: an upload followed by the step that takes it
+    # (nothing else runs meanwhile), less the device time of a step
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        g.bgk_stage_f(s.ctx, 0, f_host, code)
+        g.bgk_step(s.ctx, 1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    up_ms = max(e0.elapsed_time(e1) / 3 - ms / args.steps, 1e-6)
+    h2d_gbs = h2d / (up_ms * 1e-3) / 1e9
+    s.sync(stream)
 
     # ---- plain FP64 GPU step on the same workload (the comparison the metric names) ----
     fp64 = None
@@ -752,9 +764,10 @@ def main():
                                  % (n * ncomp * NV * elem / 1e6)},
                 "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "steps": args.e2e_steps,
-                        "how": "bgk_stage_f of every step's f from pinned host memory (the upload overlaps "
-                               "the step before), bgk_step, bgk_moments to pinned host memory"},
+                        "steps": args.e2e_steps, "h2d_gbs": h2d_gbs,
+                        "how": "bgk_stage_f of every step's f from pinned host memory (four copies on "
+                               "four streams; the upload overlaps the step before), bgk_step, bgk_moments "
+                               "to pinned host memory; h2d_gbs: the upload alone"},
                 "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj, "batched": batched,
                 "manage": manage, "extra": extra}
         if world == 1 and not args.no_cpu_baseline:

@@ -196,7 +196,8 @@ int bgk_get_f(bgk_ctx* ctx, int32_t c, void* f, int32_t dtype, int32_t on_device
 
 /* Upload case c's distribution for the next bgk_step without waiting: f is
  * page-locked host memory, layout [n][ncomp][NV] of the storage type (NV a multiple of
- * 4).  The copy goes into a third device buffer on an internal stream, so it overlaps
+ * 4).  The copy goes into a third device buffer on internal streams (four copies of
+ * a quarter of the rows each, so that several copy engines share it), so it overlaps
  * whatever runs meanwhile (the step before, typically); the next bgk_step waits for it
  * on its stream, takes it as the state (as bgk_set_f would, moments included) and steps
  * from it.  A second call before that step replaces the pending input; bgk_manage and

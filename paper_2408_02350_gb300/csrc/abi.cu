@@ -106,7 +106,11 @@ struct bgk_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
   cudaStream_t side = nullptr;  // ALE motion and next-step lists, concurrent with the wall kernel
-  cudaStream_t copy = nullptr;  // uploads of bgk_stage_f
+  cudaStream_t copy = nullptr;  // uploads of bgk_stage_f (the first part, and the join)
+  // the other parts of an upload, each on a stream of its own so that several copy
+  // engines take part; ev_part[k] joins part k + 1 back into copy
+  cudaStream_t copy_part[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_part[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> allocs;
   DevStatus* status = nullptr;
   std::string err;
@@ -1078,7 +1082,13 @@ int bgk_stage_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype) {
     return fail(ctx, BGK_E_INVAL, "bgk_stage_f: f must be page-locked host memory");
   }
   int st;
-  if (!ctx->copy) CK(ctx, cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+  if (!ctx->copy) {
+    CK(ctx, cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    for (int k = 0; k < 3; ++k) {
+      CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_part[k], cudaStreamNonBlocking));
+      CK(ctx, cudaEventCreateWithFlags(&ctx->ev_part[k], cudaEventDisableTiming));
+    }
+  }
   if (!c.staged) {
     if ((st = dalloc_bytes(ctx, &c.staged, (size_t)c.cap_n * c.cv.ncomp * c.cv.NVp * c.s_bytes))) return st;
     CK(ctx, cudaEventCreateWithFlags(&c.ev_staged, cudaEventDisableTiming));
@@ -1086,8 +1096,20 @@ int bgk_stage_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype) {
   }
   // the staging buffer may be the state buffer a step replaced: wait until that step began
   if (c.free_recorded) CK(ctx, cudaStreamWaitEvent(ctx->copy, c.ev_free, 0));
-  const size_t bytes = (size_t)c.cv.n * c.cv.ncomp * c.cv.NVp * c.s_bytes;
-  CK(ctx, cudaMemcpyAsync(c.staged, f, bytes, cudaMemcpyHostToDevice, ctx->copy));
+  // four parts of whole rows (one cudaMemcpyAsync each) on four streams, joined into copy
+  const size_t row = (size_t)c.cv.ncomp * c.cv.NVp * c.s_bytes;
+  const size_t rows = (size_t)c.cv.n, per = (rows + 3) / 4;
+  for (int k = 0; k < 3; ++k) {
+    const size_t r0 = std::min(rows, per * (k + 1)), r1 = std::min(rows, per * (k + 2));
+    cudaStream_t q = ctx->copy_part[k];
+    if (c.free_recorded) CK(ctx, cudaStreamWaitEvent(q, c.ev_free, 0));
+    if (r1 > r0)
+      CK(ctx, cudaMemcpyAsync(static_cast<char*>(c.staged) + r0 * row, static_cast<const char*>(f) + r0 * row,
+                              (r1 - r0) * row, cudaMemcpyHostToDevice, q));
+    CK(ctx, cudaEventRecord(ctx->ev_part[k], q));
+  }
+  CK(ctx, cudaMemcpyAsync(c.staged, f, std::min(rows, per) * row, cudaMemcpyHostToDevice, ctx->copy));
+  for (int k = 0; k < 3; ++k) CK(ctx, cudaStreamWaitEvent(ctx->copy, ctx->ev_part[k], 0));
   CK(ctx, cudaEventRecord(c.ev_staged, ctx->copy));
   c.staged_ready = true;
   return BGK_OK;
@@ -1563,6 +1585,10 @@ void bgk_free(bgk_ctx* ctx) {
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->copy) cudaStreamDestroy(ctx->copy);
+  for (int k = 0; k < 3; ++k) {
+    if (ctx->copy_part[k]) cudaStreamDestroy(ctx->copy_part[k]);
+    if (ctx->ev_part[k]) cudaEventDestroy(ctx->ev_part[k]);
+  }
   for (auto& c : ctx->cases) {
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_staged) cudaEventDestroy(c.ev_staged);

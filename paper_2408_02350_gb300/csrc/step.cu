@@ -1396,61 +1396,84 @@ __global__ void k_moments(CaseView cv, const S* f) {
   }
 }
 
-// FP32/BF16 storage: one warp per point, each lane 4 consecutive velocities per chunk
-// (16-byte loads, velocity nodes staged in shared memory as FP32), the lanes'
-// Kahan-compensated FP32 sums added by warp shuffles as in the transport kernel, the
-// moments finished in FP64.
+// FP32/BF16 storage: each warp streams MOM_GP consecutive points in turn, each lane 4
+// consecutive velocities per chunk (16-byte loads, eight chunks in flight, velocity nodes
+// staged in shared memory as FP32) into Kahan-compensated FP32 sums.  A point's lane sums
+// are reduced across the warp as FP32 pairs with exact high-part additions (no FP64 on
+// the 32-lane path); once the warp has all its points, lane g converts point g's pair
+// totals to FP64 and forms rho, U, T in FP64, so each FP64 instruction serves MOM_GP
+// points (FP64 runs at a small fraction of the FP32 rate).  SH: the raw sums of the
+// velocity slab (in FP64) to the exchange buffer instead.
+constexpr int MOM_GP = 8, MOM_WARPS = 4;  // points per warp, warps per CTA
 template <typename S, int DIM, bool ROW, bool SH = false>
-__global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
-  constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4;
+__global__ void __launch_bounds__(32 * MOM_WARPS) k_moments_wp(CaseView cv, const S* f) {
+  constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4, NQ = DIM + 2;
   __shared__ float s_v[64];
+  __shared__ float2 s_tot[MOM_WARPS][MOM_GP][NQ];
   for (int t = threadIdx.x; t < cv.nv; t += blockDim.x) s_v[t] = (float)cv.vnodes[t];
   __syncthreads();
-  const int W = blockDim.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * W + (threadIdx.x >> 5);
-  if (i >= cv.n) return;
+  const int W = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * W + warp) * MOM_GP;
+  if (i0 >= cv.n) return;
+  const int np = min(MOM_GP, cv.n - i0);
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const int vk0 = SH ? cv.vk0 : 0;
   const float inv_nv = 1.0f / (float)nv;
-  const S* fi = f + (int64_t)i * NC * NVp;
-  float msum[DIM + 2], mcmp[DIM + 2];
+  for (int g = 0; g < np; ++g) {
+    const S* fi = f + (int64_t)(i0 + g) * NC * NVp;
+    float msum[NQ], mcmp[NQ];
 #pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) { msum[q] = 0.0f; mcmp[q] = 0.0f; }
-  for (int chunk = lane; chunk * VPL < NVp; chunk += 32) {
-    const int k0 = chunk * VPL;
-    float vel[VPL][DIM];
-    bool kin[VPL];
-    chunk_velocities<DIM, VPL, ROW>(k0 + vk0, nv, NV + vk0, inv_nv, s_v, vel, kin);
-    float g[NC][VPL];
+    for (int q = 0; q < NQ; ++q) { msum[q] = 0.0f; mcmp[q] = 0.0f; }
+#pragma unroll 8
+    for (int chunk = lane; chunk * VPL < NVp; chunk += 32) {
+      const int k0 = chunk * VPL;
+      float vel[VPL][DIM];
+      bool kin[VPL];
+      chunk_velocities<DIM, VPL, ROW>(k0 + vk0, nv, NV + vk0, inv_nv, s_v, vel, kin);
+      float gv[NC][VPL];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, g[c]);
-    float ps[DIM + 2];
+      for (int c = 0; c < NC; ++c) ldv<S, VPL>(fi + (int64_t)c * NVp + k0, gv[c]);
+      float ps[NQ];
 #pragma unroll
-    for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+      for (int q = 0; q < NQ; ++q) ps[q] = 0.0f;
 #pragma unroll
-    for (int e = 0; e < VPL; ++e) {
-      const float g0 = kin[e] ? g[0][e] : 0.0f;
-      float v2 = 0.0f;
-      ps[0] += g0;
+      for (int e = 0; e < VPL; ++e) {
+        const float g0 = kin[e] ? gv[0][e] : 0.0f;
+        float v2 = 0.0f;
+        ps[0] += g0;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g0, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
-      ps[DIM + 1] = fmaf(v2, g0, ps[DIM + 1]);
-      if (NC == 2) ps[DIM + 1] += kin[e] ? g[NC - 1][e] : 0.0f;
+        for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g0, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
+        ps[DIM + 1] = fmaf(v2, g0, ps[DIM + 1]);
+        if (NC == 2) ps[DIM + 1] += kin[e] ? gv[NC - 1][e] : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float y = ps[q] - mcmp[q];
+        const float t = msum[q] + y;
+        mcmp[q] = (t - msum[q]) - y;
+        msum[q] = t;
+      }
     }
+    // warp totals as FP32 pairs (every lane ends with the same pair)
 #pragma unroll
-    for (int q = 0; q < DIM + 2; ++q) {
-      const float y = ps[q] - mcmp[q];
-      const float t = msum[q] + y;
-      mcmp[q] = (t - msum[q]) - y;
-      msum[q] = t;
+    for (int q = 0; q < NQ; ++q) {
+      float hi = msum[q], lo = -mcmp[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        pair_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+      if (lane == 0) s_tot[warp][g][q] = make_float2(hi, lo);
     }
   }
-  double tot[DIM + 2];
-  warp_total_f64<DIM + 2>(msum, mcmp, tot);
-  if (SH && lane == 0) {
+  __syncwarp();
+  if (lane >= np) return;
+  const int i = i0 + lane;
+  double tot[NQ];
 #pragma unroll
-    for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = tot[q];
-  } else if (lane == 0) {
+  for (int q = 0; q < NQ; ++q) tot[q] = (double)s_tot[warp][lane][q].x + (double)s_tot[warp][lane][q].y;
+  if (SH) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) cv.xs[(int64_t)i * NQ + q] = tot[q];
+  } else {
     double rho, Un[3] = {0, 0, 0}, T;
     const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
@@ -1460,7 +1483,7 @@ __global__ void __launch_bounds__(256) k_moments_wp(CaseView cv, const S* f) {
 }
 
 int launch_moments(const CaseView& cv, const void* f, cudaStream_t s) {
-  const int W = 8, grid = (cv.n + W - 1) / W;
+  const int W = MOM_WARPS, grid = (cv.n + W * MOM_GP - 1) / (W * MOM_GP);
   const bool row = cv.nv % 4 == 0;
 #define BGK_MOM_WP(S, D)                                                                               \
   {                                                                                                    \
@@ -1561,7 +1584,7 @@ int launch_shard_walls(const CaseView& cv, int phase, cudaStream_t s) {
 }
 
 int launch_shard_partial(const CaseView& cv, cudaStream_t s) {
-  const int W = 8, grid = (cv.n + W - 1) / W;
+  const int W = MOM_WARPS, grid = (cv.n + W * MOM_GP - 1) / (W * MOM_GP);
   const bool row = cv.nv % 4 == 0;
 #define BGK_PART_WP(S, D)                                                                                   \
   {                                                                                                         \
