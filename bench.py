@@ -370,14 +370,15 @@ def extra_configs(g, torch, stream, workload: str) -> dict:
     return out
 
 
-def batched_cost(g, torch, stream, steps: int = 20) -> dict:
-    """64 independent 2D cavities (sides 41..121, 16..32 velocity nodes, FP32): batched + graph vs per case."""
-    ps = bi.batched_cases(64)
+def batched_cost(g, torch, stream, steps: int = 20, cases: int = 64) -> dict:
+    """64 independent 2D cavities (sides 41..121, 16..32 velocity nodes, FP32): batched + graph vs per case
+    (`cases` < 64 takes the first ones, for profiling runs)."""
+    ps = bi.batched_cases(cases)
     cls = [bi.cloud_for(p) for p in ps]
     s = g.Solver(ps, cls)
     s.set_maxwellian(stream=stream)
     upd = sum(len(c["kind"]) * p["nv"] ** 2 for p, c in zip(ps, cls))
-    out = {"workload": "batched2d_64", "cases": len(ps), "updates_per_step": upd}
+    out = {"workload": "batched2d_%d" % len(ps), "cases": len(ps), "updates_per_step": upd}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for mode, key in ((0, "per_case"), (2, "batched_graph")):
         g.bgk_set_batching(s.ctx, mode)
@@ -568,6 +569,10 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the Kn sweep and the FP64 41^2 cavity")
     ap.add_argument("--sharded", action="store_true",
                     help="one cavity split over the ranks by velocity slabs (strong scaling)")
+    ap.add_argument("--batch-cases", type=int, default=64,
+                    help="cavities of the batched measurement (fewer than 64 for profiling runs)")
+    ap.add_argument("--manage-steps", type=int, default=200,
+                    help="ALE steps before the point-management measurement")
     ap.add_argument("--no-sharded", action="store_true",
                     help="under torchrun, skip the velocity-sharded line beside the replica line")
     ap.add_argument("--time-order", type=int, default=None,
@@ -711,13 +716,13 @@ def main():
     adj = None
     manage = None
     if not args.no_manage and world == 1 and p.get("ale"):
-        manage = manage_cost(g, torch, stream, p, args.workload)
+        manage = manage_cost(g, torch, stream, p, args.workload, steps=args.manage_steps)
     if not args.no_adjoint and world == 1:
         adj = adjoint_cost(g, torch, stream)
 
     batched = None
     if not args.no_batched and world == 1:
-        batched = batched_cost(g, torch, stream)
+        batched = batched_cost(g, torch, stream, cases=args.batch_cases)
     extra = None
     if not args.no_extra and world == 1:
         extra = extra_configs(g, torch, stream, args.workload)

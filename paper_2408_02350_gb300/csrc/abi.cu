@@ -343,8 +343,9 @@ int move_and_prebuild(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
     if ((st = dalloc_bytes(ctx, &c.nx_P, n * cap * dim * dim * c.c_bytes))) return st;
     if ((st = dalloc_bytes(ctx, &c.nx_recon, n * cap * c.c_bytes))) return st;
     // empty rows until the first build fills them (a build cut short by a watchdog
-    // timeout leaves the rows it did not reach as they were)
-    CK(ctx, cudaMemset(c.nx_cnt, 0, sizeof(int32_t) * n));
+    // timeout leaves the rows it did not reach as they were); on s, before ev_fork, so
+    // that the side stream's build comes after it whatever stream s is
+    CK(ctx, cudaMemsetAsync(c.nx_cnt, 0, sizeof(int32_t) * n, s));
   }
   cudaStream_t q = ctx->side;
   CK(ctx, cudaEventRecord(c.ev_fork, s));
@@ -1208,10 +1209,17 @@ int bgk_sync(bgk_ctx* ctx, void* stream) {
         c.next_ready = false;
       }
     }
-    if (hs.flags & ST_OVERFLOW) return fail(ctx, BGK_E_NBR_OVERFLOW, "a point has more than max_nbrs neighbours");
-    if (hs.flags & ST_SINGULAR) return fail(ctx, BGK_E_SINGULAR, "singular WLS system (too few or degenerate neighbours)");
-    if (hs.flags & ST_NONFINITE) return fail(ctx, BGK_E_NONFINITE, "non-finite or non-positive density or temperature");
-    if (hs.flags & ST_TIMEOUT) return fail(ctx, BGK_E_TIMEOUT, "a bounded device wait gave up");
+    // the first condition in this order is the return code; the text names every one
+    char all[96];
+    snprintf(all, sizeof(all), " (device flags:%s%s%s%s)", hs.flags & ST_OVERFLOW ? " overflow" : "",
+             hs.flags & ST_SINGULAR ? " singular" : "", hs.flags & ST_NONFINITE ? " nonfinite" : "",
+             hs.flags & ST_TIMEOUT ? " timeout" : "");
+    if (hs.flags & ST_OVERFLOW) return fail(ctx, BGK_E_NBR_OVERFLOW, "a point has more than max_nbrs neighbours%s", all);
+    if (hs.flags & ST_SINGULAR)
+      return fail(ctx, BGK_E_SINGULAR, "singular WLS system (too few or degenerate neighbours)%s", all);
+    if (hs.flags & ST_NONFINITE)
+      return fail(ctx, BGK_E_NONFINITE, "non-finite or non-positive density or temperature%s", all);
+    if (hs.flags & ST_TIMEOUT) return fail(ctx, BGK_E_TIMEOUT, "a bounded device wait gave up%s", all);
   }
   return BGK_OK;
 }

@@ -471,8 +471,16 @@ __host__ __device__ inline size_t wp_smem_bytes(int W, int cap) {
          sizeof(float) * kahan_floats<DIM>() * W;
 }
 
+// Warps per CTA of the single-case first-order launch.  The CTA's points are consecutive
+// in Morton order, but a smaller CTA loses less to the uneven neighbour counts of its
+// warps (201^2 x 32^2 ALE cavity, transport ms: 1 warp 0.441, 2 0.440, 4 0.436, 8 0.440,
+// 16 0.453, 32 0.503).
+#ifndef BGK_WP_WARPS
+#define BGK_WP_WARPS 4
+#endif
 template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool SH = false, bool AVG = false>
-__global__ void __launch_bounds__(256, VPL == 4 ? 4 : 2) k_transport_wp(const CaseView cv) {
+__global__ void __launch_bounds__(32 * BGK_WP_WARPS, VPL == 4 ? 32 / BGK_WP_WARPS : 16 / BGK_WP_WARPS)
+    k_transport_wp(const CaseView cv) {
   constexpr int DD = DIM * DIM;
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -627,7 +635,7 @@ int transport_vpl = 0;  // 0 = automatic; 4 or 8 forces a width
 
 template <typename S, int DIM>
 static void launch_transport_wp(const CaseView& cv, cudaStream_t s) {
-  const int W = 8, threads = 32 * W;
+  const int W = BGK_WP_WARPS, threads = 32 * W;
   const size_t smem = wp_smem_bytes<DIM>(W, cv.cap);
   const int grid = (cv.n_int + W - 1) / W;
   const bool row4 = cv.nv % 4 == 0, row8 = cv.nv % 8 == 0 && cv.NVp % 8 == 0;

@@ -8,6 +8,12 @@
 
 namespace bgk {
 
+// Neighbour rows whose loads the compiler may overlap (unroll of the neighbour loop).
+#ifndef BGK_NBR_UNROLL
+#define BGK_NBR_UNROLL 2
+#endif
+constexpr int kNbrUnroll = BGK_NBR_UNROLL;
+
 // ---------------------------------------------------------------------------
 // transport + moments + relaxation, FP32 arithmetic (FP32 or BF16 storage):
 // one warp per interior point.  Each lane owns 4 consecutive velocities of
@@ -355,7 +361,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
 #pragma unroll
         for (int c = 0; c < NC; ++c) ap[c][q] = f2(0.0f, 0.0f);
       }
-#pragma unroll 2
+#pragma unroll kNbrUnroll
       for (int s = 0; s < m; ++s) {
         const int j = s_col[s];
         float P[DD];
@@ -391,7 +397,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
 #pragma unroll
         for (int c = 0; c < NC; ++c) ap[c][q] = f2(0.0f, 0.0f);
       }
-#pragma unroll 2
+#pragma unroll kNbrUnroll
       for (int s = 0; s < m; ++s) {
         const int j = s_col[s];
         float P[DD];
