@@ -682,7 +682,7 @@ int launch_transport_fp32(const CaseView& cv, cudaStream_t s) {
 
 template <typename S, int DIM>
 static void launch_transport_avg_wp(const CaseView& cv, cudaStream_t s) {
-  const int W = 8, threads = 32 * W;
+  const int W = BGK_WP_WARPS, threads = 32 * W;
   const size_t smem = wp_smem_bytes<DIM>(W, cv.cap);
   const int grid = (cv.n_int + W - 1) / W;
   if (cv.nv % 4 == 0) {
@@ -1517,7 +1517,7 @@ int launch_moments(const CaseView& cv, const void* f, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 template <typename S, int DIM>
 static void launch_shard_transport_wp(const CaseView& cv, cudaStream_t s) {
-  const int W = 8, threads = 32 * W;
+  const int W = BGK_WP_WARPS, threads = 32 * W;
   const size_t smem = wp_smem_bytes<DIM>(W, cv.cap);
   const int grid = (cv.n_int + W - 1) / W;
   const bool row4 = cv.nv % 4 == 0;
