@@ -558,6 +558,7 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.wall_T = q.wall_T;
     v.guard = q.guard;
     v.dv = q.vgrid == 1 ? 2.0 * q.vmax / (double)q.nv : 2.0 * q.vmax / (double)(q.nv - 1);
+    set_case_consts(v);
     for (int a = 0; a < 3; ++a) v.lid_u[a] = q.lid_u[a];
     v.skin = q.skin;
     v.body_wall = q.body_wall;
@@ -630,6 +631,7 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     v.wall_idx = dwall;
 
     if ((st = dalloc(ctx, &v.vnodes, q.nv))) return bail(st);
+    if ((st = dalloc(ctx, &v.vnodes_f, q.nv))) return bail(st);
     if ((st = dalloc(ctx, &v.xf, ncap * dim))) return bail(st);
     if ((st = dalloc(ctx, &v.xlo, ncap * dim))) return bail(st);
     if ((st = dalloc(ctx, &v.cell_of, ncap))) return bail(st);
@@ -1332,6 +1334,7 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
   v.kn = p->kn;
   v.tau_mode = p->tau_mode;
   v.dt = p->dt;
+  set_case_consts(v);
   v.wall_T = p->wall_T;
   v.lid_wall = p->lid_wall;
   if (v.ale != p->ale) {

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_adj_prep(CaseView cv, C* FT, C* Y) {
     double U[3] = {0, 0, 0}, u2 = 0.0;
     for (int a = 0; a < DIM; ++a) { U[a] = part[1 + a] / R; u2 += U[a] * U[a]; }
     const double T = (part[DIM + 1] - R * u2) / (3.0 * R);
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     const double rho = R * wv, pi = 3.14159265358979323846;
     double a = 1.0, b = 0.0;
     if (cv.tau_mode != 2) {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_adj_relax(CaseView cv, const C* FT, con
     double U[3] = {0, 0, 0}, u2 = 0.0;
     for (int a = 0; a < DIM; ++a) { U[a] = part[1 + a] / R; u2 += U[a] * U[a]; }
     const double T = (part[DIM + 1] - R * u2) / (3.0 * R);
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     const double rho = R * wv;
     double tau = 0.0, a = 1.0, b = 0.0, dadtau = 0.0;
     if (cv.tau_mode != 2) {
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(256) k_adj_relax(CaseView cv, const C* FT, con
       g_T += dLda * dadtau * (-tau / (2.0 * Td));
     }
     atomicAdd(&dtheta[3], dLda * dadtau * tau / cv.kn);
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     s_fin[12] = g_rho * wv - g_T * Td / R;  // constant part: g_rho wv - 3 T g_T / (3R)
     s_fin[13] = g_T / (3.0 * R);            // coefficient of |v - U|^2, and the h term
     for (int d = 0; d < DIM; ++d) s_red[d] = b * sums[5 + d] / Td / R;  // g_U_d / R
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(256) k_objective(CaseView cv, int nlid, double
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   for (int t = threadIdx.x; t < nv; t += blockDim.x) s_nodes[t] = cv.vnodes[t];
   __syncthreads();
-  const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+  const double wv = cv.wv;
   const S* fb = reinterpret_cast<const S*>(cv.f_in) + (int64_t)b * NC * NVp;
   double acc[1] = {0.0};
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(256) k_adj_relax_wp(CaseView cv, const float* 
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   float* s_v = reinterpret_cast<float*>(smem);
   int32_t* s_wb = reinterpret_cast<int32_t*>(smem + 256) + warp * cap * 3;  // (point b, wall slot w, slot of i in b)
-  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = (float)cv.vnodes[q];
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = cv.vnodes_f[q];
   __syncthreads();
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
@@ -557,11 +557,11 @@ __global__ void __launch_bounds__(256) k_adj_relax_wp(CaseView cv, const float* 
   float U[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) U[a] = (float)mo[1 + a];
-  const float wv = (float)(DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
+  const float wv = cv.wv_f;
   const float R = rho / wv;
   float tau = 0.0f, ca = 1.0f, cb = 0.0f, dadtau = 0.0f;
   if (cv.tau_mode != 2) {
-    const float kn = (float)cv.kn, dtf = (float)cv.dt;
+    const float kn = cv.kn_f, dtf = cv.dt_f;
     tau = cv.tau_mode == 1 ? 0.7978845608f * kn : 0.7978845608f * kn / (rho * sqrtf(T));
     ca = tau / (tau + dtf);
     cb = dtf / (tau + dtf);
@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(256) k_adj_transport_wp(CaseView cv, const flo
   float* s_v = reinterpret_cast<float*>(smem);
   float* s_P = reinterpret_cast<float*>(smem + 256) + (size_t)warp * cap * DD;  // coefficient of p in i's stencil
   int32_t* s_i = reinterpret_cast<int32_t*>(smem + 256 + sizeof(float) * (size_t)W * cap * DD) + warp * cap;
-  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = (float)cv.vnodes[q];
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) s_v[q] = cv.vnodes_f[q];
   __syncthreads();
   const int p = blockIdx.x * W + warp;
   if (p >= cv.n) return;
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(256) k_adj_transport_wp(CaseView cv, const flo
   const float inv_nv = 1.0f / (float)nv;
   const int nchunk = NVp >> 2, nslice = (nchunk + 31) >> 5;
   const int64_t rowlen = (int64_t)NC * NVp;
-  const float two_dt = (float)(2.0 * cv.dt);
+  const float two_dt = cv.two_dt_f;
   for (int sl = 0; sl < nslice; ++sl) {
     const int chunk = sl * 32 + lane;
     if (chunk >= nchunk) break;

@@ -52,8 +52,14 @@ struct CaseView {
   int32_t nc, ncell;  // cells per axis, total cells
   double dt, h, alpha, kn, wall_T, guard, dv;
   double lid_u[3];
+  // set on the host with the values above (set_case_consts): the quadrature weight dv^dim
+  // and FP32 copies of per-case constants, so that the FP32 kernels convert nothing per
+  // point (conversions from FP64 run on the FP64 pipe, a small fraction of the FP32 rate)
+  double wv;
+  float dt_f, two_dt_f, kn_f, wv_f;
 
   double* vnodes;          // [nv] velocity nodes (FP64)
+  float* vnodes_f;         // [nv] the same nodes rounded to FP32
   double* x;               // [n][dim]
   const int32_t* kind;     // [n]
   const double* normal;    // [n][dim]
@@ -111,6 +117,15 @@ struct CaseView {
   // transport stage (null otherwise)
   void* f_avg;
 };
+
+// The derived per-case constants of CaseView (wv and the FP32 copies), from dim, dt, kn, dv.
+inline void set_case_consts(CaseView& v) {
+  v.wv = v.dim == 2 ? v.dv * v.dv : v.dv * v.dv * v.dv;
+  v.dt_f = (float)v.dt;
+  v.two_dt_f = (float)(2.0 * v.dt);
+  v.kn_f = (float)v.kn;
+  v.wv_f = (float)v.wv;
+}
 
 // Launchers (stream-ordered; each returns the number of kernels launched).
 int launch_init_tables(const CaseView& cv, cudaStream_t s);

@@ -102,7 +102,7 @@ __device__ __forceinline__ void relax_cta(const CaseView& cv, const int i, const
   C* s_fin = reinterpret_cast<C*>(s_red + 6 * 32);  // past the slots block_sum0 uses (5 x 32)
   if (threadIdx.x == 0) {
     double rho, Un[3] = {0, 0, 0}, T;
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
     double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
     mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(256) k_relax_half_wp(const CaseView cv) {
   float* s_v = s_vall + warp * 64;
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
-  for (int q = lane; q < cv.nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  for (int q = lane; q < cv.nv; q += 32) s_v[q] = cv.vnodes_f[q];
   __syncwarp();
   const int i = cv.int_idx[t];
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(256) k_shard_relax_wp(const CaseView cv) {
   float* s_v = s_vall + warp * 64;
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
-  for (int q = lane; q < cv.nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  for (int q = lane; q < cv.nv; q += 32) s_v[q] = cv.vnodes_f[q];
   __syncwarp();
   const int i = cv.int_idx[t];
   double tot[DIM + 2];
@@ -924,7 +924,7 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   }
   if (threadIdx.x == 0) {
     double rho, Un[3] = {0, 0, 0}, T;
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
     double* mo = cv.mom + (int64_t)b * MOM_STRIDE;
     mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
@@ -964,7 +964,7 @@ __device__ __forceinline__ void walls_point_v4(const CaseView& cv, const int w, 
     }
     if (lane == 0) s_j[0] = mi;
   }
-  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (float)cv.vnodes[t];
+  for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = cv.vnodes_f[t];
   __syncthreads();
   const int mi = s_j[0];
   const int64_t rowlen = (int64_t)NC * NVp;
@@ -1061,7 +1061,7 @@ __device__ __forceinline__ void walls_point_v4(const CaseView& cv, const int w, 
   block_sum0<DIM + 2, float>(part, tot, s_red);
   if (threadIdx.x == 0) {
     double rho, Un[3] = {0, 0, 0}, T;
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
     double* mo = cv.mom + (int64_t)b * MOM_STRIDE;
     mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
@@ -1235,7 +1235,11 @@ __global__ void k_mw_table(CaseView cv) {
 // symmetric about zero (Sec. 3.3).
 __global__ void k_nodes(CaseView cv) {
   const int j = threadIdx.x;
-  if (j < cv.nv) cv.vnodes[j] = __dmul_rn(__dadd_rn((double)j, -0.5 * (double)(cv.nv - 1)), cv.dv);
+  if (j < cv.nv) {
+    const double v = __dmul_rn(__dadd_rn((double)j, -0.5 * (double)(cv.nv - 1)), cv.dv);
+    cv.vnodes[j] = v;
+    cv.vnodes_f[j] = (float)v;
+  }
 }
 
 int launch_init_tables(const CaseView& cv, cudaStream_t s) {
@@ -1397,7 +1401,7 @@ __global__ void k_moments(CaseView cv, const S* f) {
     for (int q = 0; q < DIM + 2; ++q) cv.xs[(int64_t)i * (DIM + 2) + q] = tot[q];
   } else if (threadIdx.x == 0) {
     double rho, Un[3] = {0, 0, 0}, T;
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
     double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
     mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
@@ -1418,7 +1422,7 @@ __global__ void __launch_bounds__(32 * MOM_WARPS) k_moments_wp(CaseView cv, cons
   constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4, NQ = DIM + 2;
   __shared__ float s_v[64];
   __shared__ float2 s_tot[MOM_WARPS][MOM_GP][NQ];
-  for (int t = threadIdx.x; t < cv.nv; t += blockDim.x) s_v[t] = (float)cv.vnodes[t];
+  for (int t = threadIdx.x; t < cv.nv; t += blockDim.x) s_v[t] = cv.vnodes_f[t];
   __syncthreads();
   const int W = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * W + warp) * MOM_GP;
@@ -1483,7 +1487,7 @@ __global__ void __launch_bounds__(32 * MOM_WARPS) k_moments_wp(CaseView cv, cons
     for (int q = 0; q < NQ; ++q) cv.xs[(int64_t)i * NQ + q] = tot[q];
   } else {
     double rho, Un[3] = {0, 0, 0}, T;
-    const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+    const double wv = cv.wv;
     finish_moments<DIM>(tot, wv, &rho, Un, &T);
     double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
     mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;
@@ -1620,7 +1624,7 @@ __global__ void k_shard_moments(CaseView cv) {
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) tot[q] = cv.xs[(int64_t)i * (DIM + 2) + q];
   double rho, Un[3] = {0, 0, 0}, T;
-  const double wv = DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv;
+  const double wv = cv.wv;
   finish_moments<DIM>(tot, wv, &rho, Un, &T);
   double* mo = cv.mom + (int64_t)i * MOM_STRIDE;
   mo[0] = rho; mo[1] = Un[0]; mo[2] = Un[1]; mo[3] = Un[2]; mo[4] = T;

@@ -201,7 +201,7 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
 #pragma unroll
   for (int a = 0; a < DIM; ++a) { Ud[a] = tot[1 + a] * rR; u2d = fma(Ud[a], Ud[a], u2d); }
   const double Td = fma(-R, u2d, tot[DIM + 1]) * rR * (1.0 / 3.0);
-  const double rhod = R * (DIM == 2 ? cv.dv * cv.dv : cv.dv * cv.dv * cv.dv);
+  const double rhod = R * cv.wv;
   float Un[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) Un[a] = (float)Ud[a];
@@ -217,7 +217,7 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
   }
   float ca = 1.0f, cb = 0.0f, pref = 0.0f, nl2 = 0.0f;
   if (cv.tau_mode != 2 && rho > 0.0f && Tn > 0.0f) {
-    const float kn = (float)cv.kn, dtf = (float)cv.dt;
+    const float kn = cv.kn_f, dtf = cv.dt_f;
     const float tau = cv.tau_mode == 1 ? 0.7978845608f * kn : 0.7978845608f * kn / (rho * sqrtf(Tn));
     if (RK == 1) {
       // exact relaxation over dt/2 (the second-order step): f = e f + (1 - e) M, e = exp(-dt/(2 tau))
@@ -307,7 +307,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
   const int vk0 = SH ? cv.vk0 : 0;
   const float inv_nv = 1.0f / (float)nv;
   const int m = cv.cnt[i];
-  for (int q = lane; q < nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  for (int q = lane; q < nv; q += 32) s_v[q] = cv.vnodes_f[q];
   {
     const int32_t* col = cv.col + (int64_t)i * cap;
     const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
@@ -324,7 +324,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
   const int nslice = (nchunk + 31) >> 5;
   const int64_t rowlen = (int64_t)NC * NVp;
   const S* fbase = reinterpret_cast<const S*>(cv.f_in);
-  const float two_dt = (float)(2.0 * cv.dt);
+  const float two_dt = cv.two_dt_f;
 
   // KS: s_k[q * 32 + lane] holds running sum q (q < DIM + 2) and its compensation
   // (q >= DIM + 2); otherwise rsum / rcmp do
@@ -472,7 +472,7 @@ __device__ __forceinline__ void transport_point_mirror(const CaseView& cv, const
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const float inv_nv = 1.0f / (float)nv;
   const int m = cv.cnt[i];
-  for (int q = lane; q < nv; q += 32) s_v[q] = (float)cv.vnodes[q];
+  for (int q = lane; q < nv; q += 32) s_v[q] = cv.vnodes_f[q];
   {
     const int32_t* col = cv.col + (int64_t)i * cap;
     const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
@@ -485,7 +485,7 @@ __device__ __forceinline__ void transport_point_mirror(const CaseView& cv, const
   const int nslice = (nchunk + 31) >> 5;
   const int64_t rowlen = (int64_t)NC * NVp;
   const S* fbase = reinterpret_cast<const S*>(cv.f_in);
-  const float two_dt = (float)(2.0 * cv.dt);
+  const float two_dt = cv.two_dt_f;
   const float2 neg1 = f2(-1.0f, -1.0f);
 
   float rsum[DIM + 2], rcmp[DIM + 2];
