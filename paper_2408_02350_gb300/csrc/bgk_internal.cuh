@@ -55,8 +55,9 @@ struct CaseView {
   // set on the host with the values above (set_case_consts): the quadrature weight dv^dim
   // and FP32 copies of per-case constants, so that the FP32 kernels convert nothing per
   // point (conversions from FP64 run on the FP64 pipe, a small fraction of the FP32 rate)
-  double wv;
+  double wv, h2;  // dv^dim; h^2 (IEEE double product, as the exact neighbour test takes it)
   float dt_f, two_dt_f, kn_f, wv_f;
+  float nah2_f, inv_h_f;  // -alpha / h^2 and 1 / h in FP32 (Gaussian weights of the FP32 stencils)
 
   double* vnodes;          // [nv] velocity nodes (FP64)
   float* vnodes_f;         // [nv] the same nodes rounded to FP32
@@ -118,9 +119,13 @@ struct CaseView {
   void* f_avg;
 };
 
-// The derived per-case constants of CaseView (wv and the FP32 copies), from dim, dt, kn, dv.
+// The derived per-case constants of CaseView (wv, h2 and the FP32 copies), from dim, dt,
+// kn, dv, h, alpha.
 inline void set_case_consts(CaseView& v) {
   v.wv = v.dim == 2 ? v.dv * v.dv : v.dv * v.dv * v.dv;
+  v.h2 = v.h * v.h;
+  v.nah2_f = (float)(-v.alpha / (v.h * v.h));
+  v.inv_h_f = (float)(1.0 / v.h);
   v.dt_f = (float)v.dt;
   v.two_dt_f = (float)(2.0 * v.dt);
   v.kn_f = (float)v.kn;

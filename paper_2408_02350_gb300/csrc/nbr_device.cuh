@@ -92,7 +92,7 @@ __device__ __forceinline__ void nbr_warp_point(const CaseView& cv, const int i, 
   float xif[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) xif[a] = cv.xf[(int64_t)i * DIM + a];
-  const double h2 = __dmul_rn(cv.h, cv.h);
+  const double h2 = cv.h2;
   int ci[3] = {0, 0, 0};
   {
     int r = cv.cell_of[i];
@@ -202,7 +202,7 @@ __device__ __forceinline__ void filter_warp_point(const CaseView& cv, const int 
   float xif[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) xif[a] = cv.xf[(int64_t)i * DIM + a];
-  const double h2 = __dmul_rn(cv.h, cv.h);
+  const double h2 = cv.h2;
   int m = 0;
   for (int qb = 0; qb < nc; qb += 32) {
     const int q = qb + lane;
@@ -258,7 +258,7 @@ __device__ __forceinline__ void filter_group_point(const CaseView& cv, const int
   float xif[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) xif[a] = valid ? cv.xf[(int64_t)i * DIM + a] : 0.0f;
-  const double h2 = __dmul_rn(cv.h, cv.h);
+  const double h2 = cv.h2;
   const int ncmax = __reduce_max_sync(0xffffffffu, nc);
   int m = 0;  // uniform within the group
   for (int qb = 0; qb < ncmax; qb += 4 * U) {
@@ -338,7 +338,7 @@ __device__ __forceinline__ void stencil_grp_point(const CaseView& cv, const int 
   const int m = valid ? cv.cnt[i] : 0;
   const int cap = cv.cap;
   const int32_t* row = cv.col + (int64_t)i * cap;
-  const float nah2 = (float)(-cv.alpha / (cv.h * cv.h));
+  const float nah2 = cv.nah2_f;
   double A[NA];
 #pragma unroll
   for (int q = 0; q < NA; ++q) A[q] = 0.0;

@@ -423,8 +423,8 @@ __global__ void __launch_bounds__(256) k_recon_grp(CaseView cv) {
   const int m = valid ? cv.cnt[i] : 0;
   const int cap = cv.cap;
   const int32_t* row = cv.col + (int64_t)i * cap;
-  const float nah2 = (float)(-cv.alpha / (cv.h * cv.h));
-  const float inv_h = (float)(1.0 / cv.h);  // basis (1, dr/h): same weights, O(1) matrix entries
+  const float nah2 = cv.nah2_f;
+  const float inv_h = cv.inv_h_f;  // basis (1, dr/h): same weights, O(1) matrix entries
   float B[NB], wsum = 0.0f;
   int ninner = 0;
 #pragma unroll

@@ -93,6 +93,7 @@ extern "C" int bgk_neighbours_noalloc(int32_t dim, int64_t n, const double* x, d
   cv.cap = cap;
   cv.periodic = periodic;
   cv.h = h;
+  set_case_consts(cv);  // h^2 for the exact neighbour test
   cv.nc = nc;
   cv.ncell = (int32_t)ncell;
   cv.x = const_cast<double*>(x);
