@@ -18,6 +18,8 @@
 //   reconstruction from interior f^{n+1}; leaving velocities get
 //   rho_w M_w(v) with rho_w from zero net mass flux.
 // k_move: x += dt U^{n+1} at interior points (FP64, no fused multiply-add).
+#include <algorithm>
+
 #include "bgk_internal.cuh"
 #include "device_common.cuh"
 #include "motion.cuh"
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(256) k_shard_relax_wp(const CaseView cv) {
 
 // Fixed points with a mirror-symmetric velocity grid (nv % 4 == 0, NV % 8 == 0): one
 // warp per interior point, each lane a velocity chunk and its mirror chunk; 79
-// registers, 3 CTAs per SM.  Used in 3D, where it saves a quarter of the
+// registers, 24 warps per SM.  Used in 3D, where it saves a quarter of the
 // per-neighbour instructions (41^3 x 16^3 cavity: 6.63 against 7.50 ms per step with
 // the 8-velocity kernel); in 2D the extra registers cost more than the saved
 // instructions (201^2 x 32^2 fixed points: 0.483 ms at 4 CTAs per SM with spills,
@@ -1326,13 +1328,15 @@ int launch_move(const CaseView& cv, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // initial Maxwellian, moments of a given f, layout conversion
 // ---------------------------------------------------------------------------
+// The same Maxwellian at every point: thread k of column block y evaluates M(v_k) once and
+// writes it (and T0 M, the Chu h component) into the rows of the points of its block
+// (blockIdx.x, blockIdx.x + gridDim.x, ...), so that a grid of a few hundred blocks
+// evaluates a few hundred rows' worth of exponentials, not one per (point, velocity).
 template <typename S, int DIM>
 __global__ void k_set_maxwellian(CaseView cv, double rho0, double u0, double u1, double u2, double T0) {
   constexpr int NC = DIM == 2 ? 2 : 1;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)cv.n * cv.NVp;
-  if (t >= total) return;
-  const int i = (int)(t / cv.NVp), k = (int)(t % cv.NVp);
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= cv.NVp) return;
   const double pi = 3.14159265358979323846;
   double M = 0.0;
   if (k < cv.NV) {
@@ -1347,14 +1351,17 @@ __global__ void k_set_maxwellian(CaseView cv, double rho0, double u0, double u1,
     const double pref = DIM == 2 ? rho0 / (2.0 * pi * T0) : rho0 / pow(2.0 * pi * T0, 1.5);
     M = pref * exp(-c2 / (2.0 * T0));
   }
-  S* f = reinterpret_cast<S*>(cv.f_in) + (int64_t)i * NC * cv.NVp;
-  st1(f + k, (decltype(ld1(f)))M);
-  if (NC == 2) st1(f + cv.NVp + k, (decltype(ld1(f)))(T0 * M));
+  using C = decltype(ld1(reinterpret_cast<const S*>(cv.f_in)));
+  const C m0 = (C)M, m1 = (C)(T0 * M);
+  for (int i = blockIdx.x; i < cv.n; i += gridDim.x) {
+    S* f = reinterpret_cast<S*>(cv.f_in) + (int64_t)i * NC * cv.NVp;
+    st1(f + k, m0);
+    if (NC == 2) st1(f + cv.NVp + k, m1);
+  }
 }
 
 int launch_set_maxwellian(const CaseView& cv, double rho0, const double* u0, double T0, cudaStream_t s) {
-  const int64_t total = (int64_t)cv.n * cv.NVp;
-  const int g = (int)((total + 255) / 256);
+  const dim3 g((unsigned)std::min(cv.n, 1216), (unsigned)((cv.NVp + 255) / 256));
   if (cv.dim == 2) {
     if (cv.storage == 0) k_set_maxwellian<double, 2><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], 0.0, T0);
     else if (cv.storage == 1) k_set_maxwellian<float, 2><<<g, 256, 0, s>>>(cv, rho0, u0[0], u0[1], 0.0, T0);

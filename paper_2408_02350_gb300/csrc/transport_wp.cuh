@@ -287,8 +287,8 @@ __device__ __forceinline__ void partial_out(const CaseView& cv, const int i, con
 // consecutive velocities of every (32 VPL)-velocity slice.  With KS the lanes'
 // compensated moment sums live in s_k between slices and the velocities are
 // recomputed after the neighbour loop, which keeps the 4-velocity body within 64
-// registers (4 CTAs of 8 warps per SM: 0.432 against 0.465 ms at 3 CTAs on the
-// 201^2 x 32^2 ALE cavity); without KS they stay in registers (the 8-velocity 3D
+// registers (32 warps per SM: 0.432 against 0.465 ms with 24 on the 201^2 x 32^2 ALE
+// cavity); without KS they stay in registers (the 8-velocity 3D
 // body and the batched kernel, which lose with KS).  SH (sharded step): the row holds
 // the velocity slab that starts at cv.vk0, and the slab's moment sums of f~ go to the
 // exchange buffer instead of the relaxation.  AVG (second stage of the second-order
