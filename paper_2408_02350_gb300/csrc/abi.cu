@@ -19,6 +19,11 @@
 #include <vector>
 
 #include "bgk.h"
+
+// Parts (and streams) of one staged upload (bgk_stage_f).
+#ifndef BGK_UPLOAD_PARTS
+#define BGK_UPLOAD_PARTS 4
+#endif
 #include "bgk_internal.cuh"
 
 using namespace bgk;
@@ -109,8 +114,8 @@ struct bgk_ctx {
   cudaStream_t copy = nullptr;  // uploads of bgk_stage_f (the first part, and the join)
   // the other parts of an upload, each on a stream of its own so that several copy
   // engines take part; ev_part[k] joins part k + 1 back into copy
-  cudaStream_t copy_part[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t ev_part[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t copy_part[BGK_UPLOAD_PARTS - 1] = {};
+  cudaEvent_t ev_part[BGK_UPLOAD_PARTS - 1] = {};
   std::vector<void*> allocs;
   DevStatus* status = nullptr;
   std::string err;
@@ -1087,7 +1092,7 @@ int bgk_stage_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype) {
   int st;
   if (!ctx->copy) {
     CK(ctx, cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < BGK_UPLOAD_PARTS - 1; ++k) {
       CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_part[k], cudaStreamNonBlocking));
       CK(ctx, cudaEventCreateWithFlags(&ctx->ev_part[k], cudaEventDisableTiming));
     }
@@ -1099,10 +1104,11 @@ int bgk_stage_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype) {
   }
   // the staging buffer may be the state buffer a step replaced: wait until that step began
   if (c.free_recorded) CK(ctx, cudaStreamWaitEvent(ctx->copy, c.ev_free, 0));
-  // four parts of whole rows (one cudaMemcpyAsync each) on four streams, joined into copy
+  // BGK_UPLOAD_PARTS parts of whole rows (one cudaMemcpyAsync each) on as many streams,
+  // joined into copy
   const size_t row = (size_t)c.cv.ncomp * c.cv.NVp * c.s_bytes;
-  const size_t rows = (size_t)c.cv.n, per = (rows + 3) / 4;
-  for (int k = 0; k < 3; ++k) {
+  const size_t rows = (size_t)c.cv.n, per = (rows + BGK_UPLOAD_PARTS - 1) / BGK_UPLOAD_PARTS;
+  for (int k = 0; k < BGK_UPLOAD_PARTS - 1; ++k) {
     const size_t r0 = std::min(rows, per * (k + 1)), r1 = std::min(rows, per * (k + 2));
     cudaStream_t q = ctx->copy_part[k];
     if (c.free_recorded) CK(ctx, cudaStreamWaitEvent(q, c.ev_free, 0));
@@ -1112,7 +1118,7 @@ int bgk_stage_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype) {
     CK(ctx, cudaEventRecord(ctx->ev_part[k], q));
   }
   CK(ctx, cudaMemcpyAsync(c.staged, f, std::min(rows, per) * row, cudaMemcpyHostToDevice, ctx->copy));
-  for (int k = 0; k < 3; ++k) CK(ctx, cudaStreamWaitEvent(ctx->copy, ctx->ev_part[k], 0));
+  for (int k = 0; k < BGK_UPLOAD_PARTS - 1; ++k) CK(ctx, cudaStreamWaitEvent(ctx->copy, ctx->ev_part[k], 0));
   CK(ctx, cudaEventRecord(c.ev_staged, ctx->copy));
   c.staged_ready = true;
   return BGK_OK;
@@ -1596,7 +1602,7 @@ void bgk_free(bgk_ctx* ctx) {
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->copy) cudaStreamDestroy(ctx->copy);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < BGK_UPLOAD_PARTS - 1; ++k) {
     if (ctx->copy_part[k]) cudaStreamDestroy(ctx->copy_part[k]);
     if (ctx->ev_part[k]) cudaEventDestroy(ctx->ev_part[k]);
   }
