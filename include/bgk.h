@@ -70,7 +70,10 @@ typedef struct bgk_params {
   int32_t periodic;  /* 1: periodic unit box (minimum image), no walls */
   int32_t lid_wall;  /* wall id whose points move with lid_u (diffuse reflection) */
   int32_t max_nbrs;  /* neighbour-list capacity per point */
-  int32_t storage;   /* bgk_storage of f: F64 computes in double, F32/BF16 in float */
+  int32_t storage;   /* bgk_storage of f: F64 computes in double, F32/BF16 in float,
+                        except that the WLS normal matrices are accumulated and solved
+                        and the moment sums combined (rho, U, T formed) in double for
+                        every storage type */
   double dt;         /* time step */
   double h;          /* neighbour radius and WLS support (Sec. 3.4.1) */
   double alpha;      /* Gaussian weight w = exp(-alpha r^2 / h^2), Eq. (weight) */
