@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define BGK_ABI_VERSION 8
+#define BGK_ABI_VERSION 9
 
 typedef struct bgk_ctx bgk_ctx;
 
@@ -48,7 +48,9 @@ typedef enum bgk_status {
   BGK_E_NBR_OVERFLOW = 5,  /* a point has more than max_nbrs neighbours */
   BGK_E_NONFINITE = 6,     /* non-finite or non-positive density or temperature */
   BGK_E_TIMEOUT = 7,       /* a bounded device wait gave up */
-  BGK_E_STATE = 8          /* call not valid in the context's state */
+  BGK_E_STATE = 8,         /* call not valid in the context's state */
+  BGK_E_BOUNDS = 9         /* (bounds-checked debug build only) a neighbour or point index
+                              outside the point range was found and its access skipped */
 } bgk_status;
 
 typedef enum bgk_storage { BGK_F64 = 0, BGK_F32 = 1, BGK_BF16 = 2 } bgk_storage;

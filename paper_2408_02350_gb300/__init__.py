@@ -16,16 +16,21 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libbgk.so")
+# BGK_LIBRARY=debug selects the bounds-checked debug build (libbgk_debug.so, built by
+# _build.build(debug=True)): every neighbour and point index a kernel loads is checked
+# against the point range, a bad one is recorded (BGK_E_BOUNDS at the next bgk_sync) and
+# its access skipped.
+LIB_PATH = os.path.join(_HERE, "libbgk_debug.so" if os.environ.get("BGK_LIBRARY") == "debug" else "libbgk.so")
 
 BGK_OK, BGK_E_INVAL, BGK_E_NOMEM, BGK_E_CUDA, BGK_E_SINGULAR = 0, 1, 2, 3, 4
-BGK_E_NBR_OVERFLOW, BGK_E_NONFINITE, BGK_E_TIMEOUT, BGK_E_STATE = 5, 6, 7, 8
+BGK_E_NBR_OVERFLOW, BGK_E_NONFINITE, BGK_E_TIMEOUT, BGK_E_STATE, BGK_E_BOUNDS = 5, 6, 7, 8, 9
 BGK_F64, BGK_F32, BGK_BF16 = 0, 1, 2
 STORAGE = {"f64": BGK_F64, "f32": BGK_F32, "bf16": BGK_BF16}
 K_TRANSPORT, K_WALLS, K_NBR, K_STENCIL, K_MOVE, K_ADJOINT, K_BATCH = 0, 1, 2, 3, 4, 5, 6
 
 _STATUS_NAMES = {1: "BGK_E_INVAL", 2: "BGK_E_NOMEM", 3: "BGK_E_CUDA", 4: "BGK_E_SINGULAR",
-                 5: "BGK_E_NBR_OVERFLOW", 6: "BGK_E_NONFINITE", 7: "BGK_E_TIMEOUT", 8: "BGK_E_STATE"}
+                 5: "BGK_E_NBR_OVERFLOW", 6: "BGK_E_NONFINITE", 7: "BGK_E_TIMEOUT", 8: "BGK_E_STATE",
+                 9: "BGK_E_BOUNDS"}
 
 
 class BGKError(RuntimeError):

@@ -13,6 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbgk.so")
+LIB_DEBUG = os.path.join(HERE, "libbgk_debug.so")
 SOURCES = ["abi.cu", "nbr_stencil.cu", "step.cu", "chain.cu", "adjoint.cu", "manage.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
@@ -43,7 +44,17 @@ def _stamp(paths: list[str], extra: list[str] | None) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
+    """Build libbgk.so, or with debug=True the bounds-checked libbgk_debug.so (every list
+    index a kernel loads checked against the point range; BGK_E_BOUNDS on a bad one) in a
+    build folder of its own.  Returns the library's path."""
+    if debug:
+        return _build_into(os.path.join(HERE, "_build_debug"), LIB_DEBUG, force, verbose,
+                           (extra or []) + ["-DBGK_DEBUG_BOUNDS=1"])
+    return _build_into(BUILD, LIB, force, verbose, extra)
+
+
+def _build_into(BUILD: str, LIB: str, force: bool, verbose: bool, extra: list[str] | None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(ROOT, "include", "bgk.h"))

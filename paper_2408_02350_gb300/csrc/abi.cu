@@ -20,6 +20,20 @@
 
 #include "bgk.h"
 
+// NVTX ranges (header-only NVTX 3; inert unless a profiler attaches): one per public
+// call that launches work and one per launch group inside bgk_step, named by the group.
+#ifndef BGK_NVTX
+#define BGK_NVTX 1
+#endif
+#if BGK_NVTX
+#include <nvtx3/nvToolsExt.h>
+#define BGK_RANGE_PUSH(name) nvtxRangePushA(name)
+#define BGK_RANGE_POP() nvtxRangePop()
+#else
+#define BGK_RANGE_PUSH(name) ((void)0)
+#define BGK_RANGE_POP() ((void)0)
+#endif
+
 // Parts (and streams) of one staged upload (bgk_stage_f).
 #ifndef BGK_UPLOAD_PARTS
 #define BGK_UPLOAD_PARTS 4
@@ -250,8 +264,19 @@ int settle_bound(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
   return BGK_OK;
 }
 
+// NVTX range names of the launch groups (KernelId order)
+const char* const kGroupName[K_COUNT] = {"transport", "walls", "neighbours", "stencils", "motion", "adjoint",
+                                         "batched step"};
+
+// RAII NVTX range for a public call
+struct CallRange {
+  explicit CallRange(const char* name) { BGK_RANGE_PUSH(name); }
+  ~CallRange() { BGK_RANGE_POP(); }
+};
+
 int timed_begin(bgk_ctx* ctx, int kid, cudaStream_t s, EvPair** out) {
   *out = nullptr;
+  BGK_RANGE_PUSH(kGroupName[kid]);
   if (!((ctx->timing_mask >> kid) & 1)) return BGK_OK;
   if (ctx->ev_used == ctx->ev.size()) {
     EvPair e;
@@ -268,6 +293,7 @@ int timed_begin(bgk_ctx* ctx, int kid, cudaStream_t s, EvPair** out) {
 }
 
 int timed_end(bgk_ctx* ctx, EvPair* e, cudaStream_t s) {
+  BGK_RANGE_POP();
   if (e) CK(ctx, cudaEventRecord(e->b, s));
   return BGK_OK;
 }
@@ -708,6 +734,7 @@ int bgk_set_maxwellian(bgk_ctx* ctx, double rho0, const double* u0, double T0, v
 }
 
 int bgk_set_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype, int32_t on_device, void* stream) {
+  CallRange range_("bgk_set_f");
   if (!ctx || !f || ci < 0 || ci >= (int)ctx->cases.size() || dtype < 0 || dtype > 2)
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_set_f: bad argument") : BGK_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -764,6 +791,7 @@ int bgk_get_f(bgk_ctx* ctx, int32_t ci, void* f, int32_t dtype, int32_t on_devic
 }
 
 int bgk_neighbours(bgk_ctx* ctx, void* stream) {
+  CallRange range_("bgk_neighbours");
   if (!ctx) return BGK_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   invalidate_batch(ctx);
@@ -876,6 +904,7 @@ static int take_staged(bgk_ctx* ctx, CaseHost& c, cudaStream_t s) {
 }
 
 int bgk_step(bgk_ctx* ctx, int32_t nsteps, void* stream) {
+  CallRange range_("bgk_step");
   if (!ctx || nsteps < 0) return ctx ? fail(ctx, BGK_E_INVAL, "bgk_step: nsteps < 0") : BGK_E_INVAL;
   for (const CaseHost& c : ctx->cases)
     if (c.slab) return fail(ctx, BGK_E_STATE, "bgk_step: a case holds a velocity slab (step it with bgk_shard_*)");
@@ -969,6 +998,7 @@ int bgk_shard_sizes(bgk_ctx* ctx, int32_t ci, int64_t* n_xm, int64_t* n_xw) {
 }
 
 int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
+  CallRange range_("bgk_shard_transport");
   CaseHost* cp;
   int st;
   if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_transport", &cp))) return st;
@@ -998,6 +1028,7 @@ int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
 }
 
 int bgk_shard_relax(bgk_ctx* ctx, int32_t ci, const double* xm, double* xw, void* stream) {
+  CallRange range_("bgk_shard_relax");
   CaseHost* cp;
   int st;
   if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_relax", &cp))) return st;
@@ -1025,6 +1056,7 @@ int bgk_shard_relax(bgk_ctx* ctx, int32_t ci, const double* xm, double* xw, void
 }
 
 int bgk_shard_walls(bgk_ctx* ctx, int32_t ci, const double* xw, void* stream) {
+  CallRange range_("bgk_shard_walls");
   CaseHost* cp;
   int st;
   if ((st = shard_case(ctx, ci, xw, true, "bgk_shard_walls", &cp))) return st;
@@ -1078,6 +1110,7 @@ int bgk_shard_allreduce(double* const* bufs, int32_t nbufs, int64_t count, void*
 }
 
 int bgk_stage_f(bgk_ctx* ctx, int32_t ci, const void* f, int32_t dtype) {
+  CallRange range_("bgk_stage_f");
   if (!ctx || !f || ci < 0 || ci >= (int)ctx->cases.size())
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_stage_f: bad argument") : BGK_E_INVAL;
   CaseHost& c = ctx->cases[ci];
@@ -1217,11 +1250,14 @@ int bgk_sync(bgk_ctx* ctx, void* stream) {
         c.next_ready = false;
       }
     }
-    // the first condition in this order is the return code; the text names every one
+    // the first condition in this order (bounds, overflow, singular, non-finite, timeout)
+    // is the return code; the text names every one
     char all[96];
-    snprintf(all, sizeof(all), " (device flags:%s%s%s%s)", hs.flags & ST_OVERFLOW ? " overflow" : "",
-             hs.flags & ST_SINGULAR ? " singular" : "", hs.flags & ST_NONFINITE ? " nonfinite" : "",
-             hs.flags & ST_TIMEOUT ? " timeout" : "");
+    snprintf(all, sizeof(all), " (device flags:%s%s%s%s%s)", hs.flags & ST_BOUNDS ? " bounds" : "",
+             hs.flags & ST_OVERFLOW ? " overflow" : "", hs.flags & ST_SINGULAR ? " singular" : "",
+             hs.flags & ST_NONFINITE ? " nonfinite" : "", hs.flags & ST_TIMEOUT ? " timeout" : "");
+    if (hs.flags & ST_BOUNDS)
+      return fail(ctx, BGK_E_BOUNDS, "an index outside the point range was found and skipped%s", all);
     if (hs.flags & ST_OVERFLOW) return fail(ctx, BGK_E_NBR_OVERFLOW, "a point has more than max_nbrs neighbours%s", all);
     if (hs.flags & ST_SINGULAR)
       return fail(ctx, BGK_E_SINGULAR, "singular WLS system (too few or degenerate neighbours)%s", all);
@@ -1363,6 +1399,7 @@ int bgk_set_params(bgk_ctx* ctx, int32_t ci, const bgk_params* p) {
 }
 
 int bgk_manage(bgk_ctx* ctx, int32_t ci, double rmin, int32_t min_nbrs, int64_t* counts, void* stream) {
+  CallRange range_("bgk_manage");
   if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !counts || !(rmin >= 0) || min_nbrs < 0)
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_manage: bad argument") : BGK_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1449,6 +1486,7 @@ int bgk_objective(bgk_ctx* ctx, int32_t ci, double* J, void* lam, double scale, 
 }
 
 int bgk_adjoint_step(bgk_ctx* ctx, int32_t ci, const void* lam_in, void* lam_out, double* dtheta, void* stream) {
+  CallRange range_("bgk_adjoint_step");
   if (!ctx || ci < 0 || ci >= (int)ctx->cases.size() || !lam_in || !lam_out || !dtheta || lam_in == lam_out)
     return ctx ? fail(ctx, BGK_E_INVAL, "bgk_adjoint_step: bad argument") : BGK_E_INVAL;
   CaseHost& c = ctx->cases[ci];

@@ -10,7 +10,7 @@
 namespace bgk {
 
 // Device status bits (reported by bgk_sync).
-enum : int32_t { ST_OVERFLOW = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
+enum : int32_t { ST_OVERFLOW = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8, ST_BOUNDS = 16 };
 
 // Verlet-list state of an ALE case: the largest squared displacement of an interior
 // point since the candidate build (FP32 bits, rounded up), the rebuild decision for

@@ -171,4 +171,33 @@ __device__ __forceinline__ void block_sum(T (&v)[NVAL], double (&out)[NVAL], dou
 
 __device__ __forceinline__ void set_status(DevStatus* st, int32_t bit) { atomicOr(&st->flags, bit); }
 
+// Bounds-checked debug build (BGK_DEBUG_BOUNDS=1): an index j loaded from a list must lie
+// in [0, n); a bad one is recorded (ST_BOUNDS) and replaced by `fallback`, an index that
+// makes the access harmless (the point's own row, whose upwind term cancels).  The
+// regular build returns j unchecked.
+#ifndef BGK_DEBUG_BOUNDS
+#define BGK_DEBUG_BOUNDS 0
+#endif
+__device__ __forceinline__ int checked_index(int j, int n, int fallback, DevStatus* st) {
+#if BGK_DEBUG_BOUNDS
+  if ((unsigned)j >= (unsigned)n) {
+    set_status(st, ST_BOUNDS);
+    return fallback;
+  }
+#endif
+  (void)n; (void)fallback; (void)st;
+  return j;
+}
+// The same for a list length m, which must lie in [0, cap] (a bad one becomes 0).
+__device__ __forceinline__ int checked_count(int m, int cap, DevStatus* st) {
+#if BGK_DEBUG_BOUNDS
+  if (m < 0 || m > cap) {
+    set_status(st, ST_BOUNDS);
+    return 0;
+  }
+#endif
+  (void)cap; (void)st;
+  return m;
+}
+
 }  // namespace bgk

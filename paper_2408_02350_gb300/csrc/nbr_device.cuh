@@ -139,7 +139,7 @@ __device__ __forceinline__ void nbr_warp_point(const CaseView& cv, const int i, 
           bool inside = false;
           int j = -1;
           if (q < q1) {
-            j = cv.cell_pts[q];
+            j = checked_index(cv.cell_pts[q], cv.n, i, cv.status);
             if (j != i) {
               float d2f = 0.0f;
 #pragma unroll
@@ -209,7 +209,7 @@ __device__ __forceinline__ void filter_warp_point(const CaseView& cv, const int 
     bool inside = false;
     int j = -1;
     if (q < nc) {
-      j = cand[q];
+      j = checked_index(cand[q], cv.n, i, cv.status);
       float d2f = 0.0f;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
@@ -267,7 +267,7 @@ __device__ __forceinline__ void filter_group_point(const CaseView& cv, const int
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int q = qb + 4 * u + sub;
-      jj[u] = q < nc ? cand[q] : -1;
+      jj[u] = q < nc ? checked_index(cand[q], cv.n, -1, cv.status) : -1;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {

@@ -177,14 +177,14 @@ __global__ void __launch_bounds__(256) k_transport(const CaseView cv) {
   C* s_P = reinterpret_cast<C*>(smem + RED_BYTES + NODE_BYTES + align16(sizeof(int32_t) * cv.cap));
 
   const int i = cv.int_idx[blockIdx.x];
-  const int m = cv.cnt[i];
+  const int m = checked_count(cv.cnt[i], cv.cap, cv.status);
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const int nchunk = NVp >> 2;
   const int vk0 = SH ? cv.vk0 : 0;
   {
     const int32_t* col = cv.col + (int64_t)i * cv.cap;
     const C* P = reinterpret_cast<const C*>(cv.P) + (int64_t)i * cv.cap * DD;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) s_col[t] = col[t];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) s_col[t] = checked_index(col[t], cv.n, i, cv.status);
     for (int t = threadIdx.x; t < m * DD; t += blockDim.x) s_P[t] = P[t];
     for (int t = threadIdx.x; t < nv; t += blockDim.x) s_v[t] = (C)cv.vnodes[t];
   }
@@ -783,13 +783,13 @@ __device__ __forceinline__ void walls_point(const CaseView& cv, const int w, uns
   const int vk0 = PH ? cv.vk0 : 0;
   if (PH != 2 && threadIdx.x < 32) {
     // warp 0 stages the interior neighbours in list order (ballot compaction)
-    const int lane = threadIdx.x, m = cv.cnt[b];
+    const int lane = threadIdx.x, m = checked_count(cv.cnt[b], cv.cap, cv.status);
     const int32_t* col = cv.col + (int64_t)b * cv.cap;
     const C* R = reinterpret_cast<const C*>(cv.recon) + (int64_t)b * cv.cap;
     int mi = 0;
     for (int s0 = 0; s0 < m; s0 += 32) {
       const int s = s0 + lane;
-      const int j = s < m ? col[s] : 0;
+      const int j = s < m ? checked_index(col[s], cv.n, b, cv.status) : 0;
       const bool in = s < m && cv.kind[j] == 0;
       const unsigned bal = __ballot_sync(0xffffffffu, in);
       if (in) {
@@ -948,13 +948,13 @@ __device__ __forceinline__ void walls_point_v4(const CaseView& cv, const int w, 
   const int b = cv.wall_idx[w];
   const int nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x, m = cv.cnt[b];
+    const int lane = threadIdx.x, m = checked_count(cv.cnt[b], cv.cap, cv.status);
     const int32_t* col = cv.col + (int64_t)b * cv.cap;
     const float* R = reinterpret_cast<const float*>(cv.recon) + (int64_t)b * cv.cap;
     int mi = 0;
     for (int s0 = 0; s0 < m; s0 += 32) {
       const int s = s0 + lane;
-      const int j = s < m ? col[s] : 0;
+      const int j = s < m ? checked_index(col[s], cv.n, b, cv.status) : 0;
       const bool in = s < m && cv.kind[j] == 0;
       const unsigned bal = __ballot_sync(0xffffffffu, in);
       if (in) {

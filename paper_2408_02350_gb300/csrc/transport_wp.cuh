@@ -306,12 +306,12 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const int vk0 = SH ? cv.vk0 : 0;
   const float inv_nv = 1.0f / (float)nv;
-  const int m = cv.cnt[i];
+  const int m = checked_count(cv.cnt[i], cap, cv.status);
   for (int q = lane; q < nv; q += 32) s_v[q] = cv.vnodes_f[q];
   {
     const int32_t* col = cv.col + (int64_t)i * cap;
     const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
-    for (int q = lane; q < m; q += 32) s_col[q] = col[q];
+    for (int q = lane; q < m; q += 32) s_col[q] = checked_index(col[q], cv.n, i, cv.status);
     for (int q = lane; q < m * DD; q += 32) s_P[q] = P[q];
   }
   __syncwarp();
@@ -471,12 +471,12 @@ __device__ __forceinline__ void transport_point_mirror(const CaseView& cv, const
   const int lane = threadIdx.x & 31;
   const int cap = cv.cap, nv = cv.nv, NV = cv.NV, NVp = cv.NVp;
   const float inv_nv = 1.0f / (float)nv;
-  const int m = cv.cnt[i];
+  const int m = checked_count(cv.cnt[i], cap, cv.status);
   for (int q = lane; q < nv; q += 32) s_v[q] = cv.vnodes_f[q];
   {
     const int32_t* col = cv.col + (int64_t)i * cap;
     const float* P = reinterpret_cast<const float*>(cv.P) + (int64_t)i * cap * DD;
-    for (int q = lane; q < m; q += 32) s_col[q] = col[q];
+    for (int q = lane; q < m; q += 32) s_col[q] = checked_index(col[q], cv.n, i, cv.status);
     for (int q = lane; q < m * DD; q += 32) s_P[q] = P[q];
   }
   __syncwarp();

@@ -36,7 +36,26 @@ def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in _declared() if not hasattr(h, n)]
     assert not missing, missing
     assert set(_declared()) <= set(lib.exported_symbols()) | {"bgk_version"}
-    assert lib.bgk_version() == 8
+    assert lib.bgk_version() == 9
+
+
+def test_error_codes_match_header(lib):
+    src = open(os.path.join(ROOT, "include", "bgk.h")).read()
+    codes = {name: int(v) for name, v in re.findall(r"\b(BGK_(?:OK|E_[A-Z_]+))\s*=\s*(\d+)", src)}
+    assert codes["BGK_E_BOUNDS"] == 9
+    for name, v in codes.items():
+        assert getattr(lib, name) == v, name
+
+
+def test_bounds_checked_debug_build_exports_every_symbol():
+    # the debug build (every list index a kernel loads checked against the point range)
+    # compiles for sm_103a and exports the same ABI
+    from paper_2408_02350_gb300 import _build
+    path = _build.build(debug=True)
+    h = C.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(h, n)]
+    assert not missing, missing
+    assert h.bgk_version() == 9
 
 
 @pytest.mark.parametrize("struct", ["bgk_params", "bgk_stats"])
