@@ -16,11 +16,13 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# BGK_LIBRARY=debug selects the bounds-checked debug build (libbgk_debug.so, built by
-# _build.build(debug=True)): every neighbour and point index a kernel loads is checked
-# against the point range, a bad one is recorded (BGK_E_BOUNDS at the next bgk_sync) and
-# its access skipped.
-LIB_PATH = os.path.join(_HERE, "libbgk_debug.so" if os.environ.get("BGK_LIBRARY") == "debug" else "libbgk.so")
+# BGK_LIBRARY selects a build variant (_build.build(variant=...)): "debug", the bounds-
+# checked build (libbgk_debug.so: every neighbour and point index a kernel loads is
+# checked against the point range, a bad one is recorded, BGK_E_BOUNDS at the next
+# bgk_sync, and its access skipped), or "staged" (libbgk_staged.so: the 2D FP32 transport
+# stages its neighbour rows in shared memory by bulk copies; same results, slower).
+_VARIANT = os.environ.get("BGK_LIBRARY")
+LIB_PATH = os.path.join(_HERE, "libbgk_%s.so" % _VARIANT if _VARIANT in ("debug", "staged") else "libbgk.so")
 
 BGK_OK, BGK_E_INVAL, BGK_E_NOMEM, BGK_E_CUDA, BGK_E_SINGULAR = 0, 1, 2, 3, 4
 BGK_E_NBR_OVERFLOW, BGK_E_NONFINITE, BGK_E_TIMEOUT, BGK_E_STATE, BGK_E_BOUNDS = 5, 6, 7, 8, 9

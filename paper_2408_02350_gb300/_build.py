@@ -44,13 +44,29 @@ def _stamp(paths: list[str], extra: list[str] | None) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
-    """Build libbgk.so, or with debug=True the bounds-checked libbgk_debug.so (every list
-    index a kernel loads checked against the point range; BGK_E_BOUNDS on a bad one) in a
-    build folder of its own.  Returns the library's path."""
+# Build variants, each a library of its own (libbgk_<name>.so, built in _build_<name>/):
+#   debug   every list index a kernel loads checked against the point range (BGK_E_BOUNDS
+#           on a bad one, the access skipped);
+#   staged  the 2D FP32 transport takes its neighbour rows through per-warp rings of bulk
+#           copies into shared memory (transport_stage.cuh) instead of through L1; the same
+#           results bit for bit, kept as the measured alternative to the default kernel.
+VARIANTS = {"debug": ["-DBGK_DEBUG_BOUNDS=1"],
+            "staged": ["-DBGK_WP_STAGE=1", "-DBGK_STAGE_G=4", "-DBGK_STAGE_D=2"]}
+
+
+def lib_path(variant: str | None = None) -> str:
+    return LIB if not variant else os.path.join(HERE, "libbgk_%s.so" % variant)
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False,
+          variant: str | None = None) -> str:
+    """Build libbgk.so, or the library of one of VARIANTS (debug=True: the bounds-checked
+    "debug" one) in a build folder of its own.  Returns the library's path."""
     if debug:
-        return _build_into(os.path.join(HERE, "_build_debug"), LIB_DEBUG, force, verbose,
-                           (extra or []) + ["-DBGK_DEBUG_BOUNDS=1"])
+        variant = "debug"
+    if variant:
+        return _build_into(os.path.join(HERE, "_build_" + variant), lib_path(variant), force, verbose,
+                           (extra or []) + VARIANTS[variant])
     return _build_into(BUILD, LIB, force, verbose, extra)
 
 

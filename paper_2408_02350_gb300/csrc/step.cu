@@ -19,11 +19,13 @@
 //   rho_w M_w(v) with rho_w from zero net mass flux.
 // k_move: x += dt U^{n+1} at interior points (FP64, no fused multiply-add).
 #include <algorithm>
+#include <type_traits>
 
 #include "bgk_internal.cuh"
 #include "device_common.cuh"
 #include "motion.cuh"
 #include "transport_wp.cuh"
+#include "transport_stage.cuh"
 
 namespace bgk {
 
@@ -497,6 +499,32 @@ __global__ void __launch_bounds__(32 * BGK_WP_WARPS, VPL == 4 ? 32 / BGK_WP_WARP
   transport_point_wp<S, DIM, ALE, ROW, VPL, VPL == 4, SH, AVG>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
 }
 
+// Staged variant (2D, FP32, nv % 4 == 0): the neighbour rows come through per-warp rings
+// of bulk copies instead of L1 (transport_stage.cuh).
+#ifndef BGK_WP_STAGE
+#define BGK_WP_STAGE 0
+#endif
+#ifndef BGK_STAGE_MINB
+#define BGK_STAGE_MINB (32 / BGK_WP_WARPS)
+#endif
+template <bool ALE>
+__global__ void __launch_bounds__(32 * BGK_WP_WARPS, BGK_STAGE_MINB) k_transport_stage(const CaseView cv) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const int cap = cv.cap;
+  float* s_v = reinterpret_cast<float*>(smem) + warp * 64;
+  int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * cap;
+  float* s_P0 = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W));
+  float* s_P = s_P0 + (size_t)warp * cap * 4;
+  float* s_k = s_P0 + (size_t)W * cap * 4 + warp * kahan_floats<2>();
+  unsigned char* ring0 = smem + stage_ring_offset(wp_smem_bytes<2>(W, cap));
+  float* s_ring = reinterpret_cast<float*>(ring0 + (size_t)warp * kStageD * kStageG * kStageRowBytes);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(ring0 + (size_t)W * kStageD * kStageG * kStageRowBytes) + warp * kStageD;
+  const int t = blockIdx.x * W + warp;
+  if (t >= cv.n_int) return;
+  transport_point_stage<ALE>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k, s_ring, s_bar);
+}
+
 // Second-order step, FP32/BF16 storage: one warp per interior point relaxes its output
 // row exactly over dt/2 in place, with the moments of that row (compensated lane sums).
 template <typename S, int DIM, bool ROW>
@@ -650,6 +678,16 @@ static void launch_transport_wp(const CaseView& cv, cudaStream_t s) {
     }
   }
   const bool v8 = transport_vpl == 8 ? (cv.NVp % 8 == 0) : (transport_vpl == 4 ? false : (DIM == 3 && row8));
+  if constexpr (BGK_WP_STAGE && DIM == 2 && std::is_same<S, float>::value) {
+    // (bulk copies need 16-byte aligned rows: caller-bound storage may start anywhere)
+    if (row4 && !v8 && cv.NVp % 4 == 0 && (reinterpret_cast<uintptr_t>(cv.f_in) & 15) == 0) {
+      const size_t ssm = stage_smem_bytes(smem, W);
+      auto k = cv.ale ? k_transport_stage<true> : k_transport_stage<false>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+      k<<<grid, threads, ssm, s>>>(cv);
+      return;
+    }
+  }
 #define BGK_LAUNCH_WP(ALE, ROW, VPL)                                                      \
   {                                                                                       \
     auto k = k_transport_wp<S, DIM, ALE, ROW, VPL>;                                       \

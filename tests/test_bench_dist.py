@@ -35,7 +35,7 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_take_independent_cavities_and_the_max_time():
     world, port = 2, _free_port()
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     assert out[0][1] == out[1][1] == 11.0          # max over ranks
     assert out[0][0] != out[1][0]                  # Kn sweep by rank (weak scaling)
@@ -66,7 +66,7 @@ def test_velocity_sharded_plan_splits_the_grid_and_sums_over_ranks(world):
     # ranks tile the 32^2 velocity grid without overlap, every rank exchanges the same
     # (dim + 2) n + (2 dim + 6) n_wall doubles, and the allreduce sums over the ranks
     port = _free_port()
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_plan_worker, args=(world, port, out), nprocs=world, join=True)
     spans = sorted((out[r][0], out[r][1]) for r in range(world))
     assert spans[0][0] == 0 and spans[-1][1] == 32 * 32

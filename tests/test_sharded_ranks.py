@@ -187,7 +187,7 @@ def test_three_gloo_ranks_with_uneven_slabs():
     assert velocity_slabs(49, 3) == [(0, 16), (16, 32), (32, 49)]
     name, over, steps, world = "cavity2d_ale_n201_v32_f32", dict(n=9, nv=7, vmax=3.0, storage="f64"), 3, 3
     port = _free_port()
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(world, port, name, over, steps, out), nprocs=world, join=True)
     p = bi.config(name, **over)
     sim = oracle.Simulation(p, bi.cloud_for(p))
@@ -209,7 +209,7 @@ def test_two_gloo_ranks_reproduce_the_unsharded_oracle(name, over, steps):
     import bgk_inputs as bi
     import oracle
     world, port = 2, _free_port()
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(world, port, name, over, steps, out), nprocs=world, join=True)
     p = bi.config(name, **over)
     sim = oracle.Simulation(p, bi.cloud_for(p))
