@@ -97,10 +97,20 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the first sample comes some 100 ms after the start: wait for it (3 s at most), so
+        # that the samples that follow fall inside the timed region
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+        with open(self.path) as fh:
+            self.before = sum(1 for line in fh if line.endswith("\n"))
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -113,7 +123,12 @@ class ClockSampler:
         self.fh.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        # the samples taken inside the timed region; when it was shorter than the sampling
+        # interval, the ones just before it (the warm-up steps) stand in
+        inside = lines[getattr(self, "before", 0):]
+        for line in (inside if any(x.strip() for x in inside) else lines):
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
