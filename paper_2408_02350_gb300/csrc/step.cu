@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(32 * BGK_WP_WARPS, VPL == 4 ? 32 / BGK_WP_WARP
 #endif
 template <bool ALE>
 __global__ void __launch_bounds__(32 * BGK_WP_WARPS, BGK_STAGE_MINB) k_transport_stage(const CaseView cv) {
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const int cap = cv.cap;
   float* s_v = reinterpret_cast<float*>(smem) + warp * 64;
