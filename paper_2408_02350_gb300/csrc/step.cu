@@ -622,9 +622,14 @@ __global__ void __launch_bounds__(256, BGK_MIRROR_MIN_BLOCKS) k_transport_mirror
 
 // Many cases in one persistent launch: items[k] = (case, interior slot), tiles of W
 // consecutive items per CTA, tiles taken in grid-stride order.  Every warp reads
-// its case's descriptor; the ROW4 / ALE variants are chosen per warp.
-// 3 CTAs per SM (80 registers, some spills) beats 2 (114 registers, no spills) on the
-// 64-cavity sweep: 4.54 against 4.99 ms per step.
+// its case's descriptor; the ROW4 variant is chosen per warp.
+// 3 CTAs per SM (80 registers, 8 bytes spilled) beats 2 (114 registers, no spills) on
+// the 64-cavity sweep: 4.54 against 4.99 ms per step (when measured); the compensated
+// sums in shared memory (KS, as the single-case kernel) lose here: 4.46 ms at 3 CTAs per
+// SM and 4.57 ms at 4 against 4.04 ms.
+#ifndef BGK_BATCH_KS
+#define BGK_BATCH_KS false
+#endif
 #ifndef BGK_BATCH_MIN_BLOCKS
 #define BGK_BATCH_MIN_BLOCKS 3
 #endif
@@ -645,14 +650,9 @@ __global__ void __launch_bounds__(256, BGK_BATCH_MIN_BLOCKS) k_transport_batch(c
     const int2 e = items[it];
     const CaseView& cv = cases[e.x];
     const int i = cv.int_idx[e.y];
-    const bool row4 = cv.nv % 4 == 0;
-    if (cv.ale) {
-      if (row4) transport_point_wp<S, DIM, true, true, 4, false>(cv, i, s_v, s_col, s_P, s_k);
-      else transport_point_wp<S, DIM, true, false, 4, false>(cv, i, s_v, s_col, s_P, s_k);
-    } else {
-      if (row4) transport_point_wp<S, DIM, false, true, 4, false>(cv, i, s_v, s_col, s_P, s_k);
-      else transport_point_wp<S, DIM, false, false, 4, false>(cv, i, s_v, s_col, s_P, s_k);
-    }
+    // (batched stepping takes fixed points only: c = v)
+    if (cv.nv % 4 == 0) transport_point_wp<S, DIM, false, true, 4, BGK_BATCH_KS>(cv, i, s_v, s_col, s_P, s_k);
+    else transport_point_wp<S, DIM, false, false, 4, BGK_BATCH_KS>(cv, i, s_v, s_col, s_P, s_k);
     __syncwarp();
   }
 }
