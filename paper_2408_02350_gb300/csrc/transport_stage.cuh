@@ -199,7 +199,7 @@ __device__ __forceinline__ void transport_point_stage(const CaseView& cv, const 
       chunk_velocities<DIM, VPL, true>(k0, nv, NV, inv_nv, s_v, vel, kin);
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
-      slice_out<float, DIM, NC, VPL>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
+      slice_out<float, DIM, NC, VPL, false, true>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
     }

@@ -63,6 +63,12 @@ __device__ __forceinline__ void chunk_velocities(int k0, int nv, int NV, float i
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+// 2^x by the hardware's approximate base-2 exponential (relative error about 2^-22).
+__device__ __forceinline__ float exp2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float2 min0(float2 p) { return make_float2(fminf(p.x, 0.0f), fminf(p.y, 0.0f)); }
 
 template <typename S, int VPL>
@@ -122,12 +128,39 @@ __device__ __forceinline__ void row_upwind(const float2 (&cx)[NP], const float (
   }
 }
 
+// a - b in packed FP32x2 with one rounding per half (b times -1 is exact), as a scalar
+// subtraction rounds.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f, -1.0f), a); }
+
+// Compensated (Kahan) addition of the slice sums ps to the running sums, two at a time
+// in packed FP32x2 (each half rounds as the scalar form would).
+template <int N>
+__device__ __forceinline__ void kahan_add(const float (&ps)[N], float (&msum)[N], float (&mcmp)[N]) {
+#pragma unroll
+  for (int q = 0; q + 1 < N; q += 2) {
+    const float2 y = sub2(f2(ps[q], ps[q + 1]), f2(mcmp[q], mcmp[q + 1]));
+    const float2 m = f2(msum[q], msum[q + 1]);
+    const float2 t = __fadd2_rn(m, y);
+    const float2 c = sub2(sub2(t, m), y);
+    msum[q] = t.x; msum[q + 1] = t.y;
+    mcmp[q] = c.x; mcmp[q + 1] = c.y;
+  }
+  if (N % 2) {
+    const float y = ps[N - 1] - mcmp[N - 1];
+    const float t = msum[N - 1] + y;
+    mcmp[N - 1] = (t - msum[N - 1]) - y;
+    msum[N - 1] = t;
+  }
+}
+
 // End of a velocity slice: f~ = f_i - 2 dt (acc - sk f_i) for the lane's VPL
 // velocities, written to the output row (and to the adjoint's tape when one is
 // attached); the slice's moment sums are Kahan-added to the lane's running sums.
 // AVG (second stage of the two-stage transport): f~ = (f_avg,i + f~) / 2, f_avg the
 // state at the start of the step, whose row i is read before the output overwrites it.
-template <typename S, int DIM, int NC, int VPL, bool AVG = false>
+// ROW: the lane's velocities share every component but the first (then the sums of
+// v_a g for a >= 1 are v_a sum g), and f~ is formed in packed FP32x2 pairs.
+template <typename S, int DIM, int NC, int VPL, bool AVG = false, bool ROW = false>
 __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const int k0, const float (&vel)[VPL][DIM],
                                           const bool (&kin)[VPL], const float (&acc)[NC][VPL],
                                           const float (&sk)[VPL], const float two_dt, float (&msum)[DIM + 2],
@@ -145,31 +178,67 @@ __device__ __forceinline__ void slice_out(const CaseView& cv, const int i, const
     for (int c = 0; c < NC; ++c) ldv<S, VPL>(fa + (int64_t)c * NVp + k0, fav[c]);
   }
   float ps[DIM + 2];
+  if constexpr (ROW && VPL % 2 == 0) {
+    constexpr int NP = VPL / 2;
+    const float2 ntd = f2(-two_dt, -two_dt);
 #pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+    for (int q = 0; q < NP; ++q) {
+      const float2 nsk = __fmul2_rn(f2(sk[2 * q], sk[2 * q + 1]), f2(-1.0f, -1.0f));
 #pragma unroll
-  for (int e = 0; e < VPL; ++e) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? fiv[c][e] - two_dt * (acc[c][e] - sk[e] * fiv[c][e]) : 0.0f;
-    if (AVG) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) ft[c][e] = 0.5f * (ft[c][e] + fav[c][e]);
+      for (int c = 0; c < NC; ++c) {
+        const float2 fq = f2(fiv[c][2 * q], fiv[c][2 * q + 1]);
+        const float2 t = __ffma2_rn(nsk, fq, f2(acc[c][2 * q], acc[c][2 * q + 1]));  // acc - sk f_i
+        float2 r = __ffma2_rn(ntd, t, fq);                                              // f_i - 2 dt (.)
+        if (AVG) r = __fmul2_rn(f2(0.5f, 0.5f), __fadd2_rn(r, f2(fav[c][2 * q], fav[c][2 * q + 1])));
+        ft[c][2 * q] = r.x; ft[c][2 * q + 1] = r.y;
+      }
     }
-    const float g = ft[0][e];
-    float v2 = 0.0f;
-    ps[0] += g;
+    if (!kin[VPL - 1]) {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
-    ps[DIM + 1] = fmaf(v2, g, ps[DIM + 1]);
-    if (NC == 2) ps[DIM + 1] += ft[NC - 1][e];
-  }
+      for (int e = 0; e < VPL; ++e)
 #pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) {
-    const float y = ps[q] - mcmp[q];
-    const float tt = msum[q] + y;
-    mcmp[q] = (tt - msum[q]) - y;
-    msum[q] = tt;
+        for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? ft[c][e] : 0.0f;
+    }
+    // sum g, sum v_x g, sum |v|^2 g (+ sum h) in pairs; |v|^2 = v_x^2 + r2
+    float r2 = 0.0f;
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) r2 = fmaf(vel[0][a], vel[0][a], r2);
+    float2 gs = f2(0.0f, 0.0f), xg = gs, wg = gs, hs = gs;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float2 g = f2(ft[0][2 * q], ft[0][2 * q + 1]);
+      const float2 vx = f2(vel[2 * q][0], vel[2 * q + 1][0]);
+      gs = __fadd2_rn(gs, g);
+      xg = __ffma2_rn(vx, g, xg);
+      wg = __ffma2_rn(__ffma2_rn(vx, vx, f2(r2, r2)), g, wg);
+      if (NC == 2) hs = __fadd2_rn(hs, f2(ft[NC - 1][2 * q], ft[NC - 1][2 * q + 1]));
+    }
+    ps[0] = gs.x + gs.y;
+    ps[1] = xg.x + xg.y;
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) ps[1 + a] = vel[0][a] * ps[0];
+    ps[DIM + 1] = NC == 2 ? (wg.x + wg.y) + (hs.x + hs.y) : wg.x + wg.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) ps[q] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < VPL; ++e) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ft[c][e] = kin[e] ? fiv[c][e] - two_dt * (acc[c][e] - sk[e] * fiv[c][e]) : 0.0f;
+      if (AVG) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ft[c][e] = 0.5f * (ft[c][e] + fav[c][e]);
+      }
+      const float g = ft[0][e];
+      float v2 = 0.0f;
+      ps[0] += g;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) { ps[1 + a] = fmaf(vel[e][a], g, ps[1 + a]); v2 = fmaf(vel[e][a], vel[e][a], v2); }
+      ps[DIM + 1] = fmaf(v2, g, ps[DIM + 1]);
+      if (NC == 2) ps[DIM + 1] += ft[NC - 1][e];
+    }
   }
+  kahan_add<DIM + 2>(ps, msum, mcmp);
 #pragma unroll
   for (int c = 0; c < NC; ++c) stv<S, VPL>(fo + (int64_t)c * NVp + k0, ft[c]);
   if (cv.ft_out) {
@@ -231,6 +300,7 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
     pref = cb * (DIM == 2 ? rho / twopiT : rho / (twopiT * sqrtf(twopiT)));
     nl2 = -0.5f / Tn;
   }
+  const float l2 = nl2 * 1.44269504f;  // log2(e)
   for (int sl = 0; sl < nslice; ++sl) {
     const int chunk = sl * 32 + lane;
     if (chunk >= nchunk) break;
@@ -241,17 +311,47 @@ __device__ __forceinline__ void relax_point(const CaseView& cv, const int i, con
     float ft[NC][VPL], out[NC][VPL];
 #pragma unroll
     for (int c = 0; c < NC; ++c) ldv<S, VPL>(fo + (int64_t)c * NVp + k0, ft[c]);
+    if constexpr (ROW && VPL % 2 == 0) {
+      // in packed pairs: |v - U|^2 = (v_x - U_x)^2 + r2, r2 shared by the lane's velocities;
+      // M from 2^(l2 |v - U|^2), l2 = -log2(e) / (2 T)
+      float r2 = 0.0f;
 #pragma unroll
-    for (int e = 0; e < VPL; ++e) {
-      float c2 = 0.0f;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const float d = vel[e][a] - Un[a];
-        c2 = fmaf(d, d, c2);
+      for (int a = 1; a < DIM; ++a) {
+        const float d = vel[0][a] - Un[a];
+        r2 = fmaf(d, d, r2);
       }
-      const float bM = kin[e] ? pref * __expf(nl2 * c2) : 0.0f;  // dt/(tau+dt) * M(v)
-      out[0][e] = kin[e] ? fmaf(ca, ft[0][e], bM) : 0.0f;
-      if (NC == 2) out[NC - 1][e] = kin[e] ? fmaf(ca, ft[NC - 1][e], Tn * bM) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < VPL / 2; ++q) {
+        const float2 dx = __fadd2_rn(f2(vel[2 * q][0], vel[2 * q + 1][0]), f2(-Un[0], -Un[0]));
+        const float2 ea = __fmul2_rn(__ffma2_rn(dx, dx, f2(r2, r2)), f2(l2, l2));
+        const float2 bM = __fmul2_rn(f2(pref, pref), f2(exp2_approx(ea.x), exp2_approx(ea.y)));
+        const float2 o0 = __ffma2_rn(f2(ca, ca), f2(ft[0][2 * q], ft[0][2 * q + 1]), bM);
+        out[0][2 * q] = o0.x; out[0][2 * q + 1] = o0.y;
+        if (NC == 2) {
+          const float2 o1 = __ffma2_rn(f2(ca, ca), f2(ft[NC - 1][2 * q], ft[NC - 1][2 * q + 1]),
+                                       __fmul2_rn(f2(Tn, Tn), bM));
+          out[NC - 1][2 * q] = o1.x; out[NC - 1][2 * q + 1] = o1.y;
+        }
+      }
+      if (!kin[VPL - 1]) {
+#pragma unroll
+        for (int e = 0; e < VPL; ++e)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) out[c][e] = kin[e] ? out[c][e] : 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VPL; ++e) {
+        float c2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const float d = vel[e][a] - Un[a];
+          c2 = fmaf(d, d, c2);
+        }
+        const float bM = kin[e] ? pref * __expf(nl2 * c2) : 0.0f;  // dt/(tau+dt) * M(v)
+        out[0][e] = kin[e] ? fmaf(ca, ft[0][e], bM) : 0.0f;
+        if (NC == 2) out[NC - 1][e] = kin[e] ? fmaf(ca, ft[NC - 1][e], Tn * bM) : 0.0f;
+      }
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) stv<S, VPL>(fo + (int64_t)c * NVp + k0, out[c]);
@@ -440,7 +540,7 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
     }
-    slice_out<S, DIM, NC, VPL, AVG>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
+    slice_out<S, DIM, NC, VPL, AVG, ROW>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
     if (KS) {
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
@@ -585,8 +685,8 @@ __device__ __forceinline__ void transport_point_mirror(const CaseView& cv, const
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
     }
-    slice_out<S, DIM, NC, VPL>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
-    slice_out<S, DIM, NC, VPL>(cv, i, km, velm, kin, accm, skm, two_dt, rsum, rcmp);
+    slice_out<S, DIM, NC, VPL, false, true>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
+    slice_out<S, DIM, NC, VPL, false, true>(cv, i, km, velm, kin, accm, skm, two_dt, rsum, rcmp);
     if (KS) {
 #pragma unroll
       for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
