@@ -471,7 +471,7 @@ static void launch_shard_relax_d(const CaseView& cv, cudaStream_t s) {
 // stencils, compensated moment sums.
 template <int DIM>
 __host__ __device__ inline size_t wp_smem_bytes(int W, int cap) {
-  return 256 * W + align16(sizeof(int32_t) * cap * W) + sizeof(float) * cap * DIM * DIM * W +
+  return 256 * W + align16(sizeof(int32_t) * cap * W) + align16(sizeof(float) * cap * DIM * DIM * W) +
          sizeof(float) * kahan_floats<DIM>() * W;
 }
 
@@ -493,7 +493,8 @@ __global__ void __launch_bounds__(32 * BGK_WP_WARPS, VPL == 4 ? 32 / BGK_WP_WARP
   int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * cap;
   float* s_P0 = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W));
   float* s_P = s_P0 + (size_t)warp * cap * DD;
-  float* s_k = s_P0 + (size_t)W * cap * DD + warp * kahan_floats<DIM>();
+  float* s_k = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s_P0) + align16(sizeof(float) * W * cap * DD)) +
+               warp * kahan_floats<DIM>();
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
   transport_point_wp<S, DIM, ALE, ROW, VPL, VPL == 4, SH, AVG>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
@@ -516,7 +517,8 @@ __global__ void __launch_bounds__(32 * BGK_WP_WARPS, BGK_STAGE_MINB) k_transport
   int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * cap;
   float* s_P0 = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W));
   float* s_P = s_P0 + (size_t)warp * cap * 4;
-  float* s_k = s_P0 + (size_t)W * cap * 4 + warp * kahan_floats<2>();
+  float* s_k = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s_P0) + align16(sizeof(float) * W * cap * 4)) +
+               warp * kahan_floats<2>();
   unsigned char* ring0 = smem + stage_ring_offset(wp_smem_bytes<2>(W, cap));
   float* s_ring = reinterpret_cast<float*>(ring0 + (size_t)warp * kStageD * kStageG * kStageRowBytes);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(ring0 + (size_t)W * kStageD * kStageG * kStageRowBytes) + warp * kStageD;
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(32 * BGK_WP_WARPS, BGK_STAGE_MINB) k_transport
 template <typename S, int DIM, bool ROW>
 __global__ void __launch_bounds__(256) k_relax_half_wp(const CaseView cv) {
   constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4;
-  __shared__ float s_vall[8 * 64];
+  __shared__ __align__(16) float s_vall[8 * 64];  // chunk_velocities reads groups of 4
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* s_v = s_vall + warp * 64;
   const int t = blockIdx.x * W + warp;
@@ -580,7 +582,7 @@ __global__ void __launch_bounds__(256) k_relax_half_wp(const CaseView cv) {
 // output row with the moments of the summed sums (the relaxation of k_transport_wp).
 template <typename S, int DIM, bool ROW>
 __global__ void __launch_bounds__(256) k_shard_relax_wp(const CaseView cv) {
-  __shared__ float s_vall[8 * 64];
+  __shared__ __align__(16) float s_vall[8 * 64];  // chunk_velocities reads groups of 4
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* s_v = s_vall + warp * 64;
   const int t = blockIdx.x * W + warp;
@@ -614,7 +616,8 @@ __global__ void __launch_bounds__(256, BGK_MIRROR_MIN_BLOCKS) k_transport_mirror
   int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * cap;
   float* s_P0 = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * cap * W));
   float* s_P = s_P0 + (size_t)warp * cap * DD;
-  float* s_k = s_P0 + (size_t)W * cap * DD + warp * kahan_floats<DIM>();
+  float* s_k = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s_P0) + align16(sizeof(float) * W * cap * DD)) +
+               warp * kahan_floats<DIM>();
   const int t = blockIdx.x * W + warp;
   if (t >= cv.n_int) return;
   transport_point_mirror<S, DIM, KS>(cv, cv.int_idx[t], s_v, s_col, s_P, s_k);
@@ -643,7 +646,8 @@ __global__ void __launch_bounds__(256, BGK_BATCH_MIN_BLOCKS) k_transport_batch(c
   int32_t* s_col = reinterpret_cast<int32_t*>(smem + 256 * W) + warp * capmax;
   float* s_P0 = reinterpret_cast<float*>(smem + 256 * W + align16(sizeof(int32_t) * capmax * W));
   float* s_P = s_P0 + (size_t)warp * capmax * DD;
-  float* s_k = s_P0 + (size_t)W * capmax * DD + warp * kahan_floats<DIM>();
+  float* s_k = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s_P0) + align16(sizeof(float) * W * capmax * DD)) +
+               warp * kahan_floats<DIM>();
   for (int tile = blockIdx.x; tile * W < n_items; tile += gridDim.x) {
     const int it = tile * W + warp;
     if (it >= n_items) continue;
@@ -1465,7 +1469,7 @@ constexpr int MOM_GP = 8, MOM_WARPS = 4;  // points per warp, warps per CTA
 template <typename S, int DIM, bool ROW, bool SH = false>
 __global__ void __launch_bounds__(32 * MOM_WARPS) k_moments_wp(CaseView cv, const S* f) {
   constexpr int NC = DIM == 2 ? 2 : 1, VPL = 4, NQ = DIM + 2;
-  __shared__ float s_v[64];
+  __shared__ __align__(16) float s_v[64];  // chunk_velocities reads groups of 4
   __shared__ float2 s_tot[MOM_WARPS][MOM_GP][NQ];
   for (int t = threadIdx.x; t < cv.nv; t += blockDim.x) s_v[t] = cv.vnodes_f[t];
   __syncthreads();

@@ -144,8 +144,7 @@ __device__ __forceinline__ void transport_point_stage(const CaseView& cv, const 
   float rsum[DIM + 2], rcmp[DIM + 2];
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) { rsum[q] = 0.0f; rcmp[q] = 0.0f; }
-#pragma unroll
-  for (int q = 0; q < 2 * (DIM + 2); ++q) s_k[q * 32 + lane] = 0.0f;
+  ks_store<DIM>(s_k, lane, rsum, rcmp);
 
   int c_t = 0;  // consumer: the next group to read
   bool lost = false;
@@ -197,11 +196,9 @@ __device__ __forceinline__ void transport_point_stage(const CaseView& cv, const 
     }
     if (act) {
       chunk_velocities<DIM, VPL, true>(k0, nv, NV, inv_nv, s_v, vel, kin);
-#pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+      ks_load<DIM>(s_k, lane, rsum, rcmp);
       slice_out<float, DIM, NC, VPL, false, true>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
-#pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
+      ks_store<DIM>(s_k, lane, rsum, rcmp);
     }
     __syncwarp();
   }
@@ -212,8 +209,7 @@ __device__ __forceinline__ void transport_point_stage(const CaseView& cv, const 
     for (int t = c_t + 1; t < p_t; ++t) (void)stage_wait(s_bar + t % D, (uint32_t)(t / D) & 1u);
     return;
   }
-#pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+  ks_load<DIM>(s_k, lane, rsum, rcmp);
   finish_point<float, DIM, true, VPL>(cv, i, s_v, rsum, rcmp);
 }
 

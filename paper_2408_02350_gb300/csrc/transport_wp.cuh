@@ -36,8 +36,20 @@ __device__ __forceinline__ void chunk_velocities(int k0, int nv, int NV, float i
   if (ROW) {
     int q = fdiv_small(k0, inv_nv);
     const int kx0 = k0 - q * nv;
+    if constexpr (VPL % 4 == 0) {
+      // kx0 is a multiple of VPL (k0 and nv are), so the first components come in
+      // aligned groups of four
 #pragma unroll
-    for (int e = 0; e < VPL; ++e) { vel[e][0] = s_v[kx0 + e]; kin[e] = k0 + e < NV; }
+      for (int e = 0; e < VPL; e += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(s_v + kx0 + e);
+        vel[e][0] = x.x; vel[e + 1][0] = x.y; vel[e + 2][0] = x.z; vel[e + 3][0] = x.w;
+      }
+#pragma unroll
+      for (int e = 0; e < VPL; ++e) kin[e] = k0 + e < NV;
+    } else {
+#pragma unroll
+      for (int e = 0; e < VPL; ++e) { vel[e][0] = s_v[kx0 + e]; kin[e] = k0 + e < NV; }
+    }
 #pragma unroll
     for (int a = 1; a < DIM; ++a) {
       const int q2 = fdiv_small(q, inv_nv);
@@ -393,8 +405,38 @@ __device__ __forceinline__ void partial_out(const CaseView& cv, const int i, con
 // the velocity slab that starts at cv.vk0, and the slab's moment sums of f~ go to the
 // exchange buffer instead of the relaxation.  AVG (second stage of the second-order
 // step): f~ is averaged with the row of cv.f_avg and relaxed exactly over dt/2.
+// KS layout: the lane's running sums and their compensations as float2 pairs, pair p of
+// the sums at s_k[p * 64 + 2 lane] and of the compensations at s_k[(KP + p) * 64 + 2 lane],
+// KP = (DIM + 3) / 2 (the second half of the last pair unused when DIM + 2 is odd); s_k
+// is 8-byte aligned.
 template <int DIM>
-__host__ __device__ constexpr int kahan_floats() { return 2 * (DIM + 2) * 32; }
+__host__ __device__ constexpr int kahan_pairs() { return (DIM + 3) / 2; }
+template <int DIM>
+__host__ __device__ constexpr int kahan_floats() { return 2 * kahan_pairs<DIM>() * 64; }
+
+template <int DIM>
+__device__ __forceinline__ void ks_store(float* s_k, const int lane, const float (&msum)[DIM + 2],
+                                         const float (&mcmp)[DIM + 2]) {
+  constexpr int KP = kahan_pairs<DIM>();
+#pragma unroll
+  for (int p = 0; p < KP; ++p) {
+    const int q1 = 2 * p + 1 < DIM + 2 ? 2 * p + 1 : 2 * p;
+    *reinterpret_cast<float2*>(s_k + p * 64 + 2 * lane) = f2(msum[2 * p], msum[q1]);
+    *reinterpret_cast<float2*>(s_k + (KP + p) * 64 + 2 * lane) = f2(mcmp[2 * p], mcmp[q1]);
+  }
+}
+template <int DIM>
+__device__ __forceinline__ void ks_load(const float* s_k, const int lane, float (&msum)[DIM + 2],
+                                        float (&mcmp)[DIM + 2]) {
+  constexpr int KP = kahan_pairs<DIM>();
+#pragma unroll
+  for (int p = 0; p < KP; ++p) {
+    const float2 a = *reinterpret_cast<const float2*>(s_k + p * 64 + 2 * lane);
+    const float2 b = *reinterpret_cast<const float2*>(s_k + (KP + p) * 64 + 2 * lane);
+    msum[2 * p] = a.x; mcmp[2 * p] = b.x;
+    if (2 * p + 1 < DIM + 2) { msum[2 * p + 1] = a.y; mcmp[2 * p + 1] = b.y; }
+  }
+}
 
 template <typename S, int DIM, bool ALE, bool ROW, int VPL, bool KS, bool SH = false, bool AVG = false>
 __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int i, float* s_v, int32_t* s_col,
@@ -426,15 +468,12 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
   const S* fbase = reinterpret_cast<const S*>(cv.f_in);
   const float two_dt = cv.two_dt_f;
 
-  // KS: s_k[q * 32 + lane] holds running sum q (q < DIM + 2) and its compensation
-  // (q >= DIM + 2); otherwise rsum / rcmp do
+  // KS: s_k holds the running sums and their compensations between slices (ks_store /
+  // ks_load); otherwise rsum / rcmp do
   float rsum[DIM + 2], rcmp[DIM + 2];
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) { rsum[q] = 0.0f; rcmp[q] = 0.0f; }
-  if (KS) {
-#pragma unroll
-    for (int q = 0; q < 2 * (DIM + 2); ++q) s_k[q * 32 + lane] = 0.0f;
-  }
+  if (KS) ks_store<DIM>(s_k, lane, rsum, rcmp);
 
   for (int sl = 0; sl < nslice; ++sl) {
     const int chunk = sl * 32 + lane;
@@ -537,18 +576,15 @@ __device__ __forceinline__ void transport_point_wp(const CaseView& cv, const int
     if (KS) {
       // the velocities again (not held in registers across the neighbour loop)
       chunk_velocities<DIM, VPL, ROW>(k0 + vk0, nv, NV + vk0, inv_nv, s_v, vel, kin);
-#pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+      ks_load<DIM>(s_k, lane, rsum, rcmp);
     }
     slice_out<S, DIM, NC, VPL, AVG, ROW>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
     if (KS) {
-#pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
+      ks_store<DIM>(s_k, lane, rsum, rcmp);
     }
   }
   if (KS) {
-#pragma unroll
-    for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+    ks_load<DIM>(s_k, lane, rsum, rcmp);
   }
   if constexpr (SH) partial_out<DIM>(cv, i, rsum, rcmp);
   else finish_point<S, DIM, ROW, VPL, AVG ? 1 : 0>(cv, i, s_v, rsum, rcmp);
@@ -591,10 +627,7 @@ __device__ __forceinline__ void transport_point_mirror(const CaseView& cv, const
   float rsum[DIM + 2], rcmp[DIM + 2];
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) { rsum[q] = 0.0f; rcmp[q] = 0.0f; }
-  if (KS) {
-#pragma unroll
-    for (int q = 0; q < 2 * (DIM + 2); ++q) s_k[q * 32 + lane] = 0.0f;
-  }
+  if (KS) ks_store<DIM>(s_k, lane, rsum, rcmp);
 
   for (int sl = 0; sl < nslice; ++sl) {
     const int chunk = sl * 32 + lane;
@@ -682,19 +715,16 @@ __device__ __forceinline__ void transport_point_mirror(const CaseView& cv, const
 #pragma unroll
       for (int a = 0; a < DIM; ++a) velm[e][a] = -vel[VPL - 1 - e][a];
     if (KS) {
-#pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+      ks_load<DIM>(s_k, lane, rsum, rcmp);
     }
     slice_out<S, DIM, NC, VPL, false, true>(cv, i, k0, vel, kin, acc, sk, two_dt, rsum, rcmp);
     slice_out<S, DIM, NC, VPL, false, true>(cv, i, km, velm, kin, accm, skm, two_dt, rsum, rcmp);
     if (KS) {
-#pragma unroll
-      for (int q = 0; q < DIM + 2; ++q) { s_k[q * 32 + lane] = rsum[q]; s_k[(DIM + 2 + q) * 32 + lane] = rcmp[q]; }
+      ks_store<DIM>(s_k, lane, rsum, rcmp);
     }
   }
   if (KS) {
-#pragma unroll
-    for (int q = 0; q < DIM + 2; ++q) { rsum[q] = s_k[q * 32 + lane]; rcmp[q] = s_k[(DIM + 2 + q) * 32 + lane]; }
+    ks_load<DIM>(s_k, lane, rsum, rcmp);
   }
   finish_point<S, DIM, true, VPL>(cv, i, s_v, rsum, rcmp);
 }
