@@ -47,6 +47,24 @@ def test_error_codes_match_header(lib):
         assert getattr(lib, name) == v, name
 
 
+def test_build_variants_are_selected_by_name(tmp_path):
+    # each variant builds into a library of its own, and BGK_LIBRARY picks it at import
+    import subprocess
+    import sys
+    from paper_2408_02350_gb300 import _build
+    assert set(_build.VARIANTS) == {"debug", "staged"}
+    assert _build.lib_path(None) == _build.LIB
+    for v in _build.VARIANTS:
+        assert _build.lib_path(v).endswith("libbgk_%s.so" % v)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for v, want in (("staged", "libbgk_staged.so"), ("debug", "libbgk_debug.so"), ("other", "libbgk.so")):
+        env = dict(os.environ, BGK_LIBRARY=v)
+        r = subprocess.run([sys.executable, "-c", "import paper_2408_02350_gb300 as g; print(g.LIB_PATH)"],
+                           cwd=root, env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-1000:]
+        assert r.stdout.strip().endswith(want), (v, r.stdout)
+
+
 def test_bounds_checked_debug_build_exports_every_symbol():
     # the debug build (every list index a kernel loads checked against the point range)
     # compiles for sm_103a and exports the same ABI
