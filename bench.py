@@ -170,9 +170,38 @@ def _traffic_record(kernel: str, workload: str):
     return r.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
+def noisy_state(p: dict, n: int, seed: int):
+    """f = M(v; 1, 0, 1) (1 + 0.1 u), u uniform in [-1, 1] per (point, component, velocity)
+    from SplitMix64, rounded to FP32 (the FP32 library and the FP64 oracle start from the
+    same values)."""
+    import oracle
+    M = oracle.maxwellian(p, 1.0, (0.0, 0.0, 0.0), 1.0)
+    u = bi.uniform01(seed, n * M.size).reshape((n,) + M.shape)
+    return (M[None] * (1.0 + 0.1 * (2.0 * u - 1.0))).astype(np.float32)
+
+
+def oracle_errors(g, p: dict, cl: dict, f0, sim, nsteps: int) -> dict:
+    """The library's steps against the oracle's from the same state f0: relative max errors
+    of rho and T, the velocity normwise (max |du| / max |u|) and f (max |df| / max |f|)."""
+    s = g.Solver([p], [cl])
+    try:
+        s.set_f(np.ascontiguousarray(f0))
+        s.step(nsteps)
+        s.sync()
+        rho, u, T = s.moments()
+        f = s.get_f()
+    finally:
+        s.close()
+    rel = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    return {"steps": nsteps, "start": "seeded non-uniform state f = M (1 + 0.1 u), FP32-rounded",
+            "rho": rel(rho, sim.rho), "u": rel(u, sim.U), "T": rel(T, sim.T), "f": rel(f, sim.f)}
+
+
+def cpu_baseline(p: dict, nsteps: int = 1, g=None) -> dict:
     """The FP64 CPU oracle on a bounded sample of the workload: single-threaded, and its
-    OpenMP build (loops over points split among all host cores) beside it."""
+    OpenMP build (loops over points split among all host cores) beside it.  The OpenMP
+    run starts from a seeded non-uniform state; with the library g given, the same three
+    steps on the GPU are compared with it (`oracle_errors`)."""
     import oracle
     cl = bi.cloud_for(p)
     sim = oracle.Simulation(p, cl)
@@ -186,7 +215,8 @@ def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
                      % (nsteps, p["n"], p["dim"], p["nv"], p["dim"], n, dt),
            "host": _host_cpu()}
     try:
-        somp = oracle.Simulation(p, cl, omp=True)
+        f0 = noisy_state(p, n, 2408105) if g is not None else None
+        somp = oracle.Simulation(p, cl, omp=True, f0=f0)
         somp.run(1)  # warm-up: thread pool start
         k = max(2, nsteps)
         t0 = time.perf_counter()
@@ -199,6 +229,12 @@ def cpu_baseline(p: dict, nsteps: int = 1) -> dict:
                                 "over points on %d threads, %.1f s" % (k, thr, dto)}
     except (OSError, subprocess.CalledProcessError) as e:
         out["omp"] = {"unavailable": "OpenMP build of the oracle failed: %s" % e}
+        return out
+    if g is not None:
+        try:
+            out["oracle_errors"] = oracle_errors(g, p, cl, f0, somp, 1 + k)
+        except Exception as e:  # noqa: BLE001 - a failed comparison must not cost the bench line
+            out["oracle_errors"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     return out
 
 
@@ -800,7 +836,7 @@ def main():
                 "roofline": roofline, "kernels": kernels, "fp64_gpu": fp64, "adjoint": adj, "batched": batched,
                 "manage": manage, "extra": extra}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(p, 1)
+            line["cpu_baseline"] = cpu_baseline(p, 1, g)
     if dist is not None and not args.no_sharded:
         # the multi-GPU design for one cavity: the same workload split over the ranks by
         # velocity slabs (strong scaling), beside the weak-scaled replicas above
