@@ -88,3 +88,47 @@ def test_reference_arm_prints_its_line():
     assert line["config"]["same_workload"] and line["config"]["points"] == 201 ** 2
     assert line["cpu_baseline"]["cores"] == line["cpu_baseline"]["host"]["logical_cores"] or \
         line["cpu_baseline"]["cores"] >= 1
+
+
+def test_cpu_baseline_compares_the_library_with_the_oracle():
+    # the cpu_baseline leg on a small cavity, with a stand-in library whose solver is the
+    # oracle itself: the comparison runs end to end and finds no difference, and the
+    # seeded start is the FP32-rounded perturbed Maxwellian
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import bgk_inputs as bi
+    import oracle
+
+    class _Solver:
+        def __init__(self, ps, cls):
+            self.p, self.cl = ps[0], cls[0]
+
+        def set_f(self, f):
+            self.sim = oracle.Simulation(self.p, self.cl, f0=f)
+
+        def step(self, k):
+            self.sim.run(k)
+
+        def sync(self):
+            pass
+
+        def moments(self):
+            return self.sim.rho, self.sim.U, self.sim.T
+
+        def get_f(self):
+            return self.sim.f
+
+        def close(self):
+            pass
+
+    class _Lib:
+        Solver = _Solver
+
+    p = bi.config("cavity2d_ale_n201_v32_f32", n=13, nv=8)
+    out = bench.cpu_baseline(p, 1, _Lib())
+    e = out["oracle_errors"]
+    assert e["steps"] == 3 and max(e["rho"], e["u"], e["T"], e["f"]) == 0.0, e
+    f0 = bench.noisy_state(p, len(bi.cloud_for(p)["kind"]), 2408105)
+    M = oracle.maxwellian(p, 1.0, (0.0, 0.0, 0.0), 1.0)
+    assert f0.dtype == np.float32 and np.all(np.abs(f0 / M[None] - 1.0) <= 0.1 + 1e-6)
