@@ -450,7 +450,7 @@ def batched_cost(g, torch, stream, steps: int = 20, cases: int = 64) -> dict:
     return out
 
 
-def run_reference(args, p: dict) -> None:
+def run_reference(args, p: dict, over: dict | None = None) -> None:
     """Reference arm: the FP64 CPU oracle (its OpenMP build, all host cores) on the bench
     workload itself, W warm-up and K timed full steps; when those would take longer than
     about four minutes, each step is instead one full step of a smaller cavity with the
@@ -470,7 +470,8 @@ def run_reference(args, p: dict) -> None:
         # a smaller cavity: the step cost is about linear in the point count
         scale = budget_s / ((args.warmup + args.steps) * t1)
         sample_n = max(11, int((p["n"] - 1) * scale ** (1.0 / p["dim"])) + 1)
-        q = bi.config(WORKLOAD, n=sample_n, kn=p["kn"], storage=p["storage"])
+        q = bi.config(args.workload, **dict(over or {}, n=sample_n))
+        q["storage"] = p["storage"]
         cl = bi.cloud_for(q)
         sim = oracle.Simulation(q, cl, omp=True)
         sim.run(1)
@@ -482,16 +483,17 @@ def run_reference(args, p: dict) -> None:
     value = n * q["nv"] ** q["dim"] * args.steps / dt
     thr = oracle.threads(True)
     same = sample_n == p["n"]
-    what = ("one full FP64 time step of the bench workload itself (%d^%d points, %d^%d velocities, ALE, Kn %.2g)"
-            % (p["n"], p["dim"], p["nv"], p["dim"], p["kn"]) if same else
-            "one full FP64 time step of a %d^%d-point cavity with the bench's %d^%d velocity grid, ALE, Kn %.2g "
+    mode = "ALE" if p.get("ale") else "fixed points"
+    what = ("one full FP64 time step of the bench workload itself (%d^%d points, %d^%d velocities, %s, Kn %.2g)"
+            % (p["n"], p["dim"], p["nv"], p["dim"], mode, p["kn"]) if same else
+            "one full FP64 time step of a %d^%d-point cavity with the bench's %d^%d velocity grid, %s, Kn %.2g "
             "(%d points; the full workload would not fit the time budget)"
-            % (sample_n, q["dim"], q["nv"], q["dim"], q["kn"], n))
+            % (sample_n, q["dim"], q["nv"], q["dim"], mode, q["kn"], n))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "points": n, "velocities": q["nv"] ** q["dim"], "kn": q["kn"],
-                       "ale": True, "l2": "n/a (CPU)", "same_workload": same},
+            "config": {"workload": args.workload, "points": n, "velocities": q["nv"] ** q["dim"], "kn": q["kn"],
+                       "ale": bool(p.get("ale")), "l2": "n/a (CPU)", "same_workload": same},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": "each step: " + what + ", OpenMP over points on %d threads" % thr,
                              "host": _host_cpu()},
@@ -611,6 +613,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--config-file", default=None,
+                    help="a workload file (workloads/<name>.json, or an edited copy): its workload and "
+                         "parameters replace --workload")
     ap.add_argument("--storage", default=None, choices=[None, "f64", "f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -632,7 +637,11 @@ def main():
                     help="2: the workload with fixed points and the second-order time step (profiling runs)")
     args = ap.parse_args()
     rank, world, local_rank = _dist_env()
-    over = {"n": args.n} if args.n else {}
+    over = {}
+    if args.config_file:
+        args.workload, over = bi.workload_from_file(args.config_file)
+    if args.n:
+        over["n"] = args.n
     if args.time_order:
         over.update(ale=0, time_order=args.time_order)
     if args.sharded and args.impl == "ours":
@@ -645,7 +654,7 @@ def main():
     if args.storage:
         p["storage"] = args.storage
     if args.impl == "reference":
-        run_reference(args, p)
+        run_reference(args, p, over)
         return
 
     import torch
@@ -796,7 +805,8 @@ def main():
     achieved = instr_per_launch / kt_avg_s / 1e12
     bytes_per_update = 2 * ncomp * elem  # read f once, write f^{n+1} once
     hbm_achieved = bytes_per_update * upd_per_step / kt_avg_s / 1e9
-    traffic = _traffic_record("k_transport", args.workload)
+    # (the captured traffic is that of the named workload as it stands: none for variants)
+    traffic = _traffic_record("k_transport", args.workload) if not over and not args.storage else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinstr/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock, %s)" % (sm_max, peaks["source"]),

@@ -30,7 +30,9 @@ points strictly inside the lid face move with the lid velocity.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 
 import numpy as np
 
@@ -206,6 +208,42 @@ def config(name: str, **overrides) -> dict:
     if "vmax" in overrides and "dt" not in overrides:
         p["dt"] = cfl_dt(p["dx"], p["vmax"], p["dim"])
     return p
+
+
+# One JSON file per workload (the parameters of CONFIGS[name], written by
+# write_workload_files); a copy with some parameters changed describes a variant.
+WORKLOAD_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads")
+
+
+def write_workload_files(folder: str = WORKLOAD_DIR) -> list[str]:
+    """Write folder/<name>.json = {"workload": name, "params": CONFIGS[name]} for every workload."""
+    os.makedirs(folder, exist_ok=True)
+    paths = []
+    for name in sorted(CONFIGS):
+        path = os.path.join(folder, name + ".json")
+        with open(path, "w") as fh:
+            json.dump({"workload": name, "params": CONFIGS[name]}, fh, indent=1, sort_keys=True)
+            fh.write("\n")
+        paths.append(path)
+    return paths
+
+
+def workload_from_file(path: str) -> tuple[str, dict]:
+    """(name, overrides) of a workload file {"workload": a CONFIGS name, "params": {...}}:
+    the overrides are the parameters that differ from the named workload, so that
+    config(name, **overrides) gives the file's parameters back.  Unknown names and keys
+    raise ValueError."""
+    with open(path) as fh:
+        d = json.load(fh)
+    name = d.get("workload")
+    if name not in CONFIGS:
+        raise ValueError("%s: workload %r is not one of %s" % (path, name, sorted(CONFIGS)))
+    base = CONFIGS[name]
+    params = d.get("params", {})
+    unknown = sorted(set(params) - set(base) - {"time_order", "wls_order", "vgrid", "spare_points", "skin"})
+    if unknown:
+        raise ValueError("%s: unknown parameters %s" % (path, unknown))
+    return name, {k: v for k, v in params.items() if base.get(k) != v}
 
 
 def batched_cases(count: int = 64, seed0: int = 2408400) -> list[dict]:
