@@ -1043,7 +1043,6 @@ void or_init_maxwellian(const or_params* p, int64_t n, double rho0, const double
 int or_adjoint_step(const or_params* p, int64_t n, const int32_t* kind, const double* normal,
                     const int32_t* cnt, const int32_t* col, const double* abar, const double* frame,
                     const double* recon, const double* f, const double* lam1, double* lam0, double* dtheta) {
-  const double pi = 3.14159265358979323846;
   int dim = p->dim, cap = p->max_nbrs, nc = ncomp_of(dim);
   int64_t NV = nvel_of(dim, p->nv), row = nc * NV;
   double wv = quad_weight(p);

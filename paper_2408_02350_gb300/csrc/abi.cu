@@ -999,7 +999,7 @@ int bgk_shard_sizes(bgk_ctx* ctx, int32_t ci, int64_t* n_xm, int64_t* n_xw) {
 
 int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
   CallRange range_("bgk_shard_transport");
-  CaseHost* cp;
+  CaseHost* cp = nullptr;
   int st;
   if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_transport", &cp))) return st;
   CaseHost& c = *cp;
@@ -1029,7 +1029,7 @@ int bgk_shard_transport(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
 
 int bgk_shard_relax(bgk_ctx* ctx, int32_t ci, const double* xm, double* xw, void* stream) {
   CallRange range_("bgk_shard_relax");
-  CaseHost* cp;
+  CaseHost* cp = nullptr;
   int st;
   if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_relax", &cp))) return st;
   CaseHost& c = *cp;
@@ -1057,7 +1057,7 @@ int bgk_shard_relax(bgk_ctx* ctx, int32_t ci, const double* xm, double* xw, void
 
 int bgk_shard_walls(bgk_ctx* ctx, int32_t ci, const double* xw, void* stream) {
   CallRange range_("bgk_shard_walls");
-  CaseHost* cp;
+  CaseHost* cp = nullptr;
   int st;
   if ((st = shard_case(ctx, ci, xw, true, "bgk_shard_walls", &cp))) return st;
   CaseHost& c = *cp;
@@ -1080,7 +1080,7 @@ int bgk_shard_walls(bgk_ctx* ctx, int32_t ci, const double* xw, void* stream) {
 }
 
 int bgk_shard_partial(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
-  CaseHost* cp;
+  CaseHost* cp = nullptr;
   int st;
   if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_partial", &cp))) return st;
   CaseView v = cp->cv;
@@ -1091,7 +1091,7 @@ int bgk_shard_partial(bgk_ctx* ctx, int32_t ci, double* xm, void* stream) {
 }
 
 int bgk_shard_set_moments(bgk_ctx* ctx, int32_t ci, const double* xm, void* stream) {
-  CaseHost* cp;
+  CaseHost* cp = nullptr;
   int st;
   if ((st = shard_case(ctx, ci, xm, false, "bgk_shard_set_moments", &cp))) return st;
   CaseView v = cp->cv;
