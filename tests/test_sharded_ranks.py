@@ -221,3 +221,42 @@ def test_two_gloo_ranks_reproduce_the_unsharded_oracle(name, over, steps):
         _, _, _, rho, U, T, x = out[r]
         assert np.abs(rho - sim.rho).max() <= 1e-12 and np.abs(T - sim.T).max() <= 1e-12
         assert np.abs(U - sim.U).max() <= 1e-12 and np.abs(x - sim.x).max() <= 1e-14
+
+
+def _lost_rank_worker(rank, world, port, out):
+    import datetime
+    import time
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bgk_inputs as bi
+    from paper_2408_02350_gb300.sharded import ShardedSolver, TorchExchange, velocity_slabs
+    from test_sharded_ranks import OracleSlab
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    p = bi.config("cavity2d_n41_v16_f64", n=9, nv=4, vmax=3.0)
+    cl = bi.cloud_for(p)
+    lo, hi = velocity_slabs(p["nv"] ** p["dim"], world)[rank]
+    s = ShardedSolver([OracleSlab(p, cl, lo, hi)], TorchExchange())
+    s.set_maxwellian()
+    s.step(1)
+    if rank == 1:
+        # the rank is lost between steps, with nothing of its own in flight
+        os._exit(0)
+    t0 = time.time()
+    try:
+        s.step(2)
+        out[rank] = ("finished", time.time() - t0)
+    except Exception as e:  # noqa: BLE001 - whatever the backend raises for the lost peer
+        out[rank] = ("error", type(e).__name__, time.time() - t0)
+
+
+def test_a_lost_rank_ends_the_survivor_s_next_exchange_with_an_error():
+    # two gloo ranks step together; one leaves between steps; the other's next step
+    # does not hang: its first exchange fails (within the group's 20 s timeout)
+    world, port = 2, _free_port()
+    out = mp.get_context("spawn").Manager().dict()
+    mp.spawn(_lost_rank_worker, args=(world, port, out), nprocs=world, join=True)
+    assert 1 not in out
+    assert out[0][0] == "error" and out[0][-1] < 30.0, out[0]
