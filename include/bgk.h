@@ -178,7 +178,11 @@ int bgk_peak_fp64(double* dfma_per_s, void* stream);
  * n_points[n_cases]; x, kind, normal are host arrays concatenated over the
  * cases.  Copies the geometry to the current CUDA device and allocates every
  * device buffer.  f is not initialised until bgk_set_maxwellian or bgk_set_f.
- * Synchronous.  Returns BGK_E_INVAL for an unsupported parameter. */
+ * Positions lie in the unit box [0, 1]^dim (the cell grid of the neighbour search
+ * spans it), kind is 0 for an interior point and a wall id > 0 otherwise, normals are
+ * finite.  Synchronous.  Returns BGK_E_INVAL, before touching the device, for an
+ * unsupported parameter, a non-finite or out-of-box coordinate, a negative kind or a
+ * non-finite normal. */
 int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, const double* x,
              const int32_t* kind, const double* normal, bgk_ctx** out);
 

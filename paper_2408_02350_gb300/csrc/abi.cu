@@ -543,6 +543,27 @@ int bgk_init(const bgk_params* p, int32_t n_cases, const int64_t* n_points, cons
     const char* why = nullptr;
     if (!check_params(p[c], n_points[c], &why)) return fail(nullptr, BGK_E_INVAL, "bgk_init: case %d: %s", c, why);
   }
+  // geometry: positions finite and inside the unit box that the cell grid spans, kinds
+  // >= 0, normals finite (the arrays are read with the offsets of the copies below)
+  {
+    int64_t off = 0;
+    for (int c = 0; c < n_cases; ++c) {
+      const int dim = p[c].dim;
+      for (int64_t k = off; k < off + n_points[c]; ++k) {
+        for (int a = 0; a < dim; ++a) {
+          const double xa = x[k * dim + a], na = normal[k * dim + a];
+          if (!(xa >= 0.0 && xa <= 1.0))
+            return fail(nullptr, BGK_E_INVAL, "bgk_init: case %d: point %lld: coordinate %d = %g is not in [0, 1]",
+                        c, (long long)(k - off), a, xa);
+          if (!std::isfinite(na))
+            return fail(nullptr, BGK_E_INVAL, "bgk_init: case %d: point %lld: normal is not finite", c,
+                        (long long)(k - off));
+        }
+        if (kind[k] < 0) return fail(nullptr, BGK_E_INVAL, "bgk_init: case %d: point %lld: kind < 0", c, (long long)(k - off));
+      }
+      off += n_points[c];
+    }
+  }
   bgk_ctx* ctx = new (std::nothrow) bgk_ctx();
   if (!ctx) return fail(nullptr, BGK_E_NOMEM, "bgk_init: host allocation failed");
   int st = BGK_OK;

@@ -109,6 +109,31 @@ def test_init_rejects_bad_parameters_before_touching_the_device(lib, field, valu
     assert "bgk_init" in lib.bgk_last_error(None)
 
 
+@pytest.mark.parametrize("what,value", [("x", float("nan")), ("x", 1.5), ("x", -0.1), ("kind", -1),
+                                        ("normal", float("inf"))])
+def test_init_rejects_corrupt_geometry_before_touching_the_device(lib, what, value):
+    # a corrupted position, kind or normal of one point of the second case
+    p = bi.config("cavity2d_n41_v16_f64", n=5)
+    cl = bi.cloud_for(p)
+    n = len(cl["kind"])
+    x = np.concatenate([cl["x"], cl["x"]])
+    kind = np.concatenate([cl["kind"], cl["kind"]])
+    normal = np.concatenate([cl["normal"], cl["normal"]])
+    i = n + 7
+    if what == "x":
+        x[i, 1] = value
+    elif what == "kind":
+        kind[i] = value
+    else:
+        normal[i, 0] = value
+    q = lib.params_from(p)
+    with pytest.raises(lib.BGKError) as e:
+        lib.bgk_init([q, q], [n, n], x, kind, normal)
+    assert e.value.code == lib.BGK_E_INVAL
+    msg = lib.bgk_last_error(None)
+    assert "case 1" in msg and "point 7" in msg, msg
+
+
 @pytest.mark.parametrize("change", ["moving_without_ale", "lid_id", "negative_radius", "negative_id"])
 def test_init_rejects_bad_body_parameters(lib, change):
     p = bi.config("body2d_ale_n201_v32_f32", n=11, nv=4, storage="f64", body_radius=0.2, body_centre=[0.5, 0.5, 0.0])
